@@ -1,0 +1,342 @@
+#!/usr/bin/env python3
+"""Superblock H·v benchmark (direct n-leg DMRG, arXiv 0707.0159).
+
+Workload: the 3-leg Hubbard ladder superblock, t = 1, U = 8, column d = 64,
+blocks of m = 256 seeded states (V is 16384 x 16384, dense, no sectors).
+One step = one full superblock H·v, Y = H_l V + V H_r^T + H_c V_c, through
+dmrg2d_apply_H on inputs already resident in HBM.  value = algorithmic flops
+of one H·v x steps x ranks / time.  V (>= 1 GB) is larger than the 129 MB L2,
+so no flush is needed between steps.
+
+Also reported: the roofline of the dominant kernel (CUDA events around every
+launch of it, from the library's own timing hook), the end-to-end rate through
+the same call with the vector staged from/to pinned host memory, SM clocks
+sampled during the timed region, the CPU oracle timed on a bounded sample, and
+(with --tte) the time to the ground energy of the mixed-precision solver next
+to the plain FP64 Lanczos.
+
+  python bench.py [--gpus N --steps K --warmup W] [--precision tf32|bf16|fp32|fp64]
+  python bench.py --impl reference     # the CPU oracle on the same workload
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "superblock H·v TFLOP/s & time to ground energy at 1e-8 rel. vs plain FP64"
+WORKLOAD = "ladder3_hubbard_d64_m256_dense"
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, r[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(seconds: float = 15.0):
+    """The oracle's H·v on the same workload, timed on a bounded slab of its outputs.
+
+    The slab is rows i1 < r of every tile in the first i3-column of V; its
+    algorithmic work is the fraction (r/m1)(1/d) of one H·v.
+    """
+    from oracle.superblock import Superblock
+    from paper_0707_0159_gb300 import synth
+    mdl, left, right, _ = synth.workload_ladder3_hubbard_m256()
+    sb = Superblock(mdl, left, right)
+    v = synth.start_vector(sb.n_vec, 12)
+    t0 = time.perf_counter()
+    sb.apply_slab(v, [0], [0])
+    t1 = time.perf_counter() - t0
+    r = int(max(1, min(sb.m1, seconds / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    sb.apply_slab(v, list(range(r)), [0])
+    dt = time.perf_counter() - t0
+    frac = (r / sb.m1) * (1.0 / sb.d)
+    flops = _flops_dense_structure(sb) * frac
+    return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": _cpu_threads(),
+            "kind": "oracle",
+            "sample": f"oracle 4-index H·v restricted to i1 < {r} and i3 = 0 "
+                      f"({frac:.2e} of one H·v), {dt:.1f} s, numpy FP64"}
+
+
+def _cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        return max(i.get("num_threads", 1) for i in threadpool_info()) or os.cpu_count()
+    except Exception:
+        return os.cpu_count()
+
+
+def _flops_dense_structure(sb):
+    """Algorithmic flops of one H·v counted from the oracle's term structure (CPU only)."""
+    import numpy as np
+    d, m1, m4 = sb.d, sb.m1, sb.m4
+    posL = np.eye(d, dtype=bool)
+    for _, X, _ in sb.terms_l[2:]:
+        posL |= X != 0
+    posR = np.eye(d, dtype=bool)
+    for _, X, _ in sb.terms_r[2:]:
+        posR |= X != 0
+    Hc = sb.col.H
+    eye = np.eye(d, dtype=bool)
+    offL = (Hc != 0) & ~posL & ~eye
+    offR = (Hc != 0) & ~posR & ~eye
+    S = (sb.H_center() != 0) | np.kron(eye, offL) | np.kron(offR, eye)
+    return (2.0 * posL.sum() * m1 * m1 * d * m4 + 2.0 * posR.sum() * m4 * m4 * m1 * d
+            + 2.0 * S.sum() * m1 * m4)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(seconds=3.0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(seconds=float(args.ref_seconds)))
+    total = time.perf_counter() - t0
+    v = statistics.median([x["value"] for x in vals])
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded blocks, numpy default_rng)",
+            "config": {"workload": WORKLOAD, "m": 256, "d": 64, "n_legs": 3, "t": 1.0, "U": 8.0},
+            "cpu_baseline": dict(vals[-1], value=v),
+            "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_0707_0159_gb300 import dmrg2d, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    prec = dmrg2d.PRECISION[args.precision]
+
+    mdl, left, right, _ = synth.workload_ladder3_hubbard_m256()
+    ops = dmrg2d.build_ops(mdl, left, right)
+    info = ops.info
+    n, flops = info["n_vec"], info["flops_per_apply"]
+    if prec in (dmrg2d.TF32, dmrg2d.BF16) and not info["tc_ok"]:
+        raise RuntimeError("tensor-core path unavailable for this workload")
+    in_dt = {dmrg2d.FP64: torch.float64, dmrg2d.FP32: torch.float32, dmrg2d.TF32: torch.float32,
+             dmrg2d.BF16: torch.bfloat16}[prec]
+    out_dt = torch.float64 if prec == dmrg2d.FP64 else torch.float32
+    v_host = torch.from_numpy(synth.start_vector(n, 12 + rank)).to(in_dt)
+    v = v_host.to(dev)
+    y = torch.empty(n, dtype=out_dt, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        dmrg2d.apply_H(ops, v, y, prec)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    clk.start()
+    time.sleep(0.3)
+    dmrg2d.profile_start(ops, args.steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        dmrg2d.apply_H(ops, v, y, prec)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    k_ms, k_n = dmrg2d.profile_stop(ops)
+    clocks = clk.stop()
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * flops / (ms * 1e-3) / 1e12
+
+    # ---- end to end through the same call: pinned host -> device -> H·v -> host ----
+    vh = v_host.pin_memory()
+    yh = torch.empty(n, dtype=out_dt).pin_memory()
+    for _ in range(2):
+        v.copy_(vh, non_blocking=True)
+        dmrg2d.apply_H(ops, v, y, prec)
+        yh.copy_(y, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier()
+    ke = max(2, args.steps // 2)
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for _ in range(ke):
+        v.copy_(vh, non_blocking=True)
+        dmrg2d.apply_H(ops, v, y, prec)
+        yh.copy_(y, non_blocking=True)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e2.elapsed_time(e3) / ke
+    if world > 1:
+        t = torch.tensor([ms_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    e2e = {"value": world * flops / (ms_e2e * 1e-3) / 1e12, "unit": "TFLOP/s",
+           "h2d_bytes_per_step": vh.numel() * vh.element_size(),
+           "d2h_bytes_per_step": yh.numel() * yh.element_size()}
+
+    # ---- roofline of the dominant kernel ----
+    pk = peaks()
+    kernel_ms = k_ms / max(k_n, 1)
+    achieved = flops / (kernel_ms * 1e-3) / 1e12
+    if prec == dmrg2d.BF16:
+        peak, pnote = pk.get("bf16_tflops", 1900.0), "measured bf16 (MEASURED_PEAKS.json)"
+        bound = "tensor"
+    elif prec == dmrg2d.TF32:
+        peak = pk.get("bf16_tflops", 1900.0) * 1.1 / 2.25
+        pnote = "measured bf16 x nominal tf32/bf16 ratio 1.1/2.25"
+        bound = "tensor"
+    elif prec == dmrg2d.FP64:
+        peak, pnote, bound = 1.25, "nominal GB300 FP64 1.25 TFLOP/s", "alu"
+    else:
+        peak, pnote, bound = 2 * 152 * 128 * 2.07e9 / 1e12, "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz", "alu"
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None, "peak_source": pnote,
+            "kernel_ms": kernel_ms, "kernel_launches": k_n}
+
+    out = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": {dmrg2d.FP64: "f64", dmrg2d.FP32: "f32", dmrg2d.TF32: "tf32",
+                     dmrg2d.BF16: "bf16"}[prec],
+           "data": "synthetic (seeded blocks and vector, numpy default_rng)",
+           "config": {"workload": WORKLOAD, "m": 256, "d": 64, "n_legs": 3, "t": 1.0, "U": 8.0,
+                      "n_vec": n, "flops_per_hv": flops, "parallelism": f"replicas{world}",
+                      "l2": "inputs larger than L2 (no flush)"},
+           "clocks": clocks, "e2e": e2e,
+           "gpu_launches": k_n if prec == dmrg2d.FP64 or prec == dmrg2d.FP32 else 2 * k_n,
+           "roofline": roof}
+
+    if args.tte and rank == 0:
+        out["time_to_energy"] = time_to_energy(ops, n, prec, args, dev)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(seconds=float(args.ref_seconds))
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def time_to_energy(ops, n, prec, args, dev):
+    import torch
+    from paper_0707_0159_gb300 import dmrg2d, synth
+    v0 = torch.from_numpy(synth.start_vector(n, 3)).to(dev)
+    res = {}
+    x = v0.clone()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e_mp, st_mp, c_mp = dmrg2d.lanczos_ground(ops, x, precision=prec, refine=1, tol=args.tte_tol,
+                                              inner_iter=40, outer_max=15)
+    torch.cuda.synchronize()
+    res["mixed"] = {"seconds": time.perf_counter() - t0, "energy": e_mp, "status": c_mp, **st_mp}
+    if args.tte_fp64:
+        x = v0.clone()
+        t0 = time.perf_counter()
+        e64, st64, c64 = dmrg2d.lanczos_ground(ops, x, precision=dmrg2d.FP64, tol=args.tte_tol,
+                                               max_iter=400, krylov_dim=100, check_every=5)
+        torch.cuda.synchronize()
+        res["fp64"] = {"seconds": time.perf_counter() - t0, "energy": e64, "status": c64, **st64}
+        res["rel_diff"] = abs(e_mp - e64) / abs(e64)
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default=os.environ.get("DMRG2D_BENCH_PREC", "tf32"),
+                    choices=["tf32", "bf16", "fp32", "fp64"])
+    ap.add_argument("--tte", action="store_true", help="also time the ground-state solve")
+    ap.add_argument("--tte-fp64", action="store_true", help="with --tte: also the plain FP64 solve")
+    ap.add_argument("--tte-tol", type=float, default=1e-7)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

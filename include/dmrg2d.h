@@ -1,0 +1,193 @@
+/*
+ * dmrg2d.h — C ABI of the GB300 superblock H·v library for the direct n-leg DMRG
+ * of Yamada, Okumura and Machida (arXiv 0707.0159).
+ *
+ * The superblock is block 1 (m1 states, index i1) · block 2 = one lattice
+ * column of n sites (d states, i2) · block 3 = one column (d states, i3) ·
+ * block 4 (m4 states, i4) — paper Fig. 2.  Its Hamiltonian is split as in
+ * Eq. (dec):  H = H_l (x) 1_{34} + H_r (x) 1_{12} + H_c (x) 1_{14},
+ * and with the superblock vector v viewed as the (m1 d) x (d m4) matrix V,
+ *     H v  ->  Y = H_l V + V H_r^T + H_c V_c
+ * (paper, text after Eq. (dec)).  This library evaluates the last term as
+ * sum_k A_k V B_k^T with A_k = a_k (x) 1_{m1}, B_k = b_k (x) 1_{m4}, the same
+ * product written on V instead of the permuted V_c.
+ *
+ * Layouts (all fixed by the paper's index map):
+ *   - vector v, dense (no sectors): element of state |i1 i2 i3 i4> at
+ *       i1 + m1*i2 + m1*d*i4 + m1*d*m4*i3          (0-based)
+ *     i.e. V = column-major (m1 d) x (d m4) matrix, leading dimension m1*d.
+ *   - column basis: spin column i = sum_y b_y 2^y (b_y = 1: spin up on leg y);
+ *     Hubbard column i = sum_y (n_{y,up} + 2 n_{y,dn}) 4^y, fermion modes
+ *     ordered by that bit position (leg 0 up, leg 0 down, leg 1 up, ...).
+ *   - fermion signs: global mode order block 1, column 2, column 3, block 4;
+ *     each subsystem's operators carry the parities of the subsystems before it.
+ *   - block operators (inputs): host arrays, row-major m x m, <i|op|j> at i*m+j.
+ *   - sector-restricted vectors (target != NULL): see dmrg2d_build_ops.
+ *
+ * Ownership: every function copies what it needs from its inputs; the caller
+ * keeps ownership of all pointers passed in.  dmrg2d_ops owns the device memory
+ * it allocates until dmrg2d_free_ops.  Device vectors passed to apply/solve are
+ * caller-owned.  No function throws; errors are returned as negative codes and
+ * dmrg2d_last_error() gives a thread-local message.
+ */
+#ifndef DMRG2D_H
+#define DMRG2D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes --------------------------------------------------------------- */
+enum {
+  DMRG2D_OK = 0,
+  DMRG2D_EINVAL = -1,       /* bad argument (NULL, out-of-range value)               */
+  DMRG2D_ESHAPE = -2,       /* inconsistent sizes                                    */
+  DMRG2D_ENOMEM = -3,       /* device or host allocation failed                      */
+  DMRG2D_ECUDA = -4,        /* a CUDA runtime call failed                            */
+  DMRG2D_ENOCONV = -5,      /* solver hit its iteration budget (best estimate kept)  */
+  DMRG2D_ETIMEOUT = -6,     /* a device-side bounded wait gave up                    */
+  DMRG2D_ENAN = -7,         /* NaN/Inf met in a reduction                            */
+  DMRG2D_EUNSUPPORTED = -8  /* precision/shape combination not built                 */
+};
+
+/* ---- models (paper: Heisenberg J_z = J_xy, Hubbard U/t; open boundaries) ------------ */
+enum { DMRG2D_HEISENBERG = 0, DMRG2D_HUBBARD = 1 };
+
+/* arithmetic of the H·v products */
+enum {
+  DMRG2D_FP64 = 0,   /* v, y double; DFMA                                            */
+  DMRG2D_TF32 = 1,   /* v float, y float; tcgen05 kind::tf32, FP32 accumulate in TMEM */
+  DMRG2D_BF16 = 2,   /* v bf16 (uint16 bits), y float; tcgen05 kind::f16, FP32 acc  */
+  DMRG2D_FP32 = 3    /* v float, y float; FP32 FMA on CUDA cores                      */
+};
+
+typedef struct dmrg2d_model {
+  int kind;          /* DMRG2D_HEISENBERG or DMRG2D_HUBBARD                            */
+  int n_legs;        /* sites per column n >= 1; d = 2^n (spins) or 4^n (electrons)  */
+  double J_leg;      /* Heisenberg coupling along the legs (between columns)          */
+  double J_rung;     /* Heisenberg coupling along a column                            */
+  double t;          /* Hubbard hopping (same along legs and rungs)                  */
+  double U;          /* Hubbard on-site repulsion                                    */
+  int rung_pbc;      /* 1: close each column into a ring (n > 2 only)                */
+} dmrg2d_model;
+
+/* One renormalised block (block 1 or block 4), host memory, row-major m x m.
+ * edge[] holds the operators of the block's sites that touch the neighbouring
+ * column, one entry per leg y:
+ *   Heisenberg: edge[2y] = S^z_y, edge[2y+1] = S^+_y   (S^- = (S^+)^T)
+ *   Hubbard:    edge[2y] = c^dag_{y,up}, edge[2y+1] = c^dag_{y,dn} (c = (c^dag)^T),
+ *               each carrying the block's own Jordan-Wigner string;
+ *               parity[i] = +1/-1 is the block's fermion parity (diagonal).
+ * n_edge = 0 describes a lattice end (the block is not coupled to the column).
+ * qn (optional): per-state quantum numbers, row-major m x nq with nq = 1
+ * (N_up) for spins and nq = 2 (N_up, N_dn) for electrons; needed only for
+ * sector-restricted operation. */
+typedef struct dmrg2d_block {
+  int m;
+  const double* H;
+  int n_edge;
+  const double* const* edge;
+  const double* parity;
+  const int32_t* qn;
+} dmrg2d_block;
+
+typedef struct dmrg2d_ops dmrg2d_ops;
+
+typedef struct dmrg2d_ops_info {
+  int64_t n_vec;           /* length of v                                          */
+  int m1, m4, d, n_legs;
+  int n_blk_left;          /* dense m1 x m1 blocks of H_l (nonzero block positions) */
+  int n_blk_right;         /* dense m4 x m4 blocks of H_r                           */
+  int n_scalar;            /* scalar tile moves (H_c terms + off-diagonal column    */
+                           /* terms of H_l/H_r, both of the form c * I_m1 (x) I_m4) */
+  double flops_per_apply;  /* algorithmic flops of one H·v (see dmrg2d_apply_H)     */
+  int tc_ok;               /* 1 if the tcgen05 path supports these shapes          */
+  int64_t device_bytes;    /* device memory owned by the ops object                */
+} dmrg2d_ops_info;
+
+/* Build the packed operators of H_l, H_r and H_c (paper Eq. (dec)).
+ *   H_l = 1_d (x) H_B1 + H_col (x) 1_m1 + sum_k X_k (x) E_k   (row index i1 + m1*i2)
+ *   H_r = 1_d (x) H_B4 + H_col (x) 1_m4 + sum_k X'_k (x) E'_k (row index i4 + m4*i3)
+ *   H_c = sum_k a_k (on i2) b_k (on i3), the n leg bonds between the columns.
+ * Column operators are built here from the model.  Every block position
+ * (i2, i2') of H_l touched by a block operator becomes one dense m1 x m1 block;
+ * terms that are multiples of the identity in block space (off-diagonal
+ * column terms, all of H_c) become scalar tile moves.
+ * target: NULL for the dense superblock; otherwise the sector is not yet
+ * supported by this build and DMRG2D_EUNSUPPORTED is returned.
+ * stream: cudaStream_t (may be NULL) used for the uploads.
+ * Errors: EINVAL for NULL/invalid fields, ESHAPE if n_edge != 0 and != 2*n_legs,
+ * ENOMEM/ECUDA on device failures (nothing leaks; *out is left NULL). */
+int dmrg2d_build_ops(const dmrg2d_model* model, const dmrg2d_block* left,
+                     const dmrg2d_block* right, const int32_t* target,
+                     dmrg2d_ops** out, void* stream);
+
+int dmrg2d_ops_get_info(const dmrg2d_ops* ops, dmrg2d_ops_info* info);
+
+/* y = H v (paper: H_l V + V H_r^T + H_c V_c).  v and y are caller-owned device
+ * buffers of info.n_vec elements in the layout above; they must not overlap.
+ * Element types by precision: FP64 double/double; FP32 and TF32 float/float;
+ * BF16 bf16/float.  TF32 and BF16 need info.tc_ok (else EUNSUPPORTED).
+ * Algorithmic flops: 2*n_blk_left*m1^2*(d*m4) + 2*n_blk_right*m4^2*(m1*d)
+ * + 2*n_scalar*m1*m4.  Asynchronous on `stream`; allocates nothing; no host
+ * synchronisation, so the call can be captured in a CUDA graph. */
+int dmrg2d_apply_H(const dmrg2d_ops* ops, const void* v, void* y, int precision, void* stream);
+
+/* Ground state of H by Lanczos (implied by the paper's "exact diagonalization"
+ * of the superblock; the algorithm is not named there). */
+typedef struct dmrg2d_solver_opts {
+  int max_iter;        /* Lanczos steps (plain) or total inner steps budget (mixed) */
+  int krylov_dim;      /* basis vectors kept before an explicit restart (>= 2)      */
+  double tol;          /* stop when ||H x - theta x|| <= tol * |theta|              */
+  int fixed_steps;     /* 1: run exactly max_iter steps with no convergence test    */
+  int precision;       /* precision of the inner H·v (FP64 for the plain method)    */
+  int refine;          /* 1: FP64 outer residual correction (mixed precision)       */
+  int inner_iter;      /* mixed: low-precision steps per correction solve          */
+  int outer_max;       /* mixed: maximum FP64 outer iterations                      */
+  int check_every;     /* plain: convergence test every this many steps             */
+} dmrg2d_solver_opts;
+
+typedef struct dmrg2d_solver_stats {
+  int iters;           /* Lanczos / inner steps taken                               */
+  int outer;           /* FP64 outer iterations (mixed)                             */
+  int n_hv_fp64;       /* FP64 H·v calls                                            */
+  int n_hv_low;        /* low-precision H·v calls                                   */
+  double resid;        /* final ||H x - theta x|| (FP64)                            */
+  double hv_ms;        /* device time spent in H·v launches (CUDA events)           */
+  double elapsed_ms;   /* wall time of the call                                     */
+} dmrg2d_solver_stats;
+
+/* x_inout: device double[n_vec]; on entry the start vector (any norm, nonzero),
+ * on exit the normalised ground-state estimate.  energy_out: host double.
+ * Allocates its Krylov basis on the device for the duration of the call.
+ * Returns OK, ENOCONV (estimate kept), ENAN, or an allocation/CUDA error. */
+int dmrg2d_lanczos_ground(const dmrg2d_ops* ops, const dmrg2d_solver_opts* opts,
+                          double* x_inout, double* energy_out,
+                          dmrg2d_solver_stats* stats, void* stream);
+
+void dmrg2d_default_solver_opts(dmrg2d_solver_opts* opts);
+
+/* Kernel timing for benchmarks.  After dmrg2d_profile_start, every apply_H call
+ * records a CUDA event pair around its dominant kernel (the fused H_l V + V H_r^T
+ * contraction) on the call's stream, for at most max_launches calls; the event
+ * pairs are created here, so apply_H still allocates nothing.
+ * dmrg2d_profile_stop waits for the recorded events, returns the summed kernel
+ * time in milliseconds and the number of timed launches, and turns timing off. */
+int dmrg2d_profile_start(dmrg2d_ops* ops, int max_launches);
+int dmrg2d_profile_stop(dmrg2d_ops* ops, double* total_ms, int* launches);
+
+void dmrg2d_free_ops(dmrg2d_ops* ops);
+
+/* Thread-local text of the last error of this thread ("" if none). */
+const char* dmrg2d_last_error(void);
+
+/* Library version string. */
+const char* dmrg2d_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DMRG2D_H */

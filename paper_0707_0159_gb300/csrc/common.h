@@ -1,0 +1,103 @@
+// Internal declarations shared by the translation units of libdmrg2d.
+// Not part of the public ABI (see include/dmrg2d.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/dmrg2d.h"
+
+namespace dmrg2d {
+
+// ---- error reporting (thread-local message, negative status codes) --------------------
+int set_error(int code, const char* fmt, ...);
+void clear_error();
+
+#define D2_CUDA(call)                                                                   \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return ::dmrg2d::set_error(DMRG2D_ECUDA, "%s failed: %s (%s:%d)", #call,          \
+                                 cudaGetErrorString(e_), __FILE__, __LINE__);           \
+  } while (0)
+
+#define D2_TRY(expr)                                                                    \
+  do {                                                                                  \
+    int s_ = (expr);                                                                    \
+    if (s_ != DMRG2D_OK) return s_;                                                     \
+  } while (0)
+
+// ---- packed operators -------------------------------------------------------------------
+// Output tile (i2, i3) of V is the m1 x m4 sub-matrix with rows i1 + m1*i2 and
+// columns i4 + m4*i3; its flat tile id is i2 + d*i3.
+struct DeviceOps {
+  // H_l: CSR over block rows i2; block e couples (i2, Lcol[e]); m1 x m1 row-major
+  int nL = 0;
+  int* Lptr = nullptr;
+  int* Lcol = nullptr;
+  double* HL64 = nullptr;
+  float* HL32 = nullptr;
+  __nv_bfloat16* HL16 = nullptr;
+  // H_r: CSR over block columns i3; block e couples (i3, Rcol[e]); m4 x m4 row-major
+  // stored as [i4][i4'] so that Y(:, i4) += sum_i4' V(:, i4') * HR[i4][i4']
+  int nR = 0;
+  int* Rptr = nullptr;
+  int* Rcol = nullptr;
+  double* HR64 = nullptr;
+  float* HR32 = nullptr;
+  __nv_bfloat16* HR16 = nullptr;
+  // scalar tile moves: CSR over destination tiles t = i2 + d*i3
+  int nC = 0;
+  int* Cptr = nullptr;
+  int* Csrc = nullptr;
+  double* Cval64 = nullptr;
+  float* Cval32 = nullptr;
+};
+
+}  // namespace dmrg2d
+
+struct dmrg2d_ops {
+  int kind = 0, n_legs = 0, d = 0, m1 = 0, m4 = 0;
+  int64_t n_vec = 0;
+  int64_t ld = 0;  // rows of V = m1*d (leading dimension of the column-major V)
+  double flops = 0.0;
+  int64_t device_bytes = 0;
+  int tc_ok = 0;
+  int device = 0;
+  dmrg2d::DeviceOps dev;
+  // host copies of the CSR structure (tile schedulers, tests)
+  std::vector<int> hLptr, hLcol, hRptr, hRcol, hCptr, hCsrc;
+  std::vector<double> hCval;
+  // tensor-core path state (tensor maps of the operator blocks), opaque here
+  void* tc = nullptr;
+  // kernel timing (dmrg2d_profile_start/stop); apply_H only records into it
+  mutable std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
+  mutable size_t prof_used = 0;
+  mutable bool prof_on = false;
+};
+
+namespace dmrg2d {
+
+// event pair around the dominant kernel of one apply_H call (null when not profiling)
+inline std::pair<cudaEvent_t, cudaEvent_t> prof_slot(const dmrg2d_ops* ops) {
+  if (!ops->prof_on || ops->prof_used >= ops->prof_ev.size()) return {nullptr, nullptr};
+  return ops->prof_ev[ops->prof_used++];
+}
+
+// hv_simt.cu
+int launch_hv_simt_f64(const dmrg2d_ops* ops, const double* v, double* y, cudaStream_t s);
+int launch_hv_simt_f32(const dmrg2d_ops* ops, const float* v, float* y, cudaStream_t s);
+
+// hv_tc.cu
+int tc_prepare(dmrg2d_ops* ops, cudaStream_t s);
+void tc_release(dmrg2d_ops* ops);
+int launch_hv_tc(const dmrg2d_ops* ops, const void* v, float* y, int precision, cudaStream_t s);
+
+// vector kernels used by the solvers (solver.cu)
+int convert_f64_to(const double* x, void* out, int precision, int64_t n, cudaStream_t s);
+
+}  // namespace dmrg2d

@@ -1,0 +1,722 @@
+// Ground-state solvers on the GPU: FP64 Lanczos and the mixed-precision outer loop.
+//
+// The paper obtains the superblock ground state by repeated H·v ("HMED",
+// discussion of Fig. 5) without naming the eigensolver; this file uses
+//   * Lanczos with full reorthogonalisation (classical Gram-Schmidt twice), the
+//     tridiagonal eigenproblem solved on the GPU (Sturm bisection + inverse
+//     iteration), explicit restart with the Ritz vector when the basis is full;
+//   * mixed precision: Lanczos with low-precision H·v gives a start vector; an
+//     FP64 outer loop then keeps a small subspace U with H U computed in FP64,
+//     takes the Rayleigh-Ritz pair (theta, x) and its FP64 residual r, and adds a
+//     correction t from a few conjugate-gradient steps on
+//         (I - x x^T)(H~ - theta)(I - x x^T) t = -r
+//     with H~ the low-precision H·v.  Only the FP64 residual decides convergence.
+// All vectors are FP64 in device memory; reductions use a fixed grid and a fixed
+// summation order, so results are bitwise reproducible run to run.
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "common.h"
+
+namespace dmrg2d {
+
+namespace {
+
+constexpr int VT = 256;        // threads per vector-kernel block
+constexpr int RED_BLOCKS = 1216;  // 8 x 152 SMs; partial sums per reduction
+constexpr int MD_CHUNK = 8;    // basis vectors per multi-dot block
+
+int vgrid(int64_t n) {
+  int64_t g = (n + VT - 1) / VT;
+  return (int)(g < RED_BLOCKS ? (g < 1 ? 1 : g) : RED_BLOCKS);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ double block_sum(double v) {
+  __shared__ double ws[VT / 32];
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) ws[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    r = lane < VT / 32 ? ws[lane] : 0.0;
+    r = warp_sum(r);
+  }
+  __syncthreads();
+  return r;  // valid in thread 0
+}
+
+__global__ void k_dot_partial(const double* __restrict__ a, const double* __restrict__ b, int64_t n,
+                              double* __restrict__ part) {
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * VT + threadIdx.x; i < n; i += (int64_t)gridDim.x * VT)
+    s += a[i] * b[i];
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// out[i] = op(sum_b part[i*np + b]); one block per i.  op: 0 sum, 1 sqrt(sum)
+__global__ void k_reduce(const double* __restrict__ part, int np, double* __restrict__ out, int op) {
+  const double* p = part + (size_t)blockIdx.x * np;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < np; b += VT) s += p[b];
+  s = block_sum(s);
+  if (threadIdx.x == 0) out[blockIdx.x] = op == 1 ? sqrt(s) : s;
+}
+
+// part[(i0+c)*gridDim.x + blk] = partial of Q_{i0+c} . w
+__global__ void k_multidot_partial(const double* __restrict__ Q, int64_t stride, int k,
+                                   const double* __restrict__ w, int64_t n, double* __restrict__ part) {
+  const int i0 = blockIdx.y * MD_CHUNK;
+  double acc[MD_CHUNK];
+#pragma unroll
+  for (int c = 0; c < MD_CHUNK; ++c) acc[c] = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * VT + threadIdx.x; e < n; e += (int64_t)gridDim.x * VT) {
+    const double we = w[e];
+#pragma unroll
+    for (int c = 0; c < MD_CHUNK; ++c)
+      if (i0 + c < k) acc[c] += Q[(int64_t)(i0 + c) * stride + e] * we;
+  }
+#pragma unroll
+  for (int c = 0; c < MD_CHUNK; ++c) {
+    double s = block_sum(acc[c]);
+    if (threadIdx.x == 0 && i0 + c < k) part[(size_t)(i0 + c) * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// w -= sum_i h[i] Q_i   (sign = -1)  or  x = sum_i h[i] Q_i  (sign = 0)
+__global__ void k_combo(double* __restrict__ out, const double* __restrict__ Q, int64_t stride, int k,
+                        const double* __restrict__ h, int64_t n, int sign) {
+  extern __shared__ double hs[];
+  for (int i = threadIdx.x; i < k; i += VT) hs[i] = h[i];
+  __syncthreads();
+  for (int64_t e = (int64_t)blockIdx.x * VT + threadIdx.x; e < n; e += (int64_t)gridDim.x * VT) {
+    double s = 0.0;
+    for (int i = 0; i < k; ++i) s += hs[i] * Q[(int64_t)i * stride + e];
+    out[e] = sign ? out[e] - s : s;
+  }
+}
+
+// w -= alpha[j] q_j + beta[j-1] q_{j-1}
+__global__ void k_lz_axpy2(double* __restrict__ w, const double* __restrict__ qj,
+                           const double* __restrict__ qjm1, const double* __restrict__ alpha_j,
+                           const double* __restrict__ beta_jm1, int64_t n) {
+  const double a = *alpha_j;
+  const double b = beta_jm1 ? *beta_jm1 : 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * VT + threadIdx.x; e < n; e += (int64_t)gridDim.x * VT) {
+    double r = w[e] - a * qj[e];
+    if (qjm1) r -= b * qjm1[e];
+    w[e] = r;
+  }
+}
+
+// out = in / *nrm   (zero when the norm is zero)
+__global__ void k_scale_inv(double* __restrict__ out, const double* __restrict__ in,
+                            const double* __restrict__ nrm, int64_t n) {
+  const double s = *nrm;
+  const double f = s > 0.0 ? 1.0 / s : 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * VT + threadIdx.x; e < n; e += (int64_t)gridDim.x * VT)
+    out[e] = in[e] * f;
+}
+
+// y = a*x + b*y with host scalars
+__global__ void k_axpby(double* __restrict__ y, const double* __restrict__ x, double a, double b,
+                        int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * VT + threadIdx.x; e < n; e += (int64_t)gridDim.x * VT)
+    y[e] = a * x[e] + b * y[e];
+}
+
+__global__ void k_f64_to_f32(const double* __restrict__ x, float* __restrict__ o, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * VT + threadIdx.x; e < n; e += (int64_t)gridDim.x * VT)
+    o[e] = (float)x[e];
+}
+
+__global__ void k_f64_to_bf16(const double* __restrict__ x, __nv_bfloat16* __restrict__ o, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * VT + threadIdx.x; e < n; e += (int64_t)gridDim.x * VT)
+    o[e] = __float2bfloat16_rn((float)x[e]);
+}
+
+__global__ void k_f32_to_f64(const float* __restrict__ x, double* __restrict__ o, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * VT + threadIdx.x; e < n; e += (int64_t)gridDim.x * VT)
+    o[e] = (double)x[e];
+}
+
+// ---- lowest eigenpair of the Lanczos tridiagonal T_k (diag alpha, off-diag beta) ----
+// Sturm-sequence bisection for the eigenvalue, inverse iteration (tridiagonal LU with
+// partial pivoting) for the eigenvector.  out[0] = theta, out[1] = |beta_{k-1} s_{k-1}|,
+// out[2] = status (0 ok, 1 NaN).  scratch: 6*k doubles.
+__device__ int sturm_count(const double* a, const double* b, int k, double x) {
+  int cnt = 0;
+  double q = a[0] - x;
+  if (q < 0) ++cnt;
+  for (int i = 1; i < k; ++i) {
+    if (q == 0.0) q = 1e-300;
+    q = (a[i] - x) - b[i - 1] * b[i - 1] / q;
+    if (q < 0) ++cnt;
+  }
+  return cnt;
+}
+
+__global__ void k_tridiag_ground(const double* __restrict__ alpha, const double* __restrict__ beta,
+                                 int k, double* __restrict__ s, double* __restrict__ out,
+                                 double* __restrict__ scr) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double lo = 1e300, hi = -1e300;
+  bool bad = false;
+  for (int i = 0; i < k; ++i) {
+    const double r = (i > 0 ? fabs(beta[i - 1]) : 0.0) + (i + 1 < k ? fabs(beta[i]) : 0.0);
+    lo = fmin(lo, alpha[i] - r);
+    hi = fmax(hi, alpha[i] + r);
+    if (!isfinite(alpha[i]) || !isfinite(beta[i])) bad = true;
+  }
+  if (bad) {
+    out[0] = nan("");
+    out[1] = nan("");
+    out[2] = 1.0;
+    return;
+  }
+  for (int it = 0; it < 200 && hi - lo > 2.2e-16 * fmax(fabs(lo), fabs(hi)) + 1e-300; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (sturm_count(alpha, beta, k, mid) >= 1) hi = mid; else lo = mid;
+  }
+  const double theta = 0.5 * (lo + hi);
+  // inverse iteration: solve (T - theta) z = s, with gtsv-style partial pivoting
+  double* dl = scr;          // sub-diagonal
+  double* dd = scr + k;      // diagonal
+  double* du = scr + 2 * k;  // super-diagonal
+  double* du2 = scr + 3 * k; // second super-diagonal (fill-in)
+  double* z = scr + 4 * k;
+  const double tiny = 1e-14 * fmax(fabs(lo), fabs(hi)) + 1e-300;
+  for (int i = 0; i < k; ++i) s[i] = 1.0 / sqrt((double)k);
+  for (int rep = 0; rep < 3; ++rep) {
+    for (int i = 0; i < k; ++i) {
+      dd[i] = alpha[i] - theta;
+      du[i] = i + 1 < k ? beta[i] : 0.0;
+      dl[i] = i + 1 < k ? beta[i] : 0.0;
+      du2[i] = 0.0;
+      z[i] = s[i];
+    }
+    for (int i = 0; i + 1 < k; ++i) {   // forward elimination with row swaps
+      if (fabs(dd[i]) >= fabs(dl[i])) {
+        if (dd[i] == 0.0) dd[i] = tiny;
+        const double f = dl[i] / dd[i];
+        dd[i + 1] -= f * du[i];
+        z[i + 1] -= f * z[i];
+        dl[i] = 0.0;
+      } else {
+        const double f = dd[i] / dl[i];
+        dd[i] = dl[i];
+        double t = dd[i + 1];
+        dd[i + 1] = du[i] - f * t;
+        du[i] = t;
+        if (i + 2 < k) {
+          du2[i] = du[i + 1];
+          du[i + 1] = -f * du[i + 1];
+        }
+        t = z[i];
+        z[i] = z[i + 1];
+        z[i + 1] = t - f * z[i + 1];
+      }
+    }
+    if (dd[k - 1] == 0.0) dd[k - 1] = tiny;
+    z[k - 1] /= dd[k - 1];
+    if (k > 1) z[k - 2] = (z[k - 2] - du[k - 2] * z[k - 1]) / dd[k - 2];
+    for (int i = k - 3; i >= 0; --i) z[i] = (z[i] - du[i] * z[i + 1] - du2[i] * z[i + 2]) / dd[i];
+    double nrm = 0.0;
+    for (int i = 0; i < k; ++i) nrm += z[i] * z[i];
+    nrm = sqrt(nrm);
+    if (!(nrm > 0.0) || !isfinite(nrm)) {
+      out[2] = 1.0;
+      break;
+    }
+    for (int i = 0; i < k; ++i) s[i] = z[i] / nrm;
+  }
+  // fix the sign so the first nonzero component is positive (deterministic Ritz vector)
+  double sg = 1.0;
+  for (int i = 0; i < k; ++i)
+    if (s[i] != 0.0) {
+      sg = s[i] > 0 ? 1.0 : -1.0;
+      break;
+    }
+  for (int i = 0; i < k; ++i) s[i] *= sg;
+  out[0] = theta;
+  out[1] = fabs(beta[k - 1] * s[k - 1]);
+  if (out[2] != 1.0) out[2] = 0.0;
+}
+
+// lowest eigenpair of a small symmetric matrix G (n x n, leading dim ldg) by cyclic Jacobi
+__global__ void k_small_eigh(const double* __restrict__ G, int n, int ldg, double* __restrict__ out,
+                             double* __restrict__ c, double* __restrict__ scr) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double* A = scr;          // n*n
+  double* Vv = scr + n * n; // n*n
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      A[i * n + j] = 0.5 * (G[i * ldg + j] + G[j * ldg + i]);
+      Vv[i * n + j] = i == j ? 1.0 : 0.0;
+    }
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        tot += A[i * n + j] * A[i * n + j];
+        if (i != j) off += A[i * n + j] * A[i * n + j];
+      }
+    if (off <= 1e-32 * tot + 1e-300) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = A[p * n + q];
+        if (apq == 0.0) continue;
+        const double th = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+        const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+        const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+        for (int r = 0; r < n; ++r) {  // A <- J^T A J
+          const double arp = A[r * n + p], arq = A[r * n + q];
+          A[r * n + p] = cs * arp - sn * arq;
+          A[r * n + q] = sn * arp + cs * arq;
+        }
+        for (int r = 0; r < n; ++r) {
+          const double apr = A[p * n + r], aqr = A[q * n + r];
+          A[p * n + r] = cs * apr - sn * aqr;
+          A[q * n + r] = sn * apr + cs * aqr;
+        }
+        for (int r = 0; r < n; ++r) {
+          const double vrp = Vv[r * n + p], vrq = Vv[r * n + q];
+          Vv[r * n + p] = cs * vrp - sn * vrq;
+          Vv[r * n + q] = sn * vrp + cs * vrq;
+        }
+      }
+  }
+  int best = 0;
+  for (int i = 1; i < n; ++i)
+    if (A[i * n + i] < A[best * n + best]) best = i;
+  double sg = Vv[best] >= 0 ? 1.0 : -1.0;
+  for (int i = 0; i < n; ++i) c[i] = sg * Vv[i * n + best];
+  out[0] = A[best * n + best];
+}
+
+// ---- host-side helpers ---------------------------------------------------------------------
+struct DevBuf {
+  void* p = nullptr;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+};
+
+struct Ctx {
+  const dmrg2d_ops* ops;
+  cudaStream_t s;
+  int64_t n;
+  double* part = nullptr;    // RED_BLOCKS * max_k partial sums
+  double* scal = nullptr;    // small device scalars
+  double* hscal = nullptr;   // pinned host mirror
+  void* lo = nullptr;        // low-precision copy of the H·v input
+  float* y32 = nullptr;      // low-precision H·v output
+  dmrg2d_solver_stats* st = nullptr;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+  size_t ev_used = 0;
+  bool timing = true;
+
+  int hv(int prec, const double* x, double* y) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (timing) {
+      if (ev_used == ev.size()) {
+        cudaEvent_t e0, e1;
+        D2_CUDA(cudaEventCreate(&e0));
+        D2_CUDA(cudaEventCreate(&e1));
+        ev.push_back({e0, e1});
+      }
+      a = ev[ev_used].first;
+      b = ev[ev_used].second;
+      ++ev_used;
+    }
+    if (prec == DMRG2D_FP64) {
+      if (a) D2_CUDA(cudaEventRecord(a, s));
+      D2_TRY(launch_hv_simt_f64(ops, x, y, s));
+      if (b) D2_CUDA(cudaEventRecord(b, s));
+      if (st) st->n_hv_fp64++;
+      return DMRG2D_OK;
+    }
+    D2_TRY(convert_f64_to(x, lo, prec, n, s));
+    if (a) D2_CUDA(cudaEventRecord(a, s));
+    if (prec == DMRG2D_FP32) {
+      D2_TRY(launch_hv_simt_f32(ops, (const float*)lo, y32, s));
+    } else {
+      D2_TRY(launch_hv_tc(ops, lo, y32, prec, s));
+    }
+    if (b) D2_CUDA(cudaEventRecord(b, s));
+    k_f32_to_f64<<<vgrid(n), VT, 0, s>>>(y32, y, n);
+    D2_CUDA(cudaGetLastError());
+    if (st) st->n_hv_low++;
+    return DMRG2D_OK;
+  }
+
+  double hv_ms() {
+    double tot = 0.0;
+    for (size_t i = 0; i < ev_used; ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev[i].first, ev[i].second) == cudaSuccess) tot += ms;
+    }
+    return tot;
+  }
+
+  ~Ctx() {
+    for (auto& e : ev) {
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
+  }
+
+  // *out (device) = a . b
+  int dot(const double* a, const double* b, double* out) {
+    const int g = vgrid(n);
+    k_dot_partial<<<g, VT, 0, s>>>(a, b, n, part);
+    k_reduce<<<1, VT, 0, s>>>(part, g, out, 0);
+    D2_CUDA(cudaGetLastError());
+    return DMRG2D_OK;
+  }
+  int nrm(const double* a, double* out) {
+    const int g = vgrid(n);
+    k_dot_partial<<<g, VT, 0, s>>>(a, a, n, part);
+    k_reduce<<<1, VT, 0, s>>>(part, g, out, 1);
+    D2_CUDA(cudaGetLastError());
+    return DMRG2D_OK;
+  }
+  // h[0..k) = Q[0..k) . w
+  int multidot(const double* Q, int64_t stride, int k, const double* w, double* h) {
+    const int g = vgrid(n);
+    dim3 grid(g, (k + MD_CHUNK - 1) / MD_CHUNK);
+    k_multidot_partial<<<grid, VT, 0, s>>>(Q, stride, k, w, n, part);
+    k_reduce<<<k, VT, 0, s>>>(part, g, h, 0);
+    D2_CUDA(cudaGetLastError());
+    return DMRG2D_OK;
+  }
+  int combo(double* out, const double* Q, int64_t stride, int k, const double* h, int sign) {
+    k_combo<<<vgrid(n), VT, k * sizeof(double), s>>>(out, Q, stride, k, h, n, sign);
+    D2_CUDA(cudaGetLastError());
+    return DMRG2D_OK;
+  }
+  int axpby(double* y, const double* x, double a, double b) {
+    k_axpby<<<vgrid(n), VT, 0, s>>>(y, x, a, b, n);
+    D2_CUDA(cudaGetLastError());
+    return DMRG2D_OK;
+  }
+  int scale_inv(double* out, const double* in, const double* nrm_dev) {
+    k_scale_inv<<<vgrid(n), VT, 0, s>>>(out, in, nrm_dev, n);
+    D2_CUDA(cudaGetLastError());
+    return DMRG2D_OK;
+  }
+  // read k device doubles into the pinned mirror and wait
+  int fetch(const double* dsrc, int k) {
+    D2_CUDA(cudaMemcpyAsync(hscal, dsrc, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+    D2_CUDA(cudaStreamSynchronize(s));
+    return DMRG2D_OK;
+  }
+};
+
+int dmalloc(DevBuf& b, size_t bytes) {
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    return set_error(DMRG2D_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+  }
+  return DMRG2D_OK;
+}
+
+// Lanczos from x (FP64, any norm); on return x holds the normalised Ritz vector.
+// scal layout: [0] theta, [1] resid, [2] status, [3..] scratch scalars
+int lanczos(Ctx& C, int prec, double* x, int max_iter, int kdim, double tol, int fixed,
+            int check_every, double* theta_out, double* resid_out, int* iters_out) {
+  const int64_t n = C.n;
+  if (kdim < 2) kdim = 2;
+  if (kdim > max_iter + 1) kdim = max_iter + 1;
+  DevBuf Qb, wb, ab, bb, hb, sb, tb;
+  D2_TRY(dmalloc(Qb, sizeof(double) * (size_t)(kdim + 1) * n));
+  D2_TRY(dmalloc(wb, sizeof(double) * n));
+  D2_TRY(dmalloc(ab, sizeof(double) * (kdim + 1)));
+  D2_TRY(dmalloc(bb, sizeof(double) * (kdim + 1)));
+  D2_TRY(dmalloc(hb, sizeof(double) * (kdim + 1)));
+  D2_TRY(dmalloc(sb, sizeof(double) * (kdim + 1)));
+  D2_TRY(dmalloc(tb, sizeof(double) * 6 * (kdim + 1)));
+  double* Q = (double*)Qb.p;
+  double* w = (double*)wb.p;
+  double* alpha = (double*)ab.p;
+  double* beta = (double*)bb.p;
+  double* h = (double*)hb.p;
+  double* sv = (double*)sb.p;
+  double* scr = (double*)tb.p;
+  double* out3 = C.scal;
+
+  D2_TRY(C.nrm(x, C.scal + 3));
+  D2_TRY(C.scale_inv(Q, x, C.scal + 3));
+  int j = 0, total = 0;
+  double theta = 0.0, resid = INFINITY;
+  int status = DMRG2D_ENOCONV;
+  if (check_every < 1) check_every = 1;
+  while (true) {
+    double* qj = Q + (int64_t)j * n;
+    D2_TRY(C.hv(prec, qj, w));
+    D2_TRY(C.dot(qj, w, alpha + j));
+    k_lz_axpy2<<<vgrid(n), VT, 0, C.s>>>(w, qj, j > 0 ? qj - n : nullptr, alpha + j,
+                                        j > 0 ? beta + j - 1 : nullptr, n);
+    D2_CUDA(cudaGetLastError());
+    for (int pass = 0; pass < 2; ++pass) {  // CGS2 against q_0..q_j
+      D2_TRY(C.multidot(Q, n, j + 1, w, h));
+      D2_TRY(C.combo(w, Q, n, j + 1, h, -1));
+    }
+    D2_TRY(C.nrm(w, beta + j));
+    ++j;
+    ++total;
+    const bool last = total >= max_iter;
+    const bool full = j >= kdim;
+    if (last || full || (!fixed && total % check_every == 0)) {
+      k_tridiag_ground<<<1, 1, 0, C.s>>>(alpha, beta, j, sv, out3, scr);
+      D2_CUDA(cudaGetLastError());
+      D2_TRY(C.fetch(out3, 3));
+      theta = C.hscal[0];
+      resid = C.hscal[1];
+      if (C.hscal[2] != 0.0 || !std::isfinite(theta)) {
+        status = set_error(DMRG2D_ENAN, "NaN/Inf in the Lanczos recurrence");
+        break;
+      }
+      const bool conv = !fixed && resid <= tol * fabs(theta);
+      if (conv || last || full) {
+        D2_TRY(C.combo(x, Q, n, j, sv, 0));  // Ritz vector
+        if (conv) {
+          status = DMRG2D_OK;
+          break;
+        }
+        if (last) {
+          status = fixed ? DMRG2D_OK : DMRG2D_ENOCONV;
+          if (!fixed) set_error(DMRG2D_ENOCONV, "Lanczos: %d steps, residual %.3e", total, resid);
+          break;
+        }
+        // explicit restart from the Ritz vector
+        D2_TRY(C.nrm(x, C.scal + 3));
+        D2_TRY(C.scale_inv(Q, x, C.scal + 3));
+        j = 0;
+        continue;
+      }
+    }
+    D2_TRY(C.scale_inv(Q + (int64_t)j * n, w, beta + j - 1));
+  }
+  D2_TRY(C.nrm(x, C.scal + 3));
+  D2_TRY(C.scale_inv(x, x, C.scal + 3));
+  *theta_out = theta;
+  *resid_out = resid;
+  *iters_out = total;
+  return status;
+}
+
+}  // namespace
+
+int convert_f64_to(const double* x, void* out, int precision, int64_t n, cudaStream_t s) {
+  if (precision == DMRG2D_BF16)
+    k_f64_to_bf16<<<vgrid(n), VT, 0, s>>>(x, (__nv_bfloat16*)out, n);
+  else
+    k_f64_to_f32<<<vgrid(n), VT, 0, s>>>(x, (float*)out, n);
+  D2_CUDA(cudaGetLastError());
+  return DMRG2D_OK;
+}
+
+// Mixed precision: low-precision Lanczos start, FP64 outer Rayleigh-Ritz + CG corrections.
+static int mixed_solve(Ctx& C, const dmrg2d_solver_opts* o, double* x, double* energy) {
+  const int64_t n = C.n;
+  const int prec = o->precision;
+  // 1. low-precision Lanczos for the start vector
+  double th0 = 0, r0 = 0;
+  int it0 = 0;
+  int st = lanczos(C, prec, x, o->inner_iter, o->inner_iter + 1, 1e-6, 0, 5, &th0, &r0, &it0);
+  if (st != DMRG2D_OK && st != DMRG2D_ENOCONV) return st;
+  C.st->iters += it0;
+  // 2. FP64 outer loop on a small subspace
+  const int smax = 6;
+  DevBuf Ub, Wb, xb, hxb, rb, tb, pb, qb, Gb, cb, scb;
+  D2_TRY(dmalloc(Ub, sizeof(double) * (size_t)smax * n));
+  D2_TRY(dmalloc(Wb, sizeof(double) * (size_t)smax * n));
+  D2_TRY(dmalloc(hxb, sizeof(double) * n));
+  D2_TRY(dmalloc(rb, sizeof(double) * n));
+  D2_TRY(dmalloc(tb, sizeof(double) * n));
+  D2_TRY(dmalloc(pb, sizeof(double) * n));
+  D2_TRY(dmalloc(qb, sizeof(double) * n));
+  D2_TRY(dmalloc(Gb, sizeof(double) * smax * smax));
+  D2_TRY(dmalloc(cb, sizeof(double) * smax));
+  D2_TRY(dmalloc(scb, sizeof(double) * 2 * smax * smax));
+  double *U = (double*)Ub.p, *W = (double*)Wb.p, *hx = (double*)hxb.p, *r = (double*)rb.p;
+  double *t = (double*)tb.p, *p = (double*)pb.p, *q = (double*)qb.p, *G = (double*)Gb.p;
+  double *cc = (double*)cb.p, *scr = (double*)scb.p;
+  double* sc = C.scal;  // scalars: [4] tmp dot, [5..] host-fetched
+  D2_CUDA(cudaMemsetAsync(G, 0, sizeof(double) * smax * smax, C.s));
+
+  D2_TRY(C.nrm(x, sc + 3));
+  D2_TRY(C.scale_inv(U, x, sc + 3));
+  D2_TRY(C.hv(DMRG2D_FP64, U, W));
+  int s = 1;
+  std::vector<double> Gh(smax * smax, 0.0);
+  auto update_G_col = [&](int jcol) -> int {
+    // G[i][jcol] = U_i . W_jcol for i <= jcol; mirror
+    D2_TRY(C.multidot(U, n, jcol + 1, W + (int64_t)jcol * n, sc + 8));
+    D2_TRY(C.fetch(sc + 8, jcol + 1));
+    for (int i = 0; i <= jcol; ++i) Gh[i * smax + jcol] = Gh[jcol * smax + i] = C.hscal[i];
+    return DMRG2D_OK;
+  };
+  D2_TRY(update_G_col(0));
+  double theta = 0.0, rn = INFINITY;
+  int status = DMRG2D_ENOCONV;
+  for (int outer = 0; outer <= o->outer_max; ++outer) {
+    D2_CUDA(cudaMemcpyAsync(G, Gh.data(), sizeof(double) * smax * smax, cudaMemcpyHostToDevice, C.s));
+    k_small_eigh<<<1, 1, 0, C.s>>>(G, s, smax, sc + 5, cc, scr);
+    D2_CUDA(cudaGetLastError());
+    D2_TRY(C.combo(x, U, n, s, cc, 0));
+    D2_TRY(C.combo(hx, W, n, s, cc, 0));
+    D2_TRY(C.fetch(sc + 5, 1));
+    theta = C.hscal[0];
+    D2_CUDA(cudaMemcpyAsync(r, hx, sizeof(double) * n, cudaMemcpyDeviceToDevice, C.s));
+    D2_TRY(C.axpby(r, x, -theta, 1.0));  // r = hx - theta x
+    D2_TRY(C.nrm(r, sc + 6));
+    D2_TRY(C.fetch(sc + 6, 1));
+    rn = C.hscal[0];
+    C.st->outer = outer;
+    if (!std::isfinite(theta) || !std::isfinite(rn)) {
+      status = set_error(DMRG2D_ENAN, "NaN/Inf in the FP64 outer loop");
+      break;
+    }
+    if (rn <= o->tol * fabs(theta)) {
+      status = DMRG2D_OK;
+      break;
+    }
+    if (outer == o->outer_max) {
+      set_error(DMRG2D_ENOCONV, "mixed: %d outer steps, residual %.3e", outer, rn);
+      break;
+    }
+    // ---- inner CG on (I - xx^T)(H~ - theta)(I - xx^T) t = -r, t0 = 0 ----
+    D2_CUDA(cudaMemsetAsync(t, 0, sizeof(double) * n, C.s));
+    // res (stored in r) = -r projected; p = res
+    D2_TRY(C.axpby(r, r, 0.0, -1.0));
+    D2_TRY(C.dot(x, r, sc + 4));
+    D2_TRY(C.fetch(sc + 4, 1));
+    D2_TRY(C.axpby(r, x, -C.hscal[0], 1.0));
+    D2_CUDA(cudaMemcpyAsync(p, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, C.s));
+    D2_TRY(C.dot(r, r, sc + 4));
+    D2_TRY(C.fetch(sc + 4, 1));
+    double rr = C.hscal[0];
+    const double rr0 = rr;
+    for (int it = 0; it < o->inner_iter; ++it) {
+      D2_TRY(C.hv(prec, p, q));
+      D2_TRY(C.axpby(q, p, -theta, 1.0));  // q = H~p - theta p
+      D2_TRY(C.dot(x, q, sc + 4));
+      D2_TRY(C.dot(p, q, sc + 5));
+      D2_TRY(C.fetch(sc + 4, 2));
+      const double xq = C.hscal[0], pq = C.hscal[1];
+      C.st->iters++;
+      if (!(pq > 0.0)) break;
+      D2_TRY(C.axpby(q, x, -xq, 1.0));     // project
+      const double a = rr / pq;
+      D2_TRY(C.axpby(t, p, a, 1.0));
+      D2_TRY(C.axpby(r, q, -a, 1.0));
+      D2_TRY(C.dot(r, r, sc + 4));
+      D2_TRY(C.fetch(sc + 4, 1));
+      const double rr1 = C.hscal[0];
+      if (rr1 <= 1e-8 * rr0) break;
+      D2_TRY(C.axpby(p, r, 1.0, rr1 / rr));  // p = r + (rr1/rr) p
+      rr = rr1;
+    }
+    // ---- orthonormalise t against U and extend the subspace ----
+    if (s == smax) {  // restart with the current Ritz pair
+      D2_CUDA(cudaMemcpyAsync(U, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, C.s));
+      D2_CUDA(cudaMemcpyAsync(W, hx, sizeof(double) * n, cudaMemcpyDeviceToDevice, C.s));
+      s = 1;
+      std::fill(Gh.begin(), Gh.end(), 0.0);
+      Gh[0] = theta;
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+      D2_TRY(C.multidot(U, n, s, t, sc + 8));
+      D2_TRY(C.combo(t, U, n, s, sc + 8, -1));
+    }
+    D2_TRY(C.nrm(t, sc + 4));
+    D2_TRY(C.fetch(sc + 4, 1));
+    if (!(C.hscal[0] > 0.0)) {
+      set_error(DMRG2D_ENOCONV, "mixed: correction vanished, residual %.3e", rn);
+      break;
+    }
+    D2_TRY(C.scale_inv(U + (int64_t)s * n, t, sc + 4));
+    D2_TRY(C.hv(DMRG2D_FP64, U + (int64_t)s * n, W + (int64_t)s * n));
+    D2_TRY(update_G_col(s));
+    ++s;
+  }
+  C.st->resid = rn;
+  *energy = theta;
+  return status;
+}
+
+}  // namespace dmrg2d
+
+using namespace dmrg2d;
+
+extern "C" int dmrg2d_lanczos_ground(const dmrg2d_ops* ops, const dmrg2d_solver_opts* opts,
+                                     double* x_inout, double* energy_out,
+                                     dmrg2d_solver_stats* stats, void* stream) {
+  if (!ops || !x_inout || !energy_out) return set_error(DMRG2D_EINVAL, "NULL argument");
+  clear_error();
+  dmrg2d_solver_opts o;
+  if (opts) o = *opts; else dmrg2d_default_solver_opts(&o);
+  if (o.max_iter < 1) return set_error(DMRG2D_EINVAL, "max_iter < 1");
+  if (o.krylov_dim > 512 || o.inner_iter > 511)
+    return set_error(DMRG2D_EINVAL, "krylov_dim > 512 or inner_iter > 511");
+  if (o.precision != DMRG2D_FP64 && o.precision != DMRG2D_FP32 && o.precision != DMRG2D_TF32 &&
+      o.precision != DMRG2D_BF16)
+    return set_error(DMRG2D_EINVAL, "unknown precision %d", o.precision);
+  if ((o.precision == DMRG2D_TF32 || o.precision == DMRG2D_BF16) && !ops->tc_ok)
+    return set_error(DMRG2D_EUNSUPPORTED, "tensor-core path unsupported for these shapes");
+  const auto t0 = std::chrono::steady_clock::now();
+  dmrg2d_solver_stats local{};
+  Ctx C;
+  C.ops = ops;
+  C.s = (cudaStream_t)stream;
+  C.n = ops->n_vec;
+  C.st = &local;
+  DevBuf part, scal, lo, y32;
+  D2_TRY(dmalloc(part, sizeof(double) * (size_t)RED_BLOCKS * 520));
+  D2_TRY(dmalloc(scal, sizeof(double) * 64));
+  C.part = (double*)part.p;
+  C.scal = (double*)scal.p;
+  D2_CUDA(cudaMallocHost(&C.hscal, sizeof(double) * 64));
+  struct PinnedFree {
+    double* p;
+    ~PinnedFree() { cudaFreeHost(p); }
+  } pf{C.hscal};
+  if (o.precision != DMRG2D_FP64) {
+    D2_TRY(dmalloc(lo, (o.precision == DMRG2D_BF16 ? 2 : 4) * (size_t)C.n));
+    D2_TRY(dmalloc(y32, sizeof(float) * (size_t)C.n));
+    C.lo = lo.p;
+    C.y32 = (float*)y32.p;
+  }
+  int st;
+  double energy = 0.0;
+  if (o.refine && o.precision != DMRG2D_FP64) {
+    st = mixed_solve(C, &o, x_inout, &energy);
+  } else {
+    double resid = 0.0;
+    int iters = 0;
+    st = lanczos(C, o.precision, x_inout, o.max_iter, o.krylov_dim, o.tol, o.fixed_steps,
+                 o.check_every, &energy, &resid, &iters);
+    local.iters = iters;
+    local.resid = resid;
+  }
+  cudaError_t e = cudaStreamSynchronize(C.s);
+  if (e != cudaSuccess && st == DMRG2D_OK)
+    st = set_error(DMRG2D_ECUDA, "solver: %s", cudaGetErrorString(e));
+  local.hv_ms = C.hv_ms();
+  local.elapsed_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  *energy_out = energy;
+  if (stats) *stats = local;
+  return st;
+}

@@ -1,0 +1,232 @@
+"""Python binding of libdmrg2d (include/dmrg2d.h): argument marshalling only.
+
+Every step of the H·v path and the solvers runs in the library's CUDA kernels;
+this module converts numpy/torch arguments into the C structures and device
+pointers.  There is no fallback: if the shared library is missing or fails to
+load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HEISENBERG, HUBBARD = 0, 1
+FP64, TF32, BF16, FP32 = 0, 1, 2, 3
+PRECISION = {"fp64": FP64, "tf32": TF32, "bf16": BF16, "fp32": FP32}
+STATUS = {0: "OK", -1: "EINVAL", -2: "ESHAPE", -3: "ENOMEM", -4: "ECUDA", -5: "ENOCONV",
+          -6: "ETIMEOUT", -7: "ENAN", -8: "EUNSUPPORTED"}
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libdmrg2d.so")
+_lib = None
+
+
+class Dmrg2dError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Model(C.Structure):
+    _fields_ = [("kind", C.c_int), ("n_legs", C.c_int), ("J_leg", C.c_double),
+                ("J_rung", C.c_double), ("t", C.c_double), ("U", C.c_double), ("rung_pbc", C.c_int)]
+
+
+class Block(C.Structure):
+    _fields_ = [("m", C.c_int), ("H", C.POINTER(C.c_double)), ("n_edge", C.c_int),
+                ("edge", C.POINTER(C.POINTER(C.c_double))), ("parity", C.POINTER(C.c_double)),
+                ("qn", C.POINTER(C.c_int32))]
+
+
+class OpsInfo(C.Structure):
+    _fields_ = [("n_vec", C.c_int64), ("m1", C.c_int), ("m4", C.c_int), ("d", C.c_int),
+                ("n_legs", C.c_int), ("n_blk_left", C.c_int), ("n_blk_right", C.c_int),
+                ("n_scalar", C.c_int), ("flops_per_apply", C.c_double), ("tc_ok", C.c_int),
+                ("device_bytes", C.c_int64)]
+
+
+class SolverOpts(C.Structure):
+    _fields_ = [("max_iter", C.c_int), ("krylov_dim", C.c_int), ("tol", C.c_double),
+                ("fixed_steps", C.c_int), ("precision", C.c_int), ("refine", C.c_int),
+                ("inner_iter", C.c_int), ("outer_max", C.c_int), ("check_every", C.c_int)]
+
+
+class SolverStats(C.Structure):
+    _fields_ = [("iters", C.c_int), ("outer", C.c_int), ("n_hv_fp64", C.c_int),
+                ("n_hv_low", C.c_int), ("resid", C.c_double), ("hv_ms", C.c_double),
+                ("elapsed_ms", C.c_double)]
+
+
+# every symbol include/dmrg2d.h declares, with its ctypes signature
+SIGNATURES = {
+    "dmrg2d_build_ops": (C.c_int, [C.POINTER(Model), C.POINTER(Block), C.POINTER(Block),
+                                   C.POINTER(C.c_int32), C.POINTER(C.c_void_p), C.c_void_p]),
+    "dmrg2d_ops_get_info": (C.c_int, [C.c_void_p, C.POINTER(OpsInfo)]),
+    "dmrg2d_apply_H": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "dmrg2d_lanczos_ground": (C.c_int, [C.c_void_p, C.POINTER(SolverOpts), C.c_void_p,
+                                        C.POINTER(C.c_double), C.POINTER(SolverStats), C.c_void_p]),
+    "dmrg2d_default_solver_opts": (None, [C.POINTER(SolverOpts)]),
+    "dmrg2d_free_ops": (None, [C.c_void_p]),
+    "dmrg2d_profile_start": (C.c_int, [C.c_void_p, C.c_int]),
+    "dmrg2d_profile_stop": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
+    "dmrg2d_last_error": (C.c_char_p, []),
+    "dmrg2d_version": (C.c_char_p, []),
+}
+
+
+def lib():
+    """Load libdmrg2d.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"{_LIB_PATH} not built: run paper_0707_0159_gb300.build.build()")
+        h = C.CDLL(_LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(h, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = h
+    return _lib
+
+
+def last_error() -> str:
+    return lib().dmrg2d_last_error().decode()
+
+
+def version() -> str:
+    return lib().dmrg2d_version().decode()
+
+
+def _check(code):
+    if code != 0:
+        raise Dmrg2dError(code, last_error())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        if not torch.cuda.is_available():   # argument checks still run; device calls fail
+            return C.c_void_p(0)
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+class _BlockArgs:
+    """Keeps the numpy buffers of one block alive while the C struct points at them."""
+
+    def __init__(self, blk: dict, nq: int):
+        m = int(blk["m"])
+        self.H = np.ascontiguousarray(blk["H"], dtype=np.float64).reshape(m, m)
+        self.edge = [np.ascontiguousarray(e, dtype=np.float64).reshape(m, m) for e in blk["edge"]]
+        self.ptrs = (C.POINTER(C.c_double) * max(1, len(self.edge)))(
+            *[e.ctypes.data_as(C.POINTER(C.c_double)) for e in self.edge])
+        par = blk.get("parity")
+        self.par = None if par is None else np.ascontiguousarray(par, dtype=np.float64).reshape(m)
+        qn = blk.get("qn")
+        self.qn = None if qn is None else np.ascontiguousarray(qn, dtype=np.int32).reshape(m, nq)
+        self.c = Block(
+            m, self.H.ctypes.data_as(C.POINTER(C.c_double)), len(self.edge),
+            self.ptrs if self.edge else None,
+            None if self.par is None else self.par.ctypes.data_as(C.POINTER(C.c_double)),
+            None if self.qn is None else self.qn.ctypes.data_as(C.POINTER(C.c_int32)))
+
+
+class Ops:
+    """Owner of a dmrg2d_ops* (freed with the object)."""
+
+    def __init__(self, ptr):
+        self._p = ptr
+        inf = OpsInfo()
+        _check(lib().dmrg2d_ops_get_info(ptr, C.byref(inf)))
+        self.info = {k: getattr(inf, k) for k, _ in OpsInfo._fields_}
+
+    @property
+    def ptr(self):
+        return self._p
+
+    def free(self):
+        if self._p:
+            lib().dmrg2d_free_ops(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def build_ops(model: dict, left: dict, right: dict, target=None, stream=None) -> Ops:
+    kind = HEISENBERG if model["kind"] == "heisenberg" else HUBBARD
+    nq = 1 if kind == HEISENBERG else 2
+    mdl = Model(kind, int(model["n_legs"]), float(model.get("J_leg", 1.0)),
+                float(model.get("J_rung", 1.0)), float(model.get("t", 1.0)),
+                float(model.get("U", 0.0)), int(bool(model.get("rung_pbc", False))))
+    la, ra = _BlockArgs(left, nq), _BlockArgs(right, nq)
+    tgt = None
+    if target is not None:
+        tgt = (C.c_int32 * nq)(*[int(x) for x in target])
+    out = C.c_void_p()
+    code = lib().dmrg2d_build_ops(C.byref(mdl), C.byref(la.c), C.byref(ra.c), tgt, C.byref(out),
+                                  _stream(stream))
+    _check(code)
+    return Ops(out)
+
+
+_DTYPES = {FP64: ("float64", "float64"), FP32: ("float32", "float32"),
+           TF32: ("float32", "float32"), BF16: ("bfloat16", "float32")}
+
+
+def apply_H(ops: Ops, v, y, precision=FP64, stream=None):
+    """y = H v on the device (torch CUDA tensors, contiguous, n_vec elements)."""
+    precision = PRECISION.get(precision, precision)
+    vin, vout = _DTYPES[precision]
+    n = ops.info["n_vec"]
+    for t, dt, name in ((v, vin, "v"), (y, vout, "y")):
+        if not t.is_cuda or not t.is_contiguous() or t.numel() != n or str(t.dtype) != "torch." + dt:
+            raise ValueError(f"{name}: need a contiguous CUDA {dt} tensor of {n} elements, got "
+                             f"{t.dtype} {tuple(t.shape)} on {t.device}")
+    _check(lib().dmrg2d_apply_H(ops.ptr, C.c_void_p(v.data_ptr()), C.c_void_p(y.data_ptr()),
+                                int(precision), _stream(stream)))
+
+
+def profile_start(ops: Ops, max_launches: int):
+    _check(lib().dmrg2d_profile_start(ops.ptr, int(max_launches)))
+
+
+def profile_stop(ops: Ops):
+    """(summed dominant-kernel milliseconds, timed launches) since profile_start."""
+    ms, n = C.c_double(), C.c_int()
+    _check(lib().dmrg2d_profile_stop(ops.ptr, C.byref(ms), C.byref(n)))
+    return ms.value, n.value
+
+
+def default_solver_opts() -> dict:
+    o = SolverOpts()
+    lib().dmrg2d_default_solver_opts(C.byref(o))
+    return {k: getattr(o, k) for k, _ in SolverOpts._fields_}
+
+
+def lanczos_ground(ops: Ops, x, stream=None, **opts):
+    """Ground state; x (CUDA float64, n_vec) is the start vector and receives the result.
+
+    Returns (energy, stats dict, status code).  ENOCONV is returned, not raised.
+    """
+    o = default_solver_opts()
+    for k, v in opts.items():
+        if k not in o:
+            raise KeyError(k)
+        o[k] = PRECISION.get(v, v) if k == "precision" else v
+    so = SolverOpts(**o)
+    if not x.is_cuda or str(x.dtype) != "torch.float64" or x.numel() != ops.info["n_vec"]:
+        raise ValueError("x must be a CUDA float64 tensor of n_vec elements")
+    e = C.c_double()
+    st = SolverStats()
+    code = lib().dmrg2d_lanczos_ground(ops.ptr, C.byref(so), C.c_void_p(x.data_ptr()), C.byref(e),
+                                       C.byref(st), _stream(stream))
+    if code not in (0, -5):
+        _check(code)
+    return e.value, {k: getattr(st, k) for k, _ in SolverStats._fields_}, code

@@ -1,0 +1,174 @@
+"""GPU parity of dmrg2d_apply_H against the CPU oracle (paper Eq. (dec) and the V forms).
+
+FP64 must match to a relative Frobenius error <= 1e-12 (the product is exact
+linear algebra; only summation order differs).  FP32 (CUDA cores) <= 1e-5.
+TF32/BF16 tensor-core products are compared with the bound derived from their
+unit roundoff: TF32 <= 1e-3; BF16 <= 6e-3 (its expected error ~2e-3 is above
+1e-3, see the BF16 test).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle.superblock import Superblock  # noqa: E402
+from paper_0707_0159_gb300 import dmrg2d, synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def run(ops, v, prec):
+    x = torch.from_numpy(v).to(DEV)
+    if prec in (dmrg2d.FP32, dmrg2d.TF32):
+        x = x.float()
+    elif prec == dmrg2d.BF16:
+        x = x.bfloat16()
+    y = torch.empty(x.numel(), dtype=torch.float64 if prec == dmrg2d.FP64 else torch.float32,
+                    device=DEV)
+    dmrg2d.apply_H(ops, x, y, prec)
+    torch.cuda.synchronize()
+    return y.double().cpu().numpy(), x.double().cpu().numpy()
+
+
+SMALL = [
+    ("heisenberg", 2, 5, 7),      # ragged blocks, d = 4
+    ("hubbard", 1, 3, 1),         # block 4 is a one-state block
+    ("hubbard", 2, 70, 65),       # two row tiles per block, ragged tails, d = 16
+    ("heisenberg", 3, 130, 129),  # three tiles, d = 8
+    ("hubbard", 3, 17, 9),        # d = 64
+]
+
+
+def make(kind, n_legs, m1, m4, seed=0):
+    mdl = synth.model(kind, n_legs, J_leg=0.8, J_rung=1.1, t=1.0, U=6.0)
+    mk = synth.heisenberg_block if kind == "heisenberg" else synth.hubbard_block
+    left = mk(m1, n_legs, seed + 1) if m1 > 1 else synth.empty_block(kind)
+    right = mk(m4, n_legs, seed + 2) if m4 > 1 else synth.empty_block(kind)
+    return mdl, left, right
+
+
+@pytest.mark.parametrize("case", SMALL)
+def test_fp64_small_shapes(case):
+    mdl, left, right = make(*case)
+    sb = Superblock(mdl, left, right)
+    ops = dmrg2d.build_ops(mdl, left, right)
+    assert ops.info["n_vec"] == sb.n_vec
+    v = synth.start_vector(sb.n_vec, 7)
+    y, _ = run(ops, v, dmrg2d.FP64)
+    assert rel(y, sb.apply(v)) <= 1e-12
+
+
+@pytest.mark.parametrize("case", SMALL[:3])
+def test_fp32_small_shapes(case):
+    mdl, left, right = make(*case)
+    sb = Superblock(mdl, left, right)
+    ops = dmrg2d.build_ops(mdl, left, right)
+    v = synth.start_vector(sb.n_vec, 8)
+    y, _ = run(ops, v, dmrg2d.FP32)
+    assert rel(y, sb.apply(v)) <= 1e-5
+
+
+def test_block_structure_matches_oracle():
+    """Block positions and scalar moves counted independently from the oracle's terms."""
+    mdl, left, right = make("hubbard", 2, 6, 5)
+    sb = Superblock(mdl, left, right)
+    ops = dmrg2d.build_ops(mdl, left, right)
+    d = sb.d
+    posL = np.eye(d, dtype=bool)
+    for _, X, _ in sb.terms_l[2:]:          # edge terms (block operators)
+        posL |= X != 0
+    posR = np.eye(d, dtype=bool)
+    for _, X, _ in sb.terms_r[2:]:
+        posR |= X != 0
+    Hcol = sb.col.H
+    offL = (Hcol != 0) & ~posL & ~np.eye(d, dtype=bool)
+    offR = (Hcol != 0) & ~posR & ~np.eye(d, dtype=bool)
+    S = (sb.H_center() != 0) | np.kron(np.eye(d, dtype=bool), offL) | np.kron(offR, np.eye(d, dtype=bool))
+    i = ops.info
+    assert i["n_blk_left"] == posL.sum() and i["n_blk_right"] == posR.sum()
+    assert i["n_scalar"] == S.sum()
+    m1, m4 = 6, 5
+    f = (2 * posL.sum() * m1 * m1 * d * m4 + 2 * posR.sum() * m4 * m4 * m1 * d
+         + 2 * S.sum() * m1 * m4)
+    assert i["flops_per_apply"] == f
+
+
+def test_ladder2_m64_fp64_full():
+    mdl, left, right, _ = synth.workload_ladder2_heisenberg_m64()
+    sb = Superblock(mdl, left, right)
+    ops = dmrg2d.build_ops(mdl, left, right)
+    v = synth.start_vector(sb.n_vec, 2)
+    y, _ = run(ops, v, dmrg2d.FP64)
+    assert rel(y, sb.apply(v)) <= 1e-12
+    y2, _ = run(ops, v, dmrg2d.FP64)
+    assert np.array_equal(y, y2)  # deterministic
+
+
+def test_hermitian_on_gpu():
+    mdl, left, right = make("hubbard", 2, 33, 20)
+    ops = dmrg2d.build_ops(mdl, left, right)
+    n = ops.info["n_vec"]
+    v, w = synth.start_vector(n, 1), synth.start_vector(n, 2)
+    Hv, _ = run(ops, v, dmrg2d.FP64)
+    Hw, _ = run(ops, w, dmrg2d.FP64)
+    assert abs(w @ Hv - v @ Hw) <= 1e-12 * np.linalg.norm(Hv) * np.linalg.norm(w)
+
+
+def test_zero_and_linearity():
+    mdl, left, right = make("heisenberg", 2, 9, 11)
+    ops = dmrg2d.build_ops(mdl, left, right)
+    n = ops.info["n_vec"]
+    y0, _ = run(ops, np.zeros(n), dmrg2d.FP64)
+    assert np.all(y0 == 0.0)
+    a, b = synth.start_vector(n, 3), synth.start_vector(n, 4)
+    ya, _ = run(ops, a, dmrg2d.FP64)
+    yb, _ = run(ops, b, dmrg2d.FP64)
+    yab, _ = run(ops, 2 * a - 0.5 * b, dmrg2d.FP64)
+    assert rel(yab, 2 * ya - 0.5 * yb) <= 1e-13
+
+
+def test_bad_dtype_is_rejected():
+    mdl, left, right = make("heisenberg", 1, 4, 4)
+    ops = dmrg2d.build_ops(mdl, left, right)
+    n = ops.info["n_vec"]
+    x = torch.zeros(n, dtype=torch.float32, device=DEV)
+    y = torch.zeros(n, dtype=torch.float64, device=DEV)
+    with pytest.raises(ValueError):
+        dmrg2d.apply_H(ops, x, y, dmrg2d.FP64)
+
+
+# ---- full-size 3-leg Hubbard superblock (m = 256, d = 64, V 16384 x 16384) -------------------
+
+@pytest.fixture(scope="module")
+def ladder3_full():
+    mdl, left, right, _ = synth.workload_ladder3_hubbard_m256()
+    ops = dmrg2d.build_ops(mdl, left, right)
+    sb = Superblock(mdl, left, right)
+    v = synth.start_vector(sb.n_vec, 12)
+    rng = np.random.default_rng(5)
+    # sampled outputs: random entries plus the first and last rows/columns of V
+    idx = np.concatenate([rng.integers(0, sb.n_vec, 200), [0, 1, 255, 256, sb.n_vec - 1]])
+    return ops, sb, v, idx
+
+
+def test_ladder3_full_fp64_sampled(ladder3_full):
+    ops, sb, v, idx = ladder3_full
+    y, _ = run(ops, v, dmrg2d.FP64)
+    ref = sb.apply_at(v, idx)
+    assert rel(y[idx], ref) <= 1e-12
+
+
+@pytest.mark.parametrize("prec,tol", [(dmrg2d.TF32, 1e-3), (dmrg2d.BF16, 6e-3)])
+def test_ladder3_full_tensor_core_sampled(ladder3_full, prec, tol):
+    ops, sb, v, idx = ladder3_full
+    if not ops.info["tc_ok"]:
+        pytest.skip("tensor-core path not available for these shapes")
+    y, vq = run(ops, v, prec)
+    ref = sb.apply_at(v, idx)
+    assert rel(y[idx], ref) <= tol

@@ -1,0 +1,106 @@
+"""GPU ground-state solvers against the oracle and brute-force ED."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import lattice_ed  # noqa: E402
+from oracle.columns import HubbardColumn, SpinColumn  # noqa: E402
+from oracle.solvers import lanczos_ground as oracle_lanczos  # noqa: E402
+from oracle.superblock import Superblock  # noqa: E402
+from paper_0707_0159_gb300 import dmrg2d, synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def spin_column_block(n):
+    col = SpinColumn(n, 1.0)
+    edge = []
+    for y in range(n):
+        edge += [col.Sz[y], col.Sp[y]]
+    return {"m": col.d, "H": col.H, "edge": edge, "parity": None, "qn": None}
+
+
+def hubbard_column_block(n, t=1.0, U=8.0):
+    col = HubbardColumn(n, t, U)
+    edge = []
+    for y in range(n):
+        edge += [col.cdag[y][0], col.cdag[y][1]]
+    return {"m": col.d, "H": col.H, "edge": edge, "parity": col.parity, "qn": None}
+
+
+def gpu_ground(ops, v0, **kw):
+    x = torch.from_numpy(np.asarray(v0, dtype=np.float64)).to(DEV)
+    e, st, code = dmrg2d.lanczos_ground(ops, x, **kw)
+    return e, x.cpu().numpy(), st, code
+
+
+def test_ladder2_m64_200_steps_against_oracle():
+    mdl, left, right, _ = synth.workload_ladder2_heisenberg_m64()
+    ops = dmrg2d.build_ops(mdl, left, right)
+    sb = Superblock(mdl, left, right)
+    v0 = synth.start_vector(sb.n_vec, 2)
+    e, x, st, code = gpu_ground(ops, v0, max_iter=200, krylov_dim=200, fixed_steps=1)
+    assert code == 0 and st["iters"] == 200 and st["n_hv_fp64"] == 200
+    e_ref, x_ref, _ = oracle_lanczos(sb.apply, v0, max_iter=200, fixed_steps=True)
+    assert abs(e - e_ref) <= 1e-10 * abs(e_ref)
+    r = sb.apply(x) - e * x                       # residual with the oracle's H
+    assert np.linalg.norm(r) <= 1e-6 * abs(e)
+    assert abs(abs(x @ x_ref) - 1.0) <= 1e-8
+
+
+def test_untruncated_ladder_2x4_equals_ed():
+    mdl = synth.model("heisenberg", 2)
+    blk = spin_column_block(2)
+    ops = dmrg2d.build_ops(mdl, blk, blk)
+    e, _, st, code = gpu_ground(ops, synth.start_vector(ops.info["n_vec"], 1), max_iter=200,
+                                krylov_dim=200, tol=1e-13)
+    e_ed = lattice_ed.heisenberg_spectrum(2, 4)[0]
+    assert abs(e - e_ed) <= 1e-10 * abs(e_ed)
+
+
+def test_untruncated_hubbard_2x3_equals_ed():
+    mdl = synth.model("hubbard", 2, t=1.0, U=8.0)
+    col = hubbard_column_block(2)
+    ops = dmrg2d.build_ops(mdl, col, synth.empty_block("hubbard"))
+    e, _, st, code = gpu_ground(ops, synth.start_vector(ops.info["n_vec"], 1), max_iter=400,
+                                krylov_dim=400, tol=1e-13)
+    e_ed = lattice_ed.hubbard_ground(2, 3, 1.0, 8.0)
+    assert abs(e - e_ed) <= 1e-10 * abs(e_ed)
+
+
+def test_lanczos_deterministic_and_restart():
+    mdl, left, right, _ = synth.workload_ladder2_heisenberg_m64()
+    ops = dmrg2d.build_ops(mdl, left, right)
+    v0 = synth.start_vector(ops.info["n_vec"], 4)
+    e1, x1, _, c1 = gpu_ground(ops, v0, max_iter=300, krylov_dim=300, tol=1e-11)
+    e2, x2, _, c2 = gpu_ground(ops, v0, max_iter=300, krylov_dim=300, tol=1e-11)
+    assert c1 == 0 and e1 == e2 and np.array_equal(x1, x2)
+    # a small basis with explicit restarts reaches the same eigenvalue
+    e3, _, st3, c3 = gpu_ground(ops, v0, max_iter=2000, krylov_dim=40, tol=1e-11)
+    assert c3 == 0 and abs(e3 - e1) <= 1e-9 * abs(e1)
+
+
+def test_enoconv_is_reported():
+    mdl, left, right, _ = synth.workload_ladder2_heisenberg_m64()
+    ops = dmrg2d.build_ops(mdl, left, right)
+    e, _, st, code = gpu_ground(ops, synth.start_vector(ops.info["n_vec"], 4), max_iter=5,
+                                krylov_dim=5, tol=1e-14)
+    assert code == -5 and np.isfinite(e) and st["iters"] == 5
+
+
+@pytest.mark.parametrize("prec", [dmrg2d.FP32, dmrg2d.TF32, dmrg2d.BF16])
+def test_mixed_precision_reaches_fp64_energy(prec):
+    mdl, left, right, _ = synth.workload_ladder3_hubbard_m256(m=128)
+    ops = dmrg2d.build_ops(mdl, left, right)
+    if prec != dmrg2d.FP32 and not ops.info["tc_ok"]:
+        pytest.skip("tensor-core path not available")
+    v0 = synth.start_vector(ops.info["n_vec"], 3)
+    e64, x64, st64, c64 = gpu_ground(ops, v0, max_iter=400, krylov_dim=120, tol=1e-9)
+    assert c64 == 0
+    e, x, st, code = gpu_ground(ops, v0, precision=prec, refine=1, tol=1e-7, inner_iter=40,
+                                outer_max=12)
+    assert code == 0, st
+    assert abs(e - e64) <= 1e-8 * abs(e64), (e, e64, st)
+    assert st["n_hv_fp64"] < st64["n_hv_fp64"]
