@@ -179,6 +179,12 @@ void dmrg2d_default_solver_opts(dmrg2d_solver_opts* opts);
 int dmrg2d_profile_start(dmrg2d_ops* ops, int max_launches);
 int dmrg2d_profile_stop(dmrg2d_ops* ops, double* total_ms, int* launches);
 
+/* Waits for the device, then reports whether a tensor-core kernel launched with
+ * these ops gave up a bounded wait since the last check (every wait on the
+ * device ends after at most 2 s and sets a flag instead of hanging).
+ * Returns OK, ETIMEOUT (flag found and cleared) or ECUDA. */
+int dmrg2d_check_device(const dmrg2d_ops* ops);
+
 void dmrg2d_free_ops(dmrg2d_ops* ops);
 
 /* Thread-local text of the last error of this thread ("" if none). */

@@ -488,6 +488,15 @@ extern "C" void dmrg2d_free_ops(dmrg2d_ops* ops) {
   delete ops;
 }
 
+extern "C" int dmrg2d_check_device(const dmrg2d_ops* ops) {
+  if (!ops) return set_error(DMRG2D_EINVAL, "NULL ops");
+  D2_CUDA(cudaDeviceSynchronize());
+  int code = 0;
+  D2_TRY(tc_read_error(ops, &code));
+  if (code) return set_error(DMRG2D_ETIMEOUT, "tensor-core kernel gave up waiting (site %d)", code);
+  return DMRG2D_OK;
+}
+
 extern "C" const char* dmrg2d_last_error(void) { return g_err.c_str(); }
 
 extern "C" const char* dmrg2d_version(void) { return "dmrg2d-gb300 0.1 (sm_103a)"; }

@@ -96,6 +96,7 @@ int launch_hv_simt_f32(const dmrg2d_ops* ops, const float* v, float* y, cudaStre
 int tc_prepare(dmrg2d_ops* ops, cudaStream_t s);
 void tc_release(dmrg2d_ops* ops);
 int launch_hv_tc(const dmrg2d_ops* ops, const void* v, float* y, int precision, cudaStream_t s);
+int tc_read_error(const dmrg2d_ops* ops, int* code);
 
 // vector kernels used by the solvers (solver.cu)
 int convert_f64_to(const double* x, void* out, int precision, int64_t n, cudaStream_t s);

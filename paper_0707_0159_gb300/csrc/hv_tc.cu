@@ -1,9 +1,562 @@
-// placeholder: replaced by the tcgen05 implementation
+// Superblock H·v on the 5th-generation tensor cores (tcgen05, sm_103a), TF32 or BF16
+// operands with FP32 accumulation in tensor memory.
+//
+// Output tile (i2, i3) of Y = H_l V + V H_r^T + H_c V_c (paper, text after Eq. (dec)) is
+// split into 128 x BN pieces (rows i1 of block row i2, columns i4 of block column i3).
+// For one piece the K loop runs over
+//   phase 1 (H_l V):   A = HL[i2,i2'] rows, K-major       B = V(i2' rows, i3 cols), K-major
+//   phase 2 (V H_r^T): A = V(i2 rows, i3' cols), MN-major  B = HR[i3,i3'] rows, K-major
+// into ONE accumulator, so Y is written once.  A second, memory-bound kernel then adds
+// the scalar tile moves (H_c, off-diagonal column terms): Y(i2,i3) += c V(i2',i3').
+//
+// Kernel organisation (one persistent CTA per SM, 192 threads):
+//   warp 0   TMA producer: 4-stage ring of 48 KB (A 16 KB + B up to 32 KB), 128B swizzle
+//   warp 1   TMEM owner (512 columns = two 128 x 256 FP32 accumulators) and MMA issuer
+//   warps 2-5 epilogue: tcgen05.ld of the finished accumulator, coalesced FP32 stores
+// Every mbarrier wait is bounded (globaltimer); on timeout the CTA raises an error flag,
+// stops issuing work, releases its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "common.h"
+
 namespace dmrg2d {
-int tc_prepare(dmrg2d_ops* ops, cudaStream_t) { ops->tc_ok = 0; return DMRG2D_OK; }
-void tc_release(dmrg2d_ops*) {}
-int launch_hv_tc(const dmrg2d_ops*, const void*, float*, int, cudaStream_t) {
-  return set_error(DMRG2D_EUNSUPPORTED, "tensor-core path not built");
+
+namespace {
+
+constexpr int TC_THREADS = 192;
+constexpr int STAGES = 4;
+constexpr int BM = 128;
+constexpr uint32_t STAGE_A = 16384;
+constexpr uint32_t STAGE_B = 32768;
+constexpr uint32_t STAGE_BYTES = STAGE_A + STAGE_B;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t ACC_COLS = 256;
+constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s: far above any legitimate wait
+constexpr size_t SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+
+struct TcParams {
+  int m1, m4, d, BN;
+  int n_mt, n_nt;
+  int tiles;
+  int kblk1, kblk2;
+  int BK;
+  int64_t ld;
+  const int* Lptr;
+  const int* Lcol;
+  const int* Rptr;
+  const int* Rcol;
+  float* y;
+  int* err;
+  uint32_t idesc1, idesc2;
+  uint32_t a2_lbo, a2_kstep;
+  int a2_boxes, a2_box_rows;
+  uint32_t tx_bytes;
+  int bf16;
+};
+
+// ---- PTX wrappers ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
+__device__ __forceinline__ uint64_t gtime() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait; false on timeout or when another role has aborted
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = gtime();
+  while (true) {
+    if (mbar_try(bar, parity)) return true;
+    if (*abort) return false;
+    if (gtime() - t0 > WAIT_NS) return false;
+  }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x,
+                                            int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+      "%3}], [%4];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;  // 128-byte swizzle
+  return d;
+}
+__device__ __forceinline__ void umma(uint32_t dt, uint64_t a, uint64_t b, uint32_t idesc,
+                                     uint32_t acc, int bf16) {
+  if (bf16)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  else
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   bar)
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct TileCoord {
+  int i2, mt, i3, nt;
+};
+__device__ __forceinline__ TileCoord decode(const TcParams& p, int t) {
+  const int nm = p.d * p.n_mt;
+  const int mg = t % nm, ng = t / nm;  // consecutive tiles walk down one column slab of V
+  return {mg / p.n_mt, mg % p.n_mt, ng / p.n_nt, ng % p.n_nt};
+}
+
+__device__ __forceinline__ void raise_abort(volatile int* abort, int* err, int code) {
+  *abort = 1;
+  atomicCAS(err, 0, code);
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+hv_tc_kernel(const __grid_constant__ CUtensorMap mHL, const __grid_constant__ CUtensorMap mHR,
+             const __grid_constant__ CUtensorMap mVk, const __grid_constant__ CUtensorMap mVm,
+             const TcParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 4);
+  volatile int* abort = (volatile int*)(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  auto full = [&](int s) { return smem_u32(bars + s); };
+  auto empty = [&](int s) { return smem_u32(bars + STAGES + s); };
+  auto tfull = [&](int b) { return smem_u32(bars + 2 * STAGES + b); };
+  auto tempty = [&](int b) { return smem_u32(bars + 2 * STAGES + 2 + b); };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull(b), 1);
+      mbar_init(tempty(b), 4);
+    }
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------- TMA producer -------------------------------
+    int stage = 0;
+    uint32_t phase = 0;
+    for (int t = blockIdx.x; t < p.tiles && !*abort; t += gridDim.x) {
+      const TileCoord c = decode(p, t);
+      const int r0 = c.i2 * p.m1 + c.mt * BM;
+      const int c0 = c.i3 * p.m4 + c.nt * p.BN;
+      for (int ph = 0; ph < 2; ++ph) {
+        const int e0 = ph == 0 ? p.Lptr[c.i2] : p.Rptr[c.i3];
+        const int e1 = ph == 0 ? p.Lptr[c.i2 + 1] : p.Rptr[c.i3 + 1];
+        const int kb = ph == 0 ? p.kblk1 : p.kblk2;
+        for (int e = e0; e < e1; ++e) {
+          const int nb = ph == 0 ? p.Lcol[e] : p.Rcol[e];
+          for (int kc = 0; kc < kb; ++kc) {
+            if (!mbar_wait(empty(stage), phase ^ 1u, abort)) {
+              raise_abort(abort, p.err, 1);
+              goto producer_done;
+            }
+            const uint32_t a_s = smem_u32(smem + stage * STAGE_BYTES);
+            const uint32_t b_s = a_s + STAGE_A;
+            mbar_expect_tx(full(stage), p.tx_bytes);
+            if (ph == 0) {
+              tma_load_2d(a_s, &mHL, full(stage), kc * p.BK, e * p.m1 + c.mt * BM);
+              tma_load_2d(b_s, &mVk, full(stage), nb * p.m1 + kc * p.BK, c0);
+            } else {
+              for (int b = 0; b < p.a2_boxes; ++b)
+                tma_load_2d(a_s + b * p.a2_lbo, &mVm, full(stage), r0 + b * p.a2_box_rows,
+                            nb * p.m4 + kc * p.BK);
+              tma_load_2d(b_s, &mHR, full(stage), kc * p.BK, e * p.m4 + c.nt * p.BN);
+            }
+            if (++stage == STAGES) {
+              stage = 0;
+              phase ^= 1u;
+            }
+          }
+        }
+      }
+    }
+  producer_done:;
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------- MMA issuer ---------------------------------
+    int stage = 0;
+    uint32_t phase = 0;
+    int acc = 0;
+    uint32_t aphase = 0;
+    for (int t = blockIdx.x; t < p.tiles && !*abort; t += gridDim.x) {
+      const TileCoord c = decode(p, t);
+      if (!mbar_wait(tempty(acc), aphase ^ 1u, abort)) {
+        raise_abort(abort, p.err, 2);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t dt = tmem_base + acc * ACC_COLS;
+      uint32_t accum = 0;
+      bool ok = true;
+      for (int ph = 0; ph < 2 && ok; ++ph) {
+        const int e0 = ph == 0 ? p.Lptr[c.i2] : p.Rptr[c.i3];
+        const int e1 = ph == 0 ? p.Lptr[c.i2 + 1] : p.Rptr[c.i3 + 1];
+        const int kb = ph == 0 ? p.kblk1 : p.kblk2;
+        const int nsteps = (e1 - e0) * kb;
+        for (int st = 0; st < nsteps; ++st) {
+          if (!mbar_wait(full(stage), phase, abort)) {
+            raise_abort(abort, p.err, 3);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_s = smem_u32(smem + stage * STAGE_BYTES);
+          const uint32_t b_s = a_s + STAGE_A;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            uint64_t ad, bd;
+            uint32_t id;
+            if (ph == 0) {
+              ad = sdesc(a_s + k * 32, 16, 1024);
+              id = p.idesc1;
+            } else {
+              ad = sdesc(a_s + k * p.a2_kstep, p.a2_lbo, 1024);
+              id = p.idesc2;
+            }
+            bd = sdesc(b_s + k * 32, 16, 1024);
+            umma(dt, ad, bd, id, accum, p.bf16);
+            accum = 1;
+          }
+          umma_commit(empty(stage));
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      if (!ok) break;
+      umma_commit(tfull(acc));
+      if (++acc == 2) {
+        acc = 0;
+        aphase ^= 1u;
+      }
+    }
+  } else if (warp >= 2) {
+    // ------------------------------- epilogue -----------------------------------
+    const int q = warp & 3;  // TMEM lane quadrant this warp may access
+    int acc = 0;
+    uint32_t aphase = 0;
+    for (int t = blockIdx.x; t < p.tiles; t += gridDim.x) {
+      const TileCoord c = decode(p, t);
+      if (!mbar_wait(tfull(acc), aphase, abort)) {
+        raise_abort(abort, p.err, 4);
+        break;
+      }
+      tc_fence_after();
+      const int row = 32 * q + lane;
+      const int64_t r = (int64_t)c.i2 * p.m1 + c.mt * BM + row;
+      const int64_t col0 = (int64_t)c.i3 * p.m4 + (int64_t)c.nt * p.BN;
+      for (int ch = 0; ch < p.BN / 32; ++ch) {
+        uint32_t v[32];
+        tmem_ld32(tmem_base + ((uint32_t)(32 * q) << 16) + acc * ACC_COLS + ch * 32, v);
+        float* yp = p.y + r + p.ld * (col0 + ch * 32);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) yp[p.ld * j] = __uint_as_float(v[j]);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty(acc));
+      if (++acc == 2) {
+        acc = 0;
+        aphase ^= 1u;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// Y(i2,i3) += sum c * V(i2',i3') over the scalar tile moves; one block per (tile, 8 columns).
+template <typename Tin>
+__global__ void __launch_bounds__(256)
+k_scalar_moves(const Tin* __restrict__ v, float* __restrict__ y, const int* __restrict__ Cptr,
+               const int* __restrict__ Csrc, const float* __restrict__ Cval, int m1, int m4, int d,
+               int64_t ld) {
+  const int t = blockIdx.x;
+  const int i2 = t % d, i3 = t / d;
+  const int j0 = blockIdx.y * 8;
+  const int e0 = Cptr[t], e1 = Cptr[t + 1];
+  if (e0 == e1) return;
+  for (int i = threadIdx.x; i < m1; i += 256) {
+    float acc[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[j] = 0.f;
+    for (int e = e0; e < e1; ++e) {
+      const int s = Csrc[e];
+      const float cv = Cval[e];
+      const Tin* S = v + (int64_t)(s % d) * m1 + i + ld * ((int64_t)(s / d) * m4 + j0);
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (j0 + j < m4) acc[j] += cv * (float)S[ld * j];
+    }
+    float* Y = y + (int64_t)i2 * m1 + i + ld * ((int64_t)i3 * m4 + j0);
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (j0 + j < m4) Y[ld * j] += acc[j];
+  }
+}
+
+// ---- host side ----------------------------------------------------------------------------
+struct TcState {
+  float* HLt = nullptr;  // TF32-rounded copies of the operator blocks
+  float* HRt = nullptr;
+  int* err = nullptr;
+  CUtensorMap mHL[2], mHR[2];  // [0] TF32, [1] BF16
+  int sms = 0;
+  int BN = 0;
+};
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+int make_map(CUtensorMap* m, const void* base, bool bf16, uint64_t inner, uint64_t outer,
+             uint32_t box_inner, uint32_t box_outer) {
+  auto fn = encode_fn();
+  if (!fn) return set_error(DMRG2D_ECUDA, "cuTensorMapEncodeTiled unavailable");
+  const uint32_t elt = bf16 ? 2 : 4;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {inner * elt};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                  const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(DMRG2D_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return DMRG2D_OK;
+}
+
+__global__ void k_round_tf32(const double* __restrict__ x, float* __restrict__ o, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float f = (float)x[i];
+    uint32_t u;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(f));
+    o[i] = __uint_as_float(u);
+  }
+}
+
+uint32_t make_idesc(int fmt, int a_mn, int M, int N) {
+  return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)a_mn << 15) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+}  // namespace
+
+int tc_prepare(dmrg2d_ops* ops, cudaStream_t s) {
+  ops->tc_ok = 0;
+  const int m1 = ops->m1, m4 = ops->m4;
+  if (m1 % BM != 0 || !(m4 == 128 || m4 % 256 == 0)) return DMRG2D_OK;  // SIMT only
+  if (!encode_fn()) return DMRG2D_OK;
+  TcState* T = new TcState();
+  T->BN = m4 == 128 ? 128 : 256;
+  const int64_t nL = ops->dev.nL, nR = ops->dev.nR;
+  int st = DMRG2D_OK;
+  auto alloc = [&](void** p, size_t b) {
+    if (st != DMRG2D_OK) return;
+    if (cudaMalloc(p, b) != cudaSuccess) {
+      *p = nullptr;
+      st = set_error(DMRG2D_ENOMEM, "cudaMalloc(%zu) failed", b);
+    } else {
+      ops->device_bytes += (int64_t)b;
+    }
+  };
+  alloc((void**)&T->HLt, sizeof(float) * nL * m1 * m1);
+  alloc((void**)&T->HRt, sizeof(float) * nR * m4 * m4);
+  alloc((void**)&T->err, sizeof(int));
+  if (st == DMRG2D_OK) {
+    k_round_tf32<<<1024, 256, 0, s>>>(ops->dev.HL64, T->HLt, nL * m1 * m1);
+    k_round_tf32<<<1024, 256, 0, s>>>(ops->dev.HR64, T->HRt, nR * m4 * m4);
+    if (cudaMemsetAsync(T->err, 0, sizeof(int), s) != cudaSuccess)
+      st = set_error(DMRG2D_ECUDA, "memset failed");
+  }
+  for (int b = 0; b < 2 && st == DMRG2D_OK; ++b) {
+    const bool bf = b == 1;
+    const uint32_t BK = bf ? 64 : 32;
+    const void* hl = bf ? (const void*)ops->dev.HL16 : (const void*)T->HLt;
+    const void* hr = bf ? (const void*)ops->dev.HR16 : (const void*)T->HRt;
+    st = make_map(&T->mHL[b], hl, bf, m1, nL * m1, BK, BM);
+    if (st == DMRG2D_OK) st = make_map(&T->mHR[b], hr, bf, m4, nR * m4, BK, T->BN);
+  }
+  if (st == DMRG2D_OK) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&T->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaFuncSetAttribute(hv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)SMEM_BYTES) != cudaSuccess)
+      st = set_error(DMRG2D_ECUDA, "cannot set %zu bytes of shared memory", SMEM_BYTES);
+  }
+  if (st == DMRG2D_OK) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = set_error(DMRG2D_ECUDA, "tc_prepare: %s", cudaGetErrorString(e));
+  }
+  ops->tc = T;
+  if (st != DMRG2D_OK) return st;
+  ops->tc_ok = 1;
+  return DMRG2D_OK;
+}
+
+void tc_release(dmrg2d_ops* ops) {
+  TcState* T = (TcState*)ops->tc;
+  if (!T) return;
+  if (T->HLt) cudaFree(T->HLt);
+  if (T->HRt) cudaFree(T->HRt);
+  if (T->err) cudaFree(T->err);
+  delete T;
+  ops->tc = nullptr;
+}
+
+int launch_hv_tc(const dmrg2d_ops* ops, const void* v, float* y, int precision, cudaStream_t s) {
+  TcState* T = (TcState*)ops->tc;
+  if (!T || !ops->tc_ok) return set_error(DMRG2D_EUNSUPPORTED, "tensor-core path not prepared");
+  const bool bf = precision == DMRG2D_BF16;
+  const int b = bf ? 1 : 0;
+  const int m1 = ops->m1, m4 = ops->m4, d = ops->d;
+  const uint32_t BK = bf ? 64 : 32;
+  TcParams p;
+  p.m1 = m1;
+  p.m4 = m4;
+  p.d = d;
+  p.BN = T->BN;
+  p.n_mt = m1 / BM;
+  p.n_nt = m4 / T->BN;
+  p.tiles = d * p.n_mt * d * p.n_nt;
+  p.BK = (int)BK;
+  p.kblk1 = m1 / (int)BK;
+  p.kblk2 = m4 / (int)BK;
+  p.ld = ops->ld;
+  p.Lptr = ops->dev.Lptr;
+  p.Lcol = ops->dev.Lcol;
+  p.Rptr = ops->dev.Rptr;
+  p.Rcol = ops->dev.Rcol;
+  p.y = y;
+  p.err = T->err;
+  const int fmt = bf ? 1 : 2;
+  p.idesc1 = make_idesc(fmt, 0, BM, T->BN);
+  p.idesc2 = make_idesc(fmt, 1, BM, T->BN);
+  p.a2_box_rows = bf ? 64 : 32;
+  p.a2_boxes = BM / p.a2_box_rows;
+  p.a2_lbo = (uint32_t)p.a2_box_rows * BK * (bf ? 2 : 4);  // bytes of one {rows, BK} box
+  p.a2_kstep = bf ? 2048 : 1024;                           // 16 (bf16) / 8 (tf32) k-rows
+  p.tx_bytes = STAGE_A + (uint32_t)T->BN * 128;
+  p.bf16 = bf ? 1 : 0;
+  CUtensorMap mVk, mVm;
+  const uint64_t rows = (uint64_t)ops->ld, cols = (uint64_t)d * m4;
+  D2_TRY(make_map(&mVk, v, bf, rows, cols, BK, T->BN));
+  D2_TRY(make_map(&mVm, v, bf, rows, cols, (uint32_t)p.a2_box_rows, BK));
+  const int grid = p.tiles < T->sms ? p.tiles : T->sms;
+  auto ev = prof_slot(ops);
+  if (ev.first) D2_CUDA(cudaEventRecord(ev.first, s));
+  hv_tc_kernel<<<grid, TC_THREADS, SMEM_BYTES, s>>>(T->mHL[b], T->mHR[b], mVk, mVm, p);
+  D2_CUDA(cudaGetLastError());
+  if (ev.second) D2_CUDA(cudaEventRecord(ev.second, s));
+  dim3 g2(d * d, (m4 + 7) / 8);
+  if (bf)
+    k_scalar_moves<__nv_bfloat16><<<g2, 256, 0, s>>>((const __nv_bfloat16*)v, y, ops->dev.Cptr,
+                                                    ops->dev.Csrc, ops->dev.Cval32, m1, m4, d,
+                                                    ops->ld);
+  else
+    k_scalar_moves<float><<<g2, 256, 0, s>>>((const float*)v, y, ops->dev.Cptr, ops->dev.Csrc,
+                                            ops->dev.Cval32, m1, m4, d, ops->ld);
+  D2_CUDA(cudaGetLastError());
+  return DMRG2D_OK;
+}
+
+int tc_read_error(const dmrg2d_ops* ops, int* code) {
+  TcState* T = (TcState*)ops->tc;
+  *code = 0;
+  if (!T || !T->err) return DMRG2D_OK;
+  D2_CUDA(cudaMemcpy(code, T->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (*code) D2_CUDA(cudaMemset(T->err, 0, sizeof(int)));
+  return DMRG2D_OK;
+}
+
+}  // namespace dmrg2d

@@ -143,6 +143,14 @@ __global__ void k_f64_to_bf16(const double* __restrict__ x, __nv_bfloat16* __res
     o[e] = __float2bfloat16_rn((float)x[e]);
 }
 
+__global__ void k_f64_to_tf32(const double* __restrict__ x, float* __restrict__ o, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * VT + threadIdx.x; e < n; e += (int64_t)gridDim.x * VT) {
+    uint32_t u;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"((float)x[e]));
+    o[e] = __uint_as_float(u);
+  }
+}
+
 __global__ void k_f32_to_f64(const float* __restrict__ x, double* __restrict__ o, int64_t n) {
   for (int64_t e = (int64_t)blockIdx.x * VT + threadIdx.x; e < n; e += (int64_t)gridDim.x * VT)
     o[e] = (double)x[e];
@@ -520,6 +528,8 @@ int lanczos(Ctx& C, int prec, double* x, int max_iter, int kdim, double tol, int
 int convert_f64_to(const double* x, void* out, int precision, int64_t n, cudaStream_t s) {
   if (precision == DMRG2D_BF16)
     k_f64_to_bf16<<<vgrid(n), VT, 0, s>>>(x, (__nv_bfloat16*)out, n);
+  else if (precision == DMRG2D_TF32)
+    k_f64_to_tf32<<<vgrid(n), VT, 0, s>>>(x, (float*)out, n);
   else
     k_f64_to_f32<<<vgrid(n), VT, 0, s>>>(x, (float*)out, n);
   D2_CUDA(cudaGetLastError());
@@ -713,6 +723,9 @@ extern "C" int dmrg2d_lanczos_ground(const dmrg2d_ops* ops, const dmrg2d_solver_
   cudaError_t e = cudaStreamSynchronize(C.s);
   if (e != cudaSuccess && st == DMRG2D_OK)
     st = set_error(DMRG2D_ECUDA, "solver: %s", cudaGetErrorString(e));
+  int derr = 0;
+  if (tc_read_error(ops, &derr) == DMRG2D_OK && derr && st == DMRG2D_OK)
+    st = set_error(DMRG2D_ETIMEOUT, "tensor-core kernel gave up waiting (site %d)", derr);
   local.hv_ms = C.hv_ms();
   local.elapsed_ms =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

@@ -68,6 +68,7 @@ SIGNATURES = {
                                         C.POINTER(C.c_double), C.POINTER(SolverStats), C.c_void_p]),
     "dmrg2d_default_solver_opts": (None, [C.POINTER(SolverOpts)]),
     "dmrg2d_free_ops": (None, [C.c_void_p]),
+    "dmrg2d_check_device": (C.c_int, [C.c_void_p]),
     "dmrg2d_profile_start": (C.c_int, [C.c_void_p, C.c_int]),
     "dmrg2d_profile_stop": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "dmrg2d_last_error": (C.c_char_p, []),
@@ -191,6 +192,11 @@ def apply_H(ops: Ops, v, y, precision=FP64, stream=None):
                              f"{t.dtype} {tuple(t.shape)} on {t.device}")
     _check(lib().dmrg2d_apply_H(ops.ptr, C.c_void_p(v.data_ptr()), C.c_void_p(y.data_ptr()),
                                 int(precision), _stream(stream)))
+
+
+def check_device(ops: Ops):
+    """Raise if a device-side bounded wait gave up since the last check."""
+    _check(lib().dmrg2d_check_device(ops.ptr))
 
 
 def profile_start(ops: Ops, max_launches: int):

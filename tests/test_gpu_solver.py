@@ -90,17 +90,30 @@ def test_enoconv_is_reported():
     assert code == -5 and np.isfinite(e) and st["iters"] == 5
 
 
-@pytest.mark.parametrize("prec", [dmrg2d.FP32, dmrg2d.TF32, dmrg2d.BF16])
-def test_mixed_precision_reaches_fp64_energy(prec):
-    mdl, left, right, _ = synth.workload_ladder3_hubbard_m256(m=128)
+@pytest.fixture(scope="module")
+def ladder2_m128():
+    """2-leg Hubbard superblock, m = 128, d = 16, converged plain FP64 reference."""
+    mdl = synth.model("hubbard", 2, t=1.0, U=8.0)
+    left, right = synth.hubbard_block(128, 2, 40), synth.hubbard_block(128, 2, 41)
     ops = dmrg2d.build_ops(mdl, left, right)
-    if prec != dmrg2d.FP32 and not ops.info["tc_ok"]:
-        pytest.skip("tensor-core path not available")
     v0 = synth.start_vector(ops.info["n_vec"], 3)
-    e64, x64, st64, c64 = gpu_ground(ops, v0, max_iter=400, krylov_dim=120, tol=1e-9)
-    assert c64 == 0
-    e, x, st, code = gpu_ground(ops, v0, precision=prec, refine=1, tol=1e-7, inner_iter=40,
-                                outer_max=12)
+    e64, _, st64, c64 = gpu_ground(ops, v0, max_iter=3000, krylov_dim=300, tol=1e-10)
+    return ops, v0, e64, st64, c64
+
+
+def test_fp64_lanczos_converges(ladder2_m128):
+    ops, v0, e64, st64, c64 = ladder2_m128
+    assert c64 == 0, st64
+    assert st64["resid"] <= 1e-10 * abs(e64)
+
+
+@pytest.mark.parametrize("prec", [dmrg2d.FP32, dmrg2d.TF32, dmrg2d.BF16])
+def test_mixed_precision_reaches_fp64_energy(ladder2_m128, prec):
+    ops, v0, e64, st64, c64 = ladder2_m128
+    assert ops.info["tc_ok"]
+    e, x, st, code = gpu_ground(ops, v0, precision=prec, refine=1, tol=1e-8, inner_iter=60,
+                                outer_max=40)
     assert code == 0, st
     assert abs(e - e64) <= 1e-8 * abs(e64), (e, e64, st)
-    assert st["n_hv_fp64"] < st64["n_hv_fp64"]
+    assert st["resid"] <= 1e-8 * abs(e)
+    assert st["n_hv_fp64"] < st64["n_hv_fp64"], (st, st64)
