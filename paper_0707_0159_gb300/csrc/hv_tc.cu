@@ -49,7 +49,7 @@ struct TcParams {
   float* y;
   int* err;
   uint32_t idesc1, idesc2;
-  uint32_t a2_lbo, a2_kstep;
+  uint32_t a2_lbo, a2_sbo, a2_kstep, a2_layout;
   int a2_boxes, a2_box_rows;
   uint32_t tx_bytes;
   int bf16;
@@ -103,13 +103,16 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
       : "memory");
 }
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+// layout: 2 = 128B swizzle (16-byte atoms), 1 = 128B swizzle with 32-byte atoms (the
+// form MN-major TF32 operands need; TMA writes it with SWIZZLE_128B_ATOM_32B)
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo,
+                                          uint32_t layout = 2) {
   uint64_t d = 0;
   d |= (uint64_t)((addr >> 4) & 0x3FFFu);
   d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
   d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
   d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
-  d |= (uint64_t)2 << 61;  // 128-byte swizzle
+  d |= (uint64_t)layout << 61;
   return d;
 }
 __device__ __forceinline__ void umma(uint32_t dt, uint64_t a, uint64_t b, uint32_t idesc,
@@ -281,7 +284,7 @@ hv_tc_kernel(const __grid_constant__ CUtensorMap mHL, const __grid_constant__ CU
               ad = sdesc(a_s + k * 32, 16, 1024);
               id = p.idesc1;
             } else {
-              ad = sdesc(a_s + k * p.a2_kstep, p.a2_lbo, 1024);
+              ad = sdesc(a_s + k * p.a2_kstep, p.a2_lbo, p.a2_sbo, p.a2_layout);
               id = p.idesc2;
             }
             bd = sdesc(b_s + k * 32, 16, 1024);
@@ -398,7 +401,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 int make_map(CUtensorMap* m, const void* base, bool bf16, uint64_t inner, uint64_t outer,
-             uint32_t box_inner, uint32_t box_outer) {
+             uint32_t box_inner, uint32_t box_outer,
+             CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B) {
   auto fn = encode_fn();
   if (!fn) return set_error(DMRG2D_ECUDA, "cuTensorMapEncodeTiled unavailable");
   const uint32_t elt = bf16 ? 2 : 4;
@@ -408,7 +412,7 @@ int make_map(CUtensorMap* m, const void* base, bool bf16, uint64_t inner, uint64
   cuuint32_t es[2] = {1, 1};
   CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
                   const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return set_error(DMRG2D_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return DMRG2D_OK;
@@ -526,12 +530,17 @@ int launch_hv_tc(const dmrg2d_ops* ops, const void* v, float* y, int precision, 
   p.a2_boxes = BM / p.a2_box_rows;
   p.a2_lbo = (uint32_t)p.a2_box_rows * BK * (bf ? 2 : 4);  // bytes of one {rows, BK} box
   p.a2_kstep = bf ? 2048 : 1024;                           // 16 (bf16) / 8 (tf32) k-rows
+  p.a2_layout = bf ? 2u : 1u;
+  // k-row groups: 8 rows (1024 B) for the 16-byte-atom swizzle, 4 rows (512 B) for the
+  // 32-byte-atom swizzle whose pattern repeats every four 128-byte rows
+  p.a2_sbo = bf ? 1024u : 512u;
   p.tx_bytes = STAGE_A + (uint32_t)T->BN * 128;
   p.bf16 = bf ? 1 : 0;
   CUtensorMap mVk, mVm;
   const uint64_t rows = (uint64_t)ops->ld, cols = (uint64_t)d * m4;
   D2_TRY(make_map(&mVk, v, bf, rows, cols, BK, T->BN));
-  D2_TRY(make_map(&mVm, v, bf, rows, cols, (uint32_t)p.a2_box_rows, BK));
+  D2_TRY(make_map(&mVm, v, bf, rows, cols, (uint32_t)p.a2_box_rows, BK,
+                  bf ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B));
   const int grid = p.tiles < T->sms ? p.tiles : T->sms;
   auto ev = prof_slot(ops);
   if (ev.first) D2_CUDA(cudaEventRecord(ev.first, s));
