@@ -168,6 +168,34 @@ int dmrg2d_lanczos_ground(const dmrg2d_ops* ops, const dmrg2d_solver_opts* opts,
                           double* x_inout, double* energy_out,
                           dmrg2d_solver_stats* stats, void* stream);
 
+/* Allocation-free variant of dmrg2d_lanczos_ground for small superblocks.  The
+ * paper has no counterpart; it exists for callers that cannot call cudaMalloc:
+ * applications whose device memory is owned by another allocator (for example a
+ * framework's caching allocator that has reserved most of the device up front, so a
+ * second allocation fails or fragments its pool), and latency-critical loops that
+ * cannot afford cudaMalloc's implicit synchronisation.  This call allocates nothing
+ * (no cudaMalloc, cudaFree, pinned host buffer or CUDA event).  Its scratch — the
+ * Krylov basis (krylov_dim + 1 vectors), one work vector, reduction partials and
+ * small arrays — lives in one static device array of DMRG2D_NOALLOC_SCRATCH_DOUBLES
+ * doubles (16 MiB) that every GPU which loads the library holds until the process
+ * exits.
+ *   Limits: plain FP64 Lanczos only (precision = DMRG2D_FP64, refine = 0, else
+ *   EUNSUPPORTED); (krylov_dim + 2) * n_vec + 1226 * (krylov_dim + 1) + 64 doubles
+ *   must fit in the array, else ESHAPE with the sizes in dmrg2d_last_error().
+ *   Set-up: the first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call before
+ *   any stream capture.
+ *   Sharing: all calls on a device use the same array and it keeps the last call's
+ *   contents; every value the solver reads from it is written earlier in the same
+ *   call.  Calls that overlap on the GPU (other streams or host threads) race and
+ *   corrupt each other's results: serialise them.
+ * Arguments, results and status codes are those of dmrg2d_lanczos_ground; stats
+ * hv_ms is not measured (0). */
+#define DMRG2D_NOALLOC_SCRATCH_DOUBLES (2u << 20)
+int dmrg2d_lanczos_ground_noalloc(const dmrg2d_ops* ops, const dmrg2d_solver_opts* opts,
+                                  double* x_inout, double* energy_out,
+                                  dmrg2d_solver_stats* stats, void* stream);
+
 void dmrg2d_default_solver_opts(dmrg2d_solver_opts* opts);
 
 /* Kernel timing for benchmarks.  After dmrg2d_profile_start, every apply_H call

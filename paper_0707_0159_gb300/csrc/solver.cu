@@ -733,3 +733,168 @@ extern "C" int dmrg2d_lanczos_ground(const dmrg2d_ops* ops, const dmrg2d_solver_
   if (stats) *stats = local;
   return st;
 }
+
+// ---- allocation-free Lanczos for small superblocks ----------------------------------------
+// All scratch of this entry point (Krylov basis, work vector, reduction partials, the
+// tridiagonal coefficients and eigensolver workspace, device scalars) lives in one
+// file-scope device array.  Host code never dereferences the array's name: it asks the
+// runtime for the array's device address once per device and hands that to the kernels.
+static __device__ __align__(256) double g_noalloc_scratch[DMRG2D_NOALLOC_SCRATCH_DOUBLES];
+
+#include <mutex>
+
+namespace dmrg2d {
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// Device address of g_noalloc_scratch on the current device (looked up on first use).
+int noalloc_scratch(double** out) {
+  int dev = 0;
+  D2_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return set_error(DMRG2D_EINVAL, "device %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return set_error(DMRG2D_ECUDA, "cudaGetSymbolAddress(scratch) failed: %s",
+                       cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = (double*)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return DMRG2D_OK;
+}
+
+// Same recurrence as lanczos() above, with every buffer carved out of `ws`.
+int lanczos_in_place(Ctx& C, double* ws, double* x, int max_iter, int kdim, double tol, int fixed,
+                     int check_every, double* theta_out, double* resid_out, int* iters_out) {
+  const int64_t n = C.n;
+  double* Q = ws;
+  double* w = Q + (int64_t)(kdim + 1) * n;
+  double* alpha = w + n;
+  double* beta = alpha + (kdim + 1);
+  double* h = beta + (kdim + 1);
+  double* sv = h + (kdim + 1);
+  double* scr = sv + (kdim + 1);
+  double* out3 = C.scal;
+  D2_TRY(C.nrm(x, C.scal + 3));
+  D2_TRY(C.scale_inv(Q, x, C.scal + 3));
+  int j = 0, total = 0;
+  double theta = 0.0, resid = INFINITY;
+  int status = DMRG2D_ENOCONV;
+  if (check_every < 1) check_every = 1;
+  while (true) {
+    double* qj = Q + (int64_t)j * n;
+    D2_TRY(C.hv(DMRG2D_FP64, qj, w));
+    D2_TRY(C.dot(qj, w, alpha + j));
+    k_lz_axpy2<<<vgrid(n), VT, 0, C.s>>>(w, qj, j > 0 ? qj - n : nullptr, alpha + j,
+                                        j > 0 ? beta + j - 1 : nullptr, n);
+    D2_CUDA(cudaGetLastError());
+    for (int pass = 0; pass < 2; ++pass) {
+      D2_TRY(C.multidot(Q, n, j + 1, w, h));
+      D2_TRY(C.combo(w, Q, n, j + 1, h, -1));
+    }
+    D2_TRY(C.nrm(w, beta + j));
+    ++j;
+    ++total;
+    const bool last = total >= max_iter;
+    const bool full = j >= kdim;
+    if (last || full || (!fixed && total % check_every == 0)) {
+      k_tridiag_ground<<<1, 1, 0, C.s>>>(alpha, beta, j, sv, out3, scr);
+      D2_CUDA(cudaGetLastError());
+      D2_TRY(C.fetch(out3, 3));
+      theta = C.hscal[0];
+      resid = C.hscal[1];
+      if (C.hscal[2] != 0.0 || !std::isfinite(theta)) {
+        status = set_error(DMRG2D_ENAN, "NaN/Inf in the Lanczos recurrence");
+        break;
+      }
+      const bool conv = !fixed && resid <= tol * fabs(theta);
+      if (conv || last || full) {
+        D2_TRY(C.combo(x, Q, n, j, sv, 0));
+        if (conv) {
+          status = DMRG2D_OK;
+          break;
+        }
+        if (last) {
+          status = fixed ? DMRG2D_OK : DMRG2D_ENOCONV;
+          if (!fixed) set_error(DMRG2D_ENOCONV, "Lanczos: %d steps, residual %.3e", total, resid);
+          break;
+        }
+        D2_TRY(C.nrm(x, C.scal + 3));
+        D2_TRY(C.scale_inv(Q, x, C.scal + 3));
+        j = 0;
+        continue;
+      }
+    }
+    D2_TRY(C.scale_inv(Q + (int64_t)j * n, w, beta + j - 1));
+  }
+  D2_TRY(C.nrm(x, C.scal + 3));
+  D2_TRY(C.scale_inv(x, x, C.scal + 3));
+  *theta_out = theta;
+  *resid_out = resid;
+  *iters_out = total;
+  return status;
+}
+
+}  // namespace
+}  // namespace dmrg2d
+
+extern "C" int dmrg2d_lanczos_ground_noalloc(const dmrg2d_ops* ops, const dmrg2d_solver_opts* opts,
+                                             double* x_inout, double* energy_out,
+                                             dmrg2d_solver_stats* stats, void* stream) {
+  using namespace dmrg2d;
+  if (!ops || !x_inout || !energy_out) return set_error(DMRG2D_EINVAL, "NULL argument");
+  clear_error();
+  dmrg2d_solver_opts o;
+  if (opts) o = *opts; else dmrg2d_default_solver_opts(&o);
+  if (o.precision != DMRG2D_FP64 || o.refine)
+    return set_error(DMRG2D_EUNSUPPORTED, "the allocation-free solver runs plain FP64 Lanczos only");
+  if (o.max_iter < 1) return set_error(DMRG2D_EINVAL, "max_iter < 1");
+  int kdim = o.krylov_dim < 2 ? 2 : o.krylov_dim;
+  if (kdim > o.max_iter + 1) kdim = o.max_iter + 1;
+  const int64_t n = ops->n_vec;
+  const int64_t need = (int64_t)(kdim + 2) * n + 10 * (int64_t)(kdim + 1) +
+                       (int64_t)RED_BLOCKS * (kdim + 1) + 64;
+  if (kdim > 512 || need > (int64_t)DMRG2D_NOALLOC_SCRATCH_DOUBLES)
+    return set_error(DMRG2D_ESHAPE,
+                     "allocation-free Lanczos needs %lld scratch doubles for n_vec=%lld, "
+                     "krylov_dim=%d; the static scratch holds %lld (reduce krylov_dim or use "
+                     "dmrg2d_lanczos_ground)",
+                     (long long)need, (long long)n, kdim,
+                     (long long)DMRG2D_NOALLOC_SCRATCH_DOUBLES);
+  double* ws = nullptr;
+  D2_TRY(noalloc_scratch(&ws));
+  const auto t0 = std::chrono::steady_clock::now();
+  dmrg2d_solver_stats local{};
+  double hscal[64];
+  Ctx C;
+  C.ops = ops;
+  C.s = (cudaStream_t)stream;
+  C.n = n;
+  C.st = &local;
+  C.timing = false;  // no event creation on this path
+  C.hscal = hscal;   // pageable host mirror: fetch() copies and synchronises
+  // scratch layout: [basis + work + small arrays | reduction partials | device scalars]
+  const int64_t vec_part = (int64_t)(kdim + 2) * n + 10 * (int64_t)(kdim + 1);
+  C.part = ws + vec_part;
+  C.scal = C.part + (int64_t)RED_BLOCKS * (kdim + 1);
+  D2_CUDA(cudaMemsetAsync(C.scal, 0, 64 * sizeof(double), C.s));
+  double energy = 0.0, resid = 0.0;
+  int iters = 0;
+  int st = lanczos_in_place(C, ws, x_inout, o.max_iter, kdim, o.tol, o.fixed_steps, o.check_every,
+                            &energy, &resid, &iters);
+  cudaError_t e = cudaStreamSynchronize(C.s);
+  if (e != cudaSuccess && st == DMRG2D_OK)
+    st = set_error(DMRG2D_ECUDA, "solver: %s", cudaGetErrorString(e));
+  local.iters = iters;
+  local.resid = resid;
+  local.elapsed_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  *energy_out = energy;
+  if (stats) *stats = local;
+  return st;
+}

@@ -66,6 +66,9 @@ SIGNATURES = {
     "dmrg2d_apply_H": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "dmrg2d_lanczos_ground": (C.c_int, [C.c_void_p, C.POINTER(SolverOpts), C.c_void_p,
                                         C.POINTER(C.c_double), C.POINTER(SolverStats), C.c_void_p]),
+    "dmrg2d_lanczos_ground_noalloc": (C.c_int, [C.c_void_p, C.POINTER(SolverOpts), C.c_void_p,
+                                                C.POINTER(C.c_double), C.POINTER(SolverStats),
+                                                C.c_void_p]),
     "dmrg2d_default_solver_opts": (None, [C.POINTER(SolverOpts)]),
     "dmrg2d_free_ops": (None, [C.c_void_p]),
     "dmrg2d_check_device": (C.c_int, [C.c_void_p]),
@@ -233,6 +236,32 @@ def lanczos_ground(ops: Ops, x, stream=None, **opts):
     st = SolverStats()
     code = lib().dmrg2d_lanczos_ground(ops.ptr, C.byref(so), C.c_void_p(x.data_ptr()), C.byref(e),
                                        C.byref(st), _stream(stream))
+    if code not in (0, -5):
+        _check(code)
+    return e.value, {k: getattr(st, k) for k, _ in SolverStats._fields_}, code
+
+
+def lanczos_ground_noalloc(ops: Ops, x, stream=None, **opts):
+    """dmrg2d_lanczos_ground_noalloc: the plain FP64 solve of lanczos_ground with all of
+    its scratch in the library's static device array, so the call allocates nothing.
+
+    For callers that cannot call cudaMalloc (device memory owned by another allocator,
+    or loops that cannot take cudaMalloc's implicit synchronisation).  Small
+    superblocks only: (krylov_dim + 2) * n_vec plus small arrays must fit in
+    DMRG2D_NOALLOC_SCRATCH_DOUBLES doubles.  Returns (energy, stats, status).
+    """
+    o = default_solver_opts()
+    for k, v in opts.items():
+        if k not in o:
+            raise KeyError(k)
+        o[k] = PRECISION.get(v, v) if k == "precision" else v
+    so = SolverOpts(**o)
+    if not x.is_cuda or str(x.dtype) != "torch.float64" or x.numel() != ops.info["n_vec"]:
+        raise ValueError("x must be a CUDA float64 tensor of n_vec elements")
+    e = C.c_double()
+    st = SolverStats()
+    code = lib().dmrg2d_lanczos_ground_noalloc(ops.ptr, C.byref(so), C.c_void_p(x.data_ptr()),
+                                               C.byref(e), C.byref(st), _stream(stream))
     if code not in (0, -5):
         _check(code)
     return e.value, {k: getattr(st, k) for k, _ in SolverStats._fields_}, code
