@@ -106,6 +106,7 @@ typedef struct dmrg2d_ops_info {
   double flops_per_apply;  /* algorithmic flops of one H·v (see dmrg2d_apply_H)     */
   int tc_ok;               /* 1 if the tcgen05 path supports these shapes          */
   int64_t device_bytes;    /* device memory owned by the ops object                */
+  int n_sectors;           /* combined left labels (0 for a dense superblock)       */
 } dmrg2d_ops_info;
 
 /* Build the packed operators of H_l, H_r and H_c (paper Eq. (dec)).
@@ -116,8 +117,17 @@ typedef struct dmrg2d_ops_info {
  * (i2, i2') of H_l touched by a block operator becomes one dense m1 x m1 block;
  * terms that are multiples of the identity in block space (off-diagonal
  * column terms, all of H_c) become scalar tile moves.
- * target: NULL for the dense superblock; otherwise the sector is not yet
- * supported by this build and DMRG2D_EUNSUPPORTED is returned.
+ * target: NULL for the dense superblock.  Otherwise the superblock is restricted
+ * to the states whose quantum numbers add up to target[0..nq) (nq = 1: N_up for
+ * spins, nq = 2: (N_up, N_dn) for electrons); both blocks need qn, and states with
+ * equal labels must be contiguous.  Packed vector layout of a restricted superblock:
+ * for every combined left label qL = q(i1) + q(i2), in increasing lexicographic
+ * order, one column-major matrix V_qL whose rows are, for i2 = 0..d-1, the block-1
+ * sector with label qL - q(i2) (its states in order), each such segment padded with
+ * zero rows to a multiple of 8, and whose columns are, for i3 = 0..d-1, the block-4
+ * sector with label target - qL - q(i3); leading dimension = padded row count; the
+ * matrices follow one another.  Padding entries must be zero on input and are written
+ * as zero on output.  dmrg2d_sector_dense_index returns the map.
  * stream: cudaStream_t (may be NULL) used for the uploads.
  * Errors: EINVAL for NULL/invalid fields, ESHAPE if n_edge != 0 and != 2*n_legs,
  * ENOMEM/ECUDA on device failures (nothing leaks; *out is left NULL). */
@@ -126,6 +136,11 @@ int dmrg2d_build_ops(const dmrg2d_model* model, const dmrg2d_block* left,
                      dmrg2d_ops** out, void* stream);
 
 int dmrg2d_ops_get_info(const dmrg2d_ops* ops, dmrg2d_ops_info* info);
+
+/* Sector-restricted ops only: out[p] (host array of info.n_vec entries) receives the
+ * dense superblock index i1 + m1*i2 + m1*d*i4 + m1*d*m4*i3 of packed position p, or
+ * -1 for a padding row.  EINVAL for a dense ops object. */
+int dmrg2d_sector_dense_index(const dmrg2d_ops* ops, int64_t* out);
 
 /* y = H v (paper: H_l V + V H_r^T + H_c V_c).  v and y are caller-owned device
  * buffers of info.n_vec elements in the layout above; they must not overlap.

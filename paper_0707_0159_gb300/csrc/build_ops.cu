@@ -200,6 +200,11 @@ static int assemble(const dmrg2d_model* M, const dmrg2d_block* L, const dmrg2d_b
   Column col = heis ? spin_column(M->n_legs, M->J_rung, M->rung_pbc != 0)
                     : hubbard_column(M->n_legs, M->t, M->U, M->rung_pbc != 0);
   const int d = col.d, m1 = L->m, m4 = R->m;
+  ops->hqc.assign((size_t)d * 2, 0);
+  for (int i = 0; i < d; ++i) {
+    ops->hqc[2 * i] = col.nup[i];
+    ops->hqc[2 * i + 1] = col.ndn[i];
+  }
   ops->d = d;
   ops->m1 = m1;
   ops->m4 = m4;
@@ -369,8 +374,6 @@ extern "C" int dmrg2d_build_ops(const dmrg2d_model* model, const dmrg2d_block* l
     return set_error(DMRG2D_EINVAL, "n_legs = %d outside [1, %d]", model->n_legs, max_legs);
   D2_TRY(check_block(left, model->n_legs, model->kind, "left"));
   D2_TRY(check_block(right, model->n_legs, model->kind, "right"));
-  if (target)
-    return set_error(DMRG2D_EUNSUPPORTED, "sector-restricted superblocks are not supported yet");
   cudaStream_t s = (cudaStream_t)stream;
 
   dmrg2d_ops* ops = new dmrg2d_ops();
@@ -382,6 +385,17 @@ extern "C" int dmrg2d_build_ops(const dmrg2d_model* model, const dmrg2d_block* l
   if (st != DMRG2D_OK) {
     delete ops;
     return st;
+  }
+  if (target) {  // sector-restricted: pack the sub-blocks, skip the dense uploads
+    st = sec_build(ops, left, right, target, HL, HR, s);
+    if (st == DMRG2D_OK) st = tc_prepare(ops, s);
+    if (st != DMRG2D_OK) {
+      sec_release(ops);
+      delete ops;
+      return st;
+    }
+    *out = ops;
+    return DMRG2D_OK;
   }
   std::vector<float> HL32(HL.begin(), HL.end()), HR32(HR.begin(), HR.end());
   std::vector<__nv_bfloat16> HL16(HL.size()), HR16(HR.size());
@@ -436,7 +450,13 @@ extern "C" int dmrg2d_ops_get_info(const dmrg2d_ops* ops, dmrg2d_ops_info* info)
   info->flops_per_apply = ops->flops;
   info->tc_ok = ops->tc_ok;
   info->device_bytes = ops->device_bytes;
+  info->n_sectors = sec_count(ops);
   return DMRG2D_OK;
+}
+
+extern "C" int dmrg2d_sector_dense_index(const dmrg2d_ops* ops, int64_t* out) {
+  if (!ops || !out) return set_error(DMRG2D_EINVAL, "NULL argument");
+  return sec_dense_index(ops, out);
 }
 
 static void prof_clear(dmrg2d_ops* ops) {
@@ -483,6 +503,7 @@ extern "C" int dmrg2d_profile_stop(dmrg2d_ops* ops, double* total_ms, int* launc
 extern "C" void dmrg2d_free_ops(dmrg2d_ops* ops) {
   if (!ops) return;
   prof_clear(ops);
+  sec_release(ops);
   tc_release(ops);
   release_device(ops);
   delete ops;

@@ -72,6 +72,9 @@ struct dmrg2d_ops {
   // host copies of the CSR structure (tile schedulers, tests)
   std::vector<int> hLptr, hLcol, hRptr, hRcol, hCptr, hCsrc;
   std::vector<double> hCval;
+  std::vector<int> hqc;  // column quantum numbers, (N_up, N_dn) per column state
+  // sector-restricted operation (NULL for the dense superblock), opaque here
+  void* sec = nullptr;
   // tensor-core path state (tensor maps of the operator blocks), opaque here
   void* tc = nullptr;
   // kernel timing (dmrg2d_profile_start/stop); apply_H only records into it
@@ -97,6 +100,15 @@ int tc_prepare(dmrg2d_ops* ops, cudaStream_t s);
 void tc_release(dmrg2d_ops* ops);
 int launch_hv_tc(const dmrg2d_ops* ops, const void* v, float* y, int precision, cudaStream_t s);
 int tc_read_error(const dmrg2d_ops* ops, int* code);
+
+// sectors.cu
+int sec_build(dmrg2d_ops* ops, const dmrg2d_block* L, const dmrg2d_block* R, const int32_t* target,
+              const std::vector<double>& HL, const std::vector<double>& HR, cudaStream_t s);
+void sec_release(dmrg2d_ops* ops);
+int sec_apply(const dmrg2d_ops* ops, const void* v, void* y, int precision, cudaStream_t s);
+int sec_zero_padding(const dmrg2d_ops* ops, double* x, cudaStream_t s);
+int sec_dense_index(const dmrg2d_ops* ops, int64_t* out);
+int sec_count(const dmrg2d_ops* ops);
 
 // vector kernels used by the solvers (solver.cu)
 int convert_f64_to(const double* x, void* out, int precision, int64_t n, cudaStream_t s);

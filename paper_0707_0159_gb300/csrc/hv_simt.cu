@@ -156,10 +156,12 @@ int launch(const dmrg2d_ops* ops, const T* v, T* y, const T* HL, const T* HR, co
 }  // namespace
 
 int launch_hv_simt_f64(const dmrg2d_ops* ops, const double* v, double* y, cudaStream_t s) {
+  if (ops->sec) return sec_apply(ops, v, y, DMRG2D_FP64, s);
   return launch<double>(ops, v, y, ops->dev.HL64, ops->dev.HR64, ops->dev.Cval64, s);
 }
 
 int launch_hv_simt_f32(const dmrg2d_ops* ops, const float* v, float* y, cudaStream_t s) {
+  if (ops->sec) return sec_apply(ops, v, y, DMRG2D_FP32, s);
   return launch<float>(ops, v, y, ops->dev.HL32, ops->dev.HR32, ops->dev.Cval32, s);
 }
 

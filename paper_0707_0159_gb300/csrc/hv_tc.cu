@@ -437,6 +437,7 @@ uint32_t make_idesc(int fmt, int a_mn, int M, int N) {
 
 int tc_prepare(dmrg2d_ops* ops, cudaStream_t s) {
   ops->tc_ok = 0;
+  if (ops->sec) return DMRG2D_OK;  // sector-restricted superblocks: grouped path
   const int m1 = ops->m1, m4 = ops->m4;
   if (m1 % BM != 0 || !(m4 == 128 || m4 % 256 == 0)) return DMRG2D_OK;  // SIMT only
   if (!encode_fn()) return DMRG2D_OK;

@@ -710,6 +710,7 @@ extern "C" int dmrg2d_lanczos_ground(const dmrg2d_ops* ops, const dmrg2d_solver_
   }
   int st;
   double energy = 0.0;
+  D2_TRY(sec_zero_padding(ops, x_inout, C.s));  // restricted layouts: padding rows stay zero
   if (o.refine && o.precision != DMRG2D_FP64) {
     st = mixed_solve(C, &o, x_inout, &energy);
   } else {

@@ -43,7 +43,7 @@ class OpsInfo(C.Structure):
     _fields_ = [("n_vec", C.c_int64), ("m1", C.c_int), ("m4", C.c_int), ("d", C.c_int),
                 ("n_legs", C.c_int), ("n_blk_left", C.c_int), ("n_blk_right", C.c_int),
                 ("n_scalar", C.c_int), ("flops_per_apply", C.c_double), ("tc_ok", C.c_int),
-                ("device_bytes", C.c_int64)]
+                ("device_bytes", C.c_int64), ("n_sectors", C.c_int)]
 
 
 class SolverOpts(C.Structure):
@@ -63,6 +63,7 @@ SIGNATURES = {
     "dmrg2d_build_ops": (C.c_int, [C.POINTER(Model), C.POINTER(Block), C.POINTER(Block),
                                    C.POINTER(C.c_int32), C.POINTER(C.c_void_p), C.c_void_p]),
     "dmrg2d_ops_get_info": (C.c_int, [C.c_void_p, C.POINTER(OpsInfo)]),
+    "dmrg2d_sector_dense_index": (C.c_int, [C.c_void_p, C.c_void_p]),
     "dmrg2d_apply_H": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "dmrg2d_lanczos_ground": (C.c_int, [C.c_void_p, C.POINTER(SolverOpts), C.c_void_p,
                                         C.POINTER(C.c_double), C.POINTER(SolverStats), C.c_void_p]),
@@ -178,6 +179,13 @@ def build_ops(model: dict, left: dict, right: dict, target=None, stream=None) ->
                                   _stream(stream))
     _check(code)
     return Ops(out)
+
+
+def sector_dense_index(ops: Ops) -> np.ndarray:
+    """Dense superblock index of every packed position (-1 for padding rows)."""
+    out = np.empty(ops.info["n_vec"], dtype=np.int64)
+    _check(lib().dmrg2d_sector_dense_index(ops.ptr, out.ctypes.data_as(C.c_void_p)))
+    return out
 
 
 _DTYPES = {FP64: ("float64", "float64"), FP32: ("float32", "float32"),
