@@ -211,6 +211,22 @@ int dmrg2d_lanczos_ground_noalloc(const dmrg2d_ops* ops, const dmrg2d_solver_opt
                                   double* x_inout, double* energy_out,
                                   dmrg2d_solver_stats* stats, void* stream);
 
+/* Tensor-core tile configurations of the H_l V + V H_r^T kernel.  Index 0 is the
+ * dense kernel (dense superblocks with m1 % 128 == 0 and m4 = 128 or m4 % 256 == 0);
+ * index 1 + c is the grouped kernel (any sector structure; dense superblocks with
+ * m1 % 8 == 0) with pieces of 128 x 128 (c = 0..2) or 128 x 256 (c = 3..5) in
+ * column-slab, row-slab or longest-first order.  dmrg2d_autotune times every
+ * configuration that applies (one warm-up and three timed launches each, on scratch
+ * buffers it allocates and frees), keeps the fastest for later apply_H and solver
+ * calls at `precision` (TF32 or BF16), and returns its index in *best; ms[i]
+ * (optional, n_ms entries) receives candidate i's time, -1 when it does not apply.
+ * The call synchronises the stream.  dmrg2d_set_tile_config makes an explicit choice
+ * (EUNSUPPORTED if the index does not apply). */
+int dmrg2d_autotune(dmrg2d_ops* ops, int precision, int* best, double* ms, int n_ms,
+                    void* stream);
+int dmrg2d_set_tile_config(dmrg2d_ops* ops, int precision, int index);
+const char* dmrg2d_tile_config_name(int index);
+
 void dmrg2d_default_solver_opts(dmrg2d_solver_opts* opts);
 
 /* Kernel timing for benchmarks.  After dmrg2d_profile_start, every apply_H call

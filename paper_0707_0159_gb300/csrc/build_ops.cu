@@ -388,7 +388,6 @@ extern "C" int dmrg2d_build_ops(const dmrg2d_model* model, const dmrg2d_block* l
   }
   if (target) {  // sector-restricted: pack the sub-blocks, skip the dense uploads
     st = sec_build(ops, left, right, target, HL, HR, s);
-    if (st == DMRG2D_OK) st = tc_prepare(ops, s);
     if (st != DMRG2D_OK) {
       sec_release(ops);
       delete ops;
@@ -426,7 +425,7 @@ extern "C" int dmrg2d_build_ops(const dmrg2d_model* model, const dmrg2d_block* l
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) st = set_error(DMRG2D_ECUDA, "upload: %s", cudaGetErrorString(e));
   }
-  if (st == DMRG2D_OK) st = tc_prepare(ops, s);
+  if (st == DMRG2D_OK) st = tc_prepare(ops, s, HL, HR);
   if (st != DMRG2D_OK) {
     tc_release(ops);
     release_device(ops);

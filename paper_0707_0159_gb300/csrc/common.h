@@ -77,6 +77,9 @@ struct dmrg2d_ops {
   void* sec = nullptr;
   // tensor-core path state (tensor maps of the operator blocks), opaque here
   void* tc = nullptr;
+  // tensor-core kernel choice per precision: -1 the dense kernel, >= 0 a grouped-kernel
+  // tile configuration (set by dmrg2d_autotune; defaults chosen at build time)
+  int tc_cfg[4] = {-1, -1, -1, -1};
   // kernel timing (dmrg2d_profile_start/stop); apply_H only records into it
   mutable std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
   mutable size_t prof_used = 0;
@@ -96,7 +99,11 @@ int launch_hv_simt_f64(const dmrg2d_ops* ops, const double* v, double* y, cudaSt
 int launch_hv_simt_f32(const dmrg2d_ops* ops, const float* v, float* y, cudaStream_t s);
 
 // hv_tc.cu
-int tc_prepare(dmrg2d_ops* ops, cudaStream_t s);
+int tc_prepare(dmrg2d_ops* ops, cudaStream_t s, const std::vector<double>& HL,
+               const std::vector<double>& HR);
+int tc_gemm(const dmrg2d_ops* ops, const void* v, float* y, int precision, int cfg,
+            cudaStream_t s);
+int sec_read_error(const dmrg2d_ops* ops, int* code);
 void tc_release(dmrg2d_ops* ops);
 int launch_hv_tc(const dmrg2d_ops* ops, const void* v, float* y, int precision, cudaStream_t s);
 int tc_read_error(const dmrg2d_ops* ops, int* code);
@@ -109,6 +116,8 @@ int sec_apply(const dmrg2d_ops* ops, const void* v, void* y, int precision, cuda
 int sec_zero_padding(const dmrg2d_ops* ops, double* x, cudaStream_t s);
 int sec_dense_index(const dmrg2d_ops* ops, int64_t* out);
 int sec_count(const dmrg2d_ops* ops);
+int sec_tc_gemm(const dmrg2d_ops* ops, const void* v, float* y, int precision, int cfg,
+                cudaStream_t s);
 
 // vector kernels used by the solvers (solver.cu)
 int convert_f64_to(const double* x, void* out, int precision, int64_t n, cudaStream_t s);

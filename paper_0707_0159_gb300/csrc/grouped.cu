@@ -1,0 +1,613 @@
+// Grouped tcgen05 H·v over a work list of (row segment x column segment) pieces.
+//
+// Same pipeline as hv_tc_kernel (TMA ring, one MMA-issuing thread, two TMEM
+// accumulators, four epilogue warps, bounded waits), but every piece reads its
+// operator blocks and its V_q slices from per-segment lists, so one persistent launch
+// covers uneven quantum-number sectors (or the dense superblock as a single sector).
+// Rows of a piece beyond its segment and K beyond a block's width meet zero-padded
+// pool columns or are masked in the epilogue; the epilogue also writes the zero
+// padding rows of the segment.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+
+#include <cudaTypedefs.h>
+
+#include "grouped.h"
+#include "tc_ptx.cuh"
+
+namespace dmrg2d {
+
+namespace {
+
+using namespace tc;
+
+constexpr int GQ_MAX = 64;  // sectors per launch (V tensor maps travel as kernel parameters)
+constexpr int G_THREADS = 192;
+constexpr int G_STAGES = 4;
+constexpr int G_BM = 128;
+constexpr uint32_t G_STAGE_A = 16384, G_STAGE_B = 32768, G_STAGE = G_STAGE_A + G_STAGE_B;
+constexpr uint32_t G_TMEM_COLS = 512, G_ACC_COLS = 256;
+constexpr size_t G_SMEM = G_STAGES * G_STAGE + 1024 + 256;
+constexpr int N_ORDERS = 3;  // column-slab raster, row-slab raster, longest piece first
+
+struct GMaps {
+  CUtensorMap L, R;
+  CUtensorMap vk[GQ_MAX];
+  CUtensorMap vm[GQ_MAX];
+};
+
+struct GParams {
+  int ntiles, bn, BK;
+  const GTile* tiles;
+  const GRow* rows;
+  const GCol* cols;
+  const GK1* k1;
+  const GK2* k2;
+  const long long* qbase;
+  const int* qld;
+  float* y;
+  int* err;
+  uint32_t idesc1[2], idesc2[2];
+  uint32_t a2_lbo, a2_sbo, a2_kstep, a2_layout;
+  int a2_boxes, a2_box_rows;
+  uint32_t tx_bytes;
+  int bf16;
+};
+
+struct GDev {
+  GTile* tiles[2][N_ORDERS] = {};
+  int ntiles[2][N_ORDERS] = {};
+  GRow* rows = nullptr;
+  GCol* cols = nullptr;
+  GK1* k1 = nullptr;
+  GK2* k2 = nullptr;
+  long long* qbase = nullptr;
+  int* qld = nullptr;
+  float* pL32 = nullptr;
+  float* pR32 = nullptr;
+  __nv_bfloat16* pL16 = nullptr;
+  __nv_bfloat16* pR16 = nullptr;
+  int KPL = 0, KPR = 0, prL = 0, prR = 0;
+  CUtensorMap mL[2], mR[2][2];  // [precision][piece width 128/256]
+  int* err = nullptr;
+  int sms = 0;
+  std::vector<void*> allocs;
+};
+
+__global__ void __launch_bounds__(G_THREADS, 1)
+hv_tc_grouped_kernel(const __grid_constant__ GMaps maps, const GParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(smem + G_STAGES * G_STAGE);
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * G_STAGES + 4);
+  volatile int* abort = (volatile int*)(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  auto full = [&](int s) { return smem_u32(bars + s); };
+  auto empty = [&](int s) { return smem_u32(bars + G_STAGES + s); };
+  auto tfull = [&](int b) { return smem_u32(bars + 2 * G_STAGES + b); };
+  auto tempty = [&](int b) { return smem_u32(bars + 2 * G_STAGES + 2 + b); };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < G_STAGES; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull(b), 1);
+      mbar_init(tempty(b), 4);
+    }
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(G_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const int BK = p.BK;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------- TMA producer -------------------------------
+    int stage = 0;
+    uint32_t phase = 0;
+    for (int ti = blockIdx.x; ti < p.ntiles && !*abort; ti += gridDim.x) {
+      const GTile t = p.tiles[ti];
+      const GRow rs = p.rows[t.rs];
+      const GCol cs = p.cols[t.cs];
+      const int r0 = rs.off + t.r_in, c0 = cs.off + t.c_in;
+      const CUtensorMap* vk = &maps.vk[rs.q];
+      const CUtensorMap* vm = &maps.vm[rs.q];
+      for (int ph = 0; ph < 2; ++ph) {
+        const int e0 = ph == 0 ? rs.k1b : cs.k2b, e1 = ph == 0 ? rs.k1e : cs.k2e;
+        for (int e = e0; e < e1; ++e) {
+          int kdim, a_pool = 0, b_row = 0, a_col = 0, b_pool = 0;
+          if (ph == 0) {
+            const GK1 k = p.k1[e];
+            kdim = k.kdim;
+            a_pool = k.a_pool;
+            b_row = k.b_row;
+          } else {
+            const GK2 k = p.k2[e];
+            kdim = k.kdim;
+            a_col = k.a_col;
+            b_pool = k.b_pool;
+          }
+          const int nk = (kdim + BK - 1) / BK;
+          for (int kc = 0; kc < nk; ++kc) {
+            if (!mbar_wait(empty(stage), phase ^ 1u, abort)) {
+              raise_abort(abort, p.err, 11);
+              goto producer_done;
+            }
+            const uint32_t a_s = smem_u32(smem + stage * G_STAGE);
+            const uint32_t b_s = a_s + G_STAGE_A;
+            mbar_expect_tx(full(stage), p.tx_bytes);
+            if (ph == 0) {
+              tma_load_2d(a_s, &maps.L, full(stage), kc * BK, a_pool + t.r_in);
+              tma_load_2d(b_s, vk, full(stage), b_row + kc * BK, c0);
+            } else {
+              for (int b = 0; b < p.a2_boxes; ++b)
+                tma_load_2d(a_s + b * p.a2_lbo, vm, full(stage), r0 + b * p.a2_box_rows,
+                            a_col + kc * BK);
+              tma_load_2d(b_s, &maps.R, full(stage), kc * BK, b_pool + t.c_in);
+            }
+            if (++stage == G_STAGES) {
+              stage = 0;
+              phase ^= 1u;
+            }
+          }
+        }
+      }
+    }
+  producer_done:;
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------- MMA issuer ---------------------------------
+    int stage = 0;
+    uint32_t phase = 0;
+    int acc = 0;
+    uint32_t aphase = 0;
+    for (int ti = blockIdx.x; ti < p.ntiles && !*abort; ti += gridDim.x) {
+      const GTile t = p.tiles[ti];
+      const GRow rs = p.rows[t.rs];
+      const GCol cs = p.cols[t.cs];
+      if (!mbar_wait(tempty(acc), aphase ^ 1u, abort)) {
+        raise_abort(abort, p.err, 12);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t dt = tmem_base + acc * G_ACC_COLS;
+      uint32_t accum = 0;
+      bool ok = true;
+      for (int ph = 0; ph < 2 && ok; ++ph) {
+        const int e0 = ph == 0 ? rs.k1b : cs.k2b, e1 = ph == 0 ? rs.k1e : cs.k2e;
+        for (int e = e0; e < e1 && ok; ++e) {
+          const int kdim = ph == 0 ? p.k1[e].kdim : p.k2[e].kdim;
+          const int neg = ph == 0 ? p.k1[e].neg : p.k2[e].neg;
+          const uint32_t id = ph == 0 ? p.idesc1[neg] : p.idesc2[neg];
+          const int nk = (kdim + BK - 1) / BK;
+          for (int kc = 0; kc < nk; ++kc) {
+            if (!mbar_wait(full(stage), phase, abort)) {
+              raise_abort(abort, p.err, 13);
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t a_s = smem_u32(smem + stage * G_STAGE);
+            const uint32_t b_s = a_s + G_STAGE_A;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const uint64_t ad = ph == 0 ? sdesc(a_s + k * 32, 16, 1024)
+                                          : sdesc(a_s + k * p.a2_kstep, p.a2_lbo, p.a2_sbo,
+                                                  p.a2_layout);
+              const uint64_t bd = sdesc(b_s + k * 32, 16, 1024);
+              umma(dt, ad, bd, id, accum, p.bf16);
+              accum = 1;
+            }
+            umma_commit(empty(stage));
+            if (++stage == G_STAGES) {
+              stage = 0;
+              phase ^= 1u;
+            }
+          }
+        }
+      }
+      if (!ok) break;
+      umma_commit(tfull(acc));
+      if (++acc == 2) {
+        acc = 0;
+        aphase ^= 1u;
+      }
+    }
+  } else if (warp >= 2) {
+    // ------------------------------- epilogue -----------------------------------
+    const int q4 = warp & 3;
+    int acc = 0;
+    uint32_t aphase = 0;
+    for (int ti = blockIdx.x; ti < p.ntiles; ti += gridDim.x) {
+      const GTile t = p.tiles[ti];
+      const GRow rs = p.rows[t.rs];
+      const GCol cs = p.cols[t.cs];
+      if (!mbar_wait(tfull(acc), aphase, abort)) {
+        raise_abort(abort, p.err, 14);
+        break;
+      }
+      tc_fence_after();
+      const bool has_k = rs.k1e > rs.k1b || cs.k2e > cs.k2b;
+      const int rows_valid = min(G_BM, rs.dim - t.r_in);
+      const int rows_out = min(G_BM, rs.dim_pad - t.r_in);  // valid rows + zero padding rows
+      const int cols_valid = min(p.bn, cs.dim - t.c_in);
+      const int row = 32 * q4 + lane;
+      const long long ld = p.qld[rs.q];
+      float* yq = p.y + p.qbase[rs.q] + rs.off + t.r_in + row + ld * (cs.off + t.c_in);
+      for (int ch = 0; ch < p.bn / 32 && ch * 32 < cols_valid; ++ch) {
+        uint32_t v[32];
+        if (has_k) {
+          tmem_ld32(tmem_base + ((uint32_t)(32 * q4) << 16) + acc * G_ACC_COLS + ch * 32, v);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] = 0u;
+        }
+        if (row < rows_out) {
+          const bool real = row < rows_valid;
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (ch * 32 + j < cols_valid)
+              yq[ld * (ch * 32 + j)] = real ? __uint_as_float(v[j]) : 0.f;
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty(acc));
+      if (++acc == 2) {
+        acc = 0;
+        aphase ^= 1u;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(G_TMEM_COLS)
+                 : "memory");
+  }
+}
+
+__global__ void k_pool_convert(const double* __restrict__ x, float* __restrict__ o32,
+                               __nv_bfloat16* __restrict__ o16, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float f = (float)x[i];
+    uint32_t u;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(f));
+    o32[i] = __uint_as_float(u);
+    o16[i] = __float2bfloat16_rn(f);
+  }
+}
+
+uint64_t hash_vals(const double* a, int rows, int cols, int64_t ld, double sign) {
+  uint64_t h = 1469598103934665603ull ^ ((uint64_t)rows << 32 | (uint32_t)cols);
+  for (int i = 0; i < rows; ++i)
+    for (int j = 0; j < cols; ++j) {
+      double x = sign * a[(int64_t)i * ld + j];
+      if (x == 0.0) x = 0.0;  // +0 and -0 hash alike
+      uint64_t u;
+      memcpy(&u, &x, 8);
+      h = (h ^ u) * 1099511628211ull;
+    }
+  return h;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* q = nullptr;
+    cudaDriverEntryPointQueryResult r;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &q, 12000, cudaEnableDefault,
+                                         &r) == cudaSuccess &&
+        r == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)q;
+  }
+  return fn;
+}
+
+int map2d(CUtensorMap* m, const void* base, bool bf16, uint64_t inner, uint64_t outer,
+          uint32_t bi, uint32_t bo, CUtensorMapSwizzle swz) {
+  auto fn = encode();
+  if (!fn) return set_error(DMRG2D_ECUDA, "cuTensorMapEncodeTiled unavailable");
+  const uint32_t elt = bf16 ? 2 : 4;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {inner * elt};
+  cuuint32_t box[2] = {bi, bo};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                  const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return set_error(DMRG2D_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return DMRG2D_OK;
+}
+
+template <typename T>
+int gup(GDev* D, const std::vector<T>& h, T** d, int64_t* bytes, cudaStream_t s) {
+  *d = nullptr;
+  if (h.empty()) return DMRG2D_OK;
+  const size_t nb = h.size() * sizeof(T);
+  if (cudaMalloc((void**)d, nb) != cudaSuccess) {
+    *d = nullptr;
+    return set_error(DMRG2D_ENOMEM, "cudaMalloc(%zu) failed (grouped plan)", nb);
+  }
+  D->allocs.push_back(*d);
+  *bytes += (int64_t)nb;
+  D2_CUDA(cudaMemcpyAsync(*d, h.data(), nb, cudaMemcpyHostToDevice, s));
+  return DMRG2D_OK;
+}
+
+const char* kNames[2 * N_ORDERS] = {"128x128 column-slab", "128x128 row-slab", "128x128 longest-first",
+                                    "128x256 column-slab", "128x256 row-slab", "128x256 longest-first"};
+
+}  // namespace
+
+std::pair<int, int> BlockPool::add(const double* src, int rows, int cols, int64_t ld) {
+  const uint64_t hp = hash_vals(src, rows, cols, ld, 1.0);
+  const uint64_t hn = hash_vals(src, rows, cols, ld, -1.0);
+  for (size_t i = 0; i < ent.size(); ++i) {
+    const Entry& e = ent[i];
+    if (e.rows != rows || e.cols != cols || (e.h != hp && e.h != hn)) continue;
+    for (int sg = 0; sg < 2; ++sg) {
+      const double sign = sg ? -1.0 : 1.0;
+      if (e.h != (sg ? hn : hp)) continue;
+      bool same = true;
+      for (int r = 0; r < rows && same; ++r)
+        for (int c = 0; c < cols; ++c)
+          if (e.a[(size_t)r * cols + c] != sign * src[(int64_t)r * ld + c]) {
+            same = false;
+            break;
+          }
+      if (same) return {(int)i, sg};
+    }
+  }
+  Entry e;
+  e.rows = rows;
+  e.cols = cols;
+  e.h = hp;
+  e.a.resize((size_t)rows * cols);
+  for (int r = 0; r < rows; ++r)
+    for (int c = 0; c < cols; ++c) e.a[(size_t)r * cols + c] = src[(int64_t)r * ld + c];
+  ent.push_back(std::move(e));
+  return {(int)ent.size() - 1, 0};
+}
+
+int gp_num_configs() { return 2 * N_ORDERS; }
+const char* gp_config_name(int cfg) {
+  return cfg >= 0 && cfg < 2 * N_ORDERS ? kNames[cfg] : "?";
+}
+
+int gp_finalise(dmrg2d_ops* ops, GroupPlan* g, cudaStream_t s) {
+  if (g->nQ > GQ_MAX)
+    return set_error(DMRG2D_EUNSUPPORTED, "%d sectors exceed the grouped kernel's %d", g->nQ,
+                     GQ_MAX);
+  for (int q = 0; q < g->nQ; ++q)
+    if (g->qld[q] % 8 != 0 || g->qbase[q] % 8 != 0)
+      return set_error(DMRG2D_EUNSUPPORTED, "V_q not 8-element aligned");
+  GDev* D = new GDev();
+  g->dev = D;
+  // ---- pools: entries laid out row after row, K padded with zeros to a multiple of 64 ----
+  auto layout = [&](BlockPool& P, int& KP, int& prow, std::vector<int>& first) {
+    KP = 64;
+    for (auto& e : P.ent) KP = std::max(KP, (e.cols + 63) / 64 * 64);
+    prow = 0;
+    first.resize(P.ent.size());
+    for (size_t i = 0; i < P.ent.size(); ++i) {
+      first[i] = prow;
+      prow += P.ent[i].rows;
+    }
+    prow = std::max(prow, 256);  // never smaller than one TMA box of rows
+  };
+  std::vector<int> fL, fR;
+  layout(g->poolL, D->KPL, D->prL, fL);
+  layout(g->poolR, D->KPR, D->prR, fR);
+  for (auto& k : g->k1) k.a_pool = fL[k.a_pool];
+  for (auto& k : g->k2) k.b_pool = fR[k.b_pool];
+  auto fill = [](const BlockPool& P, int KP, int prow, const std::vector<int>& first) {
+    std::vector<double> h((size_t)std::max(prow, 1) * KP, 0.0);
+    for (size_t i = 0; i < P.ent.size(); ++i)
+      for (int r = 0; r < P.ent[i].rows; ++r)
+        for (int c = 0; c < P.ent[i].cols; ++c)
+          h[(size_t)(first[i] + r) * KP + c] = P.ent[i].a[(size_t)r * P.ent[i].cols + c];
+    return h;
+  };
+  std::vector<double> hL = fill(g->poolL, D->KPL, D->prL, fL);
+  std::vector<double> hR = fill(g->poolR, D->KPR, D->prR, fR);
+  // ---- tile lists: two piece widths x three orders ----
+  auto cost = [&](const GTile& t) {
+    const GRow& r = g->rows[t.rs];
+    const GCol& c = g->cols[t.cs];
+    long long w = 0;
+    for (int e = r.k1b; e < r.k1e; ++e) w += (g->k1[e].kdim + 63) / 64;
+    for (int e = c.k2b; e < c.k2e; ++e) w += (g->k2[e].kdim + 63) / 64;
+    return w;
+  };
+  std::vector<GTile> lists[2][N_ORDERS];
+  for (int b = 0; b < 2; ++b) {
+    const int bn = b ? 256 : 128;
+    std::vector<GTile> colmaj, rowmaj;
+    for (int q = 0; q < g->nQ; ++q) {
+      for (size_t c = 0; c < g->cols.size(); ++c) {
+        if (g->cols[c].q != q) continue;
+        for (int ci = 0; ci < g->cols[c].dim; ci += bn)
+          for (size_t r = 0; r < g->rows.size(); ++r) {
+            if (g->rows[r].q != q) continue;
+            for (int ri = 0; ri < g->rows[r].dim; ri += G_BM)
+              colmaj.push_back({(int)r, (int)c, ri, ci});
+          }
+      }
+      for (size_t r = 0; r < g->rows.size(); ++r) {
+        if (g->rows[r].q != q) continue;
+        for (int ri = 0; ri < g->rows[r].dim; ri += G_BM)
+          for (size_t c = 0; c < g->cols.size(); ++c) {
+            if (g->cols[c].q != q) continue;
+            for (int ci = 0; ci < g->cols[c].dim; ci += bn)
+              rowmaj.push_back({(int)r, (int)c, ri, ci});
+          }
+      }
+    }
+    std::vector<GTile> lpt = colmaj;
+    std::stable_sort(lpt.begin(), lpt.end(),
+                     [&](const GTile& x, const GTile& y) { return cost(x) > cost(y); });
+    lists[b][0] = colmaj;
+    lists[b][1] = rowmaj;
+    lists[b][2] = lpt;
+  }
+  // ---- upload ----
+  int64_t* nb = &ops->device_bytes;
+  int st = DMRG2D_OK;
+  for (int b = 0; b < 2 && st == DMRG2D_OK; ++b)
+    for (int o = 0; o < N_ORDERS && st == DMRG2D_OK; ++o) {
+      st = gup(D, lists[b][o], &D->tiles[b][o], nb, s);
+      D->ntiles[b][o] = (int)lists[b][o].size();
+    }
+  if (st == DMRG2D_OK) st = gup(D, g->rows, &D->rows, nb, s);
+  if (st == DMRG2D_OK) st = gup(D, g->cols, &D->cols, nb, s);
+  if (st == DMRG2D_OK) st = gup(D, g->k1, &D->k1, nb, s);
+  if (st == DMRG2D_OK) st = gup(D, g->k2, &D->k2, nb, s);
+  if (st == DMRG2D_OK) st = gup(D, g->qbase, &D->qbase, nb, s);
+  if (st == DMRG2D_OK) st = gup(D, g->qld, &D->qld, nb, s);
+  double *dL = nullptr, *dR = nullptr;
+  if (st == DMRG2D_OK) st = gup(D, hL, &dL, nb, s);
+  if (st == DMRG2D_OK) st = gup(D, hR, &dR, nb, s);
+  auto alloc = [&](void** p, size_t bytes) {
+    if (st != DMRG2D_OK) return;
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      *p = nullptr;
+      st = set_error(DMRG2D_ENOMEM, "cudaMalloc(%zu) failed (pools)", bytes);
+      return;
+    }
+    D->allocs.push_back(*p);
+    *nb += (int64_t)bytes;
+  };
+  alloc((void**)&D->pL32, hL.size() * 4);
+  alloc((void**)&D->pL16, hL.size() * 2);
+  alloc((void**)&D->pR32, hR.size() * 4);
+  alloc((void**)&D->pR16, hR.size() * 2);
+  alloc((void**)&D->err, sizeof(int));
+  if (st == DMRG2D_OK) {
+    k_pool_convert<<<1024, 256, 0, s>>>(dL, D->pL32, D->pL16, (int64_t)hL.size());
+    k_pool_convert<<<1024, 256, 0, s>>>(dR, D->pR32, D->pR16, (int64_t)hR.size());
+    if (cudaMemsetAsync(D->err, 0, sizeof(int), s) != cudaSuccess)
+      st = set_error(DMRG2D_ECUDA, "memset failed");
+  }
+  if (st == DMRG2D_OK) {
+    const int rowsL = std::max(D->prL, 1), rowsR = std::max(D->prR, 1);
+    st = map2d(&D->mL[0], D->pL32, false, D->KPL, rowsL, 32, G_BM, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (st == DMRG2D_OK)
+      st = map2d(&D->mL[1], D->pL16, true, D->KPL, rowsL, 64, G_BM, CU_TENSOR_MAP_SWIZZLE_128B);
+    for (int b = 0; b < 2 && st == DMRG2D_OK; ++b) {
+      const uint32_t rows_box = b ? 256 : 128;
+      st = map2d(&D->mR[0][b], D->pR32, false, D->KPR, rowsR, 32, rows_box,
+                 CU_TENSOR_MAP_SWIZZLE_128B);
+      if (st == DMRG2D_OK)
+        st = map2d(&D->mR[1][b], D->pR16, true, D->KPR, rowsR, 64, rows_box,
+                   CU_TENSOR_MAP_SWIZZLE_128B);
+    }
+  }
+  if (st == DMRG2D_OK) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&D->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaFuncSetAttribute(hv_tc_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)G_SMEM) != cudaSuccess)
+      st = set_error(DMRG2D_ECUDA, "cannot set %zu bytes of shared memory", G_SMEM);
+  }
+  if (st == DMRG2D_OK) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = set_error(DMRG2D_ECUDA, "grouped plan: %s", cudaGetErrorString(e));
+  }
+  return st;
+}
+
+void gp_release(GroupPlan* g) {
+  GDev* D = (GDev*)g->dev;
+  if (!D) return;
+  for (void* p : D->allocs) cudaFree(p);
+  delete D;
+  g->dev = nullptr;
+}
+
+int gp_launch(const dmrg2d_ops* ops, const GroupPlan* g, const void* v, float* y, int precision,
+              int cfg, cudaStream_t s) {
+  const GDev* D = (const GDev*)g->dev;
+  if (!D) return set_error(DMRG2D_EUNSUPPORTED, "grouped plan not prepared");
+  if (cfg < 0 || cfg >= 2 * N_ORDERS) return set_error(DMRG2D_EINVAL, "bad tile config %d", cfg);
+  const bool bf = precision == DMRG2D_BF16;
+  const int b = cfg / N_ORDERS, o = cfg % N_ORDERS;
+  const int bn = b ? 256 : 128;
+  const uint32_t BK = bf ? 64 : 32;
+  GMaps maps;  // 16 KB: filled per call, copied into the launch parameters
+  maps.L = D->mL[bf ? 1 : 0];
+  maps.R = D->mR[bf ? 1 : 0][b];
+  const int elt = bf ? 2 : 4;
+  const int box_rows = bf ? 64 : 32;
+  for (int q = 0; q < g->nQ; ++q) {
+    const char* base = (const char*)v + (size_t)g->qbase[q] * elt;
+    D2_TRY(map2d(&maps.vk[q], base, bf, (uint64_t)g->qld[q], (uint64_t)g->qcols[q], BK, bn,
+                 CU_TENSOR_MAP_SWIZZLE_128B));
+    D2_TRY(map2d(&maps.vm[q], base, bf, (uint64_t)g->qld[q], (uint64_t)g->qcols[q],
+                 (uint32_t)box_rows, BK,
+                 bf ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B));
+  }
+  GParams p;
+  p.ntiles = D->ntiles[b][o];
+  p.bn = bn;
+  p.BK = (int)BK;
+  p.tiles = D->tiles[b][o];
+  p.rows = D->rows;
+  p.cols = D->cols;
+  p.k1 = D->k1;
+  p.k2 = D->k2;
+  p.qbase = D->qbase;
+  p.qld = D->qld;
+  p.y = y;
+  p.err = D->err;
+  const int fmt = bf ? 1 : 2;
+  for (int n = 0; n < 2; ++n) {
+    p.idesc1[n] = make_idesc(fmt, 0, G_BM, bn, n, 0);
+    p.idesc2[n] = make_idesc(fmt, 1, G_BM, bn, 0, n);
+  }
+  p.a2_box_rows = box_rows;
+  p.a2_boxes = G_BM / box_rows;
+  p.a2_lbo = (uint32_t)box_rows * BK * elt;
+  p.a2_kstep = bf ? 2048 : 1024;
+  p.a2_layout = bf ? 2u : 1u;
+  p.a2_sbo = bf ? 1024u : 512u;
+  p.tx_bytes = G_STAGE_A + (uint32_t)bn * 128;
+  p.bf16 = bf ? 1 : 0;
+  if (p.ntiles == 0) return DMRG2D_OK;
+  const int grid = std::min(p.ntiles, D->sms);
+  auto ev = prof_slot(ops);
+  if (ev.first) D2_CUDA(cudaEventRecord(ev.first, s));
+  hv_tc_grouped_kernel<<<grid, G_THREADS, G_SMEM, s>>>(maps, p);
+  D2_CUDA(cudaGetLastError());
+  if (ev.second) D2_CUDA(cudaEventRecord(ev.second, s));
+  return DMRG2D_OK;
+}
+
+int gp_read_error(const GroupPlan* g, int* code) {
+  *code = 0;
+  const GDev* D = g ? (const GDev*)g->dev : nullptr;
+  if (!D || !D->err) return DMRG2D_OK;
+  D2_CUDA(cudaMemcpy(code, D->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (*code) D2_CUDA(cudaMemset(D->err, 0, sizeof(int)));
+  return DMRG2D_OK;
+}
+
+}  // namespace dmrg2d

@@ -1,0 +1,70 @@
+// Work list of the grouped tensor-core H·v, shared by dense and sector-restricted
+// superblocks.  Internal header.
+//
+// The vector is a list of column-major matrices V_q (one for a dense superblock).  Rows
+// of V_q are grouped in row segments (one per block row i2, or per (i2, block sector)),
+// columns in column segments.  Output pieces ("tiles") are 128 rows of one row segment
+// by BN columns of one column segment.  A row segment's phase-1 list holds one entry per
+// H_l block that feeds it (A = operator block from the pool, B = rows of V_q); a column
+// segment's phase-2 list one entry per H_r block (A = columns of V_q, B = pool block).
+// The pool stores every distinct operator block once; an entry may use it negated.
+#pragma once
+#include <cstdint>
+#include <vector>
+
+#include "common.h"
+
+namespace dmrg2d {
+
+struct GRow {
+  int q, off, dim, dim_pad, k1b, k1e;
+};
+struct GCol {
+  int q, off, dim, k2b, k2e;
+};
+struct GK1 {
+  int a_pool, b_row, kdim, neg;
+};
+struct GK2 {
+  int a_col, b_pool, kdim, neg;
+};
+struct GTile {
+  int rs, cs, r_in, c_in;
+};
+
+// Distinct operator blocks, deduplicated up to sign.
+struct BlockPool {
+  struct Entry {
+    int rows, cols;
+    std::vector<double> a;
+    uint64_t h;
+  };
+  std::vector<Entry> ent;
+  // returns (entry index, negated?) for the rows x cols block src[i*ld + j]
+  std::pair<int, int> add(const double* src, int rows, int cols, int64_t ld);
+};
+
+struct GroupPlan {
+  int nQ = 0;
+  std::vector<long long> qbase;
+  std::vector<int> qld, qcols;
+  std::vector<GRow> rows;
+  std::vector<GCol> cols;
+  std::vector<GK1> k1;  // a_pool holds the pool ENTRY index until finalise()
+  std::vector<GK2> k2;
+  BlockPool poolL, poolR;
+  void* dev = nullptr;  // device state (grouped.cu)
+};
+
+// Lays out the pools, builds the tile lists, uploads everything.  `ops` receives the
+// device bytes.  Fails with EUNSUPPORTED when the plan does not fit the kernel.
+int gp_finalise(dmrg2d_ops* ops, GroupPlan* g, cudaStream_t s);
+void gp_release(GroupPlan* g);
+// Y(all V_q) = grouped H_l V + V H_r^T (scalar moves not included); cfg = tile config
+int gp_launch(const dmrg2d_ops* ops, const GroupPlan* g, const void* v, float* y, int precision,
+              int cfg, cudaStream_t s);
+int gp_read_error(const GroupPlan* g, int* code);
+int gp_num_configs();
+const char* gp_config_name(int cfg);
+
+}  // namespace dmrg2d

@@ -19,10 +19,14 @@
 #include <cudaTypedefs.h>
 
 #include "common.h"
+#include "grouped.h"
+#include "tc_ptx.cuh"
 
 namespace dmrg2d {
 
 namespace {
+
+using namespace tc;
 
 constexpr int TC_THREADS = 192;
 constexpr int STAGES = 4;
@@ -32,7 +36,6 @@ constexpr uint32_t STAGE_B = 32768;
 constexpr uint32_t STAGE_BYTES = STAGE_A + STAGE_B;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t ACC_COLS = 256;
-constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s: far above any legitimate wait
 constexpr size_t SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 
 struct TcParams {
@@ -55,103 +58,6 @@ struct TcParams {
   int bf16;
 };
 
-// ---- PTX wrappers ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ uint64_t gtime() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait; false on timeout or when another role has aborted
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
-  if (mbar_try(bar, parity)) return true;
-  const uint64_t t0 = gtime();
-  while (true) {
-    if (mbar_try(bar, parity)) return true;
-    if (*abort) return false;
-    if (gtime() - t0 > WAIT_NS) return false;
-  }
-}
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x,
-                                            int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
-      "%3}], [%4];" ::"r"(dst),
-      "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
-      : "memory");
-}
-// layout: 2 = 128B swizzle (16-byte atoms), 1 = 128B swizzle with 32-byte atoms (the
-// form MN-major TF32 operands need; TMA writes it with SWIZZLE_128B_ATOM_32B)
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo,
-                                          uint32_t layout = 2) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
-  d |= (uint64_t)layout << 61;
-  return d;
-}
-__device__ __forceinline__ void umma(uint32_t dt, uint64_t a, uint64_t b, uint32_t idesc,
-                                     uint32_t acc, int bf16) {
-  if (bf16)
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
-  else
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-__device__ __forceinline__ void umma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   bar)
-               : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
 struct TileCoord {
   int i2, mt, i3, nt;
 };
@@ -159,11 +65,6 @@ __device__ __forceinline__ TileCoord decode(const TcParams& p, int t) {
   const int nm = p.d * p.n_mt;
   const int mg = t % nm, ng = t / nm;  // consecutive tiles walk down one column slab of V
   return {mg / p.n_mt, mg % p.n_mt, ng / p.n_nt, ng % p.n_nt};
-}
-
-__device__ __forceinline__ void raise_abort(volatile int* abort, int* err, int code) {
-  *abort = 1;
-  atomicCAS(err, 0, code);
 }
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -379,6 +280,8 @@ k_scalar_moves(const Tin* __restrict__ v, float* __restrict__ y, const int* __re
 
 // ---- host side ----------------------------------------------------------------------------
 struct TcState {
+  bool dense_ok = false;
+  GroupPlan* plan = nullptr;  // grouped form of the same superblock (m1 % 8 == 0)
   float* HLt = nullptr;  // TF32-rounded copies of the operator blocks
   float* HRt = nullptr;
   int* err = nullptr;
@@ -428,20 +331,21 @@ __global__ void k_round_tf32(const double* __restrict__ x, float* __restrict__ o
   }
 }
 
-uint32_t make_idesc(int fmt, int a_mn, int M, int N) {
-  return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)a_mn << 15) |
-         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
 
 }  // namespace
 
-int tc_prepare(dmrg2d_ops* ops, cudaStream_t s) {
+int tc_prepare(dmrg2d_ops* ops, cudaStream_t s, const std::vector<double>& HL,
+               const std::vector<double>& HR) {
   ops->tc_ok = 0;
-  if (ops->sec) return DMRG2D_OK;  // sector-restricted superblocks: grouped path
-  const int m1 = ops->m1, m4 = ops->m4;
-  if (m1 % BM != 0 || !(m4 == 128 || m4 % 256 == 0)) return DMRG2D_OK;  // SIMT only
+  if (ops->sec) return DMRG2D_OK;  // sector-restricted superblocks build their own plan
+  const int m1 = ops->m1, m4 = ops->m4, d = ops->d;
   if (!encode_fn()) return DMRG2D_OK;
+  const bool dense_ok = m1 % BM == 0 && (m4 == 128 || m4 % 256 == 0);
+  const bool grouped_ok = m1 % 8 == 0;
+  if (!dense_ok && !grouped_ok) return DMRG2D_OK;  // CUDA-core path only
   TcState* T = new TcState();
+  ops->tc = T;
+  T->dense_ok = dense_ok;
   T->BN = m4 == 128 ? 128 : 256;
   const int64_t nL = ops->dev.nL, nR = ops->dev.nR;
   int st = DMRG2D_OK;
@@ -454,38 +358,69 @@ int tc_prepare(dmrg2d_ops* ops, cudaStream_t s) {
       ops->device_bytes += (int64_t)b;
     }
   };
-  alloc((void**)&T->HLt, sizeof(float) * nL * m1 * m1);
-  alloc((void**)&T->HRt, sizeof(float) * nR * m4 * m4);
   alloc((void**)&T->err, sizeof(int));
-  if (st == DMRG2D_OK) {
-    k_round_tf32<<<1024, 256, 0, s>>>(ops->dev.HL64, T->HLt, nL * m1 * m1);
-    k_round_tf32<<<1024, 256, 0, s>>>(ops->dev.HR64, T->HRt, nR * m4 * m4);
-    if (cudaMemsetAsync(T->err, 0, sizeof(int), s) != cudaSuccess)
-      st = set_error(DMRG2D_ECUDA, "memset failed");
+  if (st == DMRG2D_OK && cudaMemsetAsync(T->err, 0, sizeof(int), s) != cudaSuccess)
+    st = set_error(DMRG2D_ECUDA, "memset failed");
+  if (dense_ok) {
+    alloc((void**)&T->HLt, sizeof(float) * nL * m1 * m1);
+    alloc((void**)&T->HRt, sizeof(float) * nR * m4 * m4);
+    if (st == DMRG2D_OK) {
+      k_round_tf32<<<1024, 256, 0, s>>>(ops->dev.HL64, T->HLt, nL * m1 * m1);
+      k_round_tf32<<<1024, 256, 0, s>>>(ops->dev.HR64, T->HRt, nR * m4 * m4);
+    }
+    for (int b = 0; b < 2 && st == DMRG2D_OK; ++b) {
+      const bool bf = b == 1;
+      const uint32_t BK = bf ? 64 : 32;
+      const void* hl = bf ? (const void*)ops->dev.HL16 : (const void*)T->HLt;
+      const void* hr = bf ? (const void*)ops->dev.HR16 : (const void*)T->HRt;
+      st = make_map(&T->mHL[b], hl, bf, m1, nL * m1, BK, BM);
+      if (st == DMRG2D_OK) st = make_map(&T->mHR[b], hr, bf, m4, nR * m4, BK, T->BN);
+    }
+    if (st == DMRG2D_OK) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&T->sms, cudaDevAttrMultiProcessorCount, dev);
+      if (cudaFuncSetAttribute(hv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)SMEM_BYTES) != cudaSuccess)
+        st = set_error(DMRG2D_ECUDA, "cannot set %zu bytes of shared memory", SMEM_BYTES);
+    }
   }
-  for (int b = 0; b < 2 && st == DMRG2D_OK; ++b) {
-    const bool bf = b == 1;
-    const uint32_t BK = bf ? 64 : 32;
-    const void* hl = bf ? (const void*)ops->dev.HL16 : (const void*)T->HLt;
-    const void* hr = bf ? (const void*)ops->dev.HR16 : (const void*)T->HRt;
-    st = make_map(&T->mHL[b], hl, bf, m1, nL * m1, BK, BM);
-    if (st == DMRG2D_OK) st = make_map(&T->mHR[b], hr, bf, m4, nR * m4, BK, T->BN);
-  }
-  if (st == DMRG2D_OK) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&T->sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaFuncSetAttribute(hv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)SMEM_BYTES) != cudaSuccess)
-      st = set_error(DMRG2D_ECUDA, "cannot set %zu bytes of shared memory", SMEM_BYTES);
+  if (grouped_ok && st == DMRG2D_OK) {
+    // the dense superblock as one sector: row segment per i2, column segment per i3,
+    // operator blocks stored once up to sign
+    GroupPlan* g = new GroupPlan();
+    T->plan = g;
+    g->nQ = 1;
+    g->qbase = {0};
+    g->qld = {(int)ops->ld};
+    g->qcols = {d * m4};
+    for (int i2 = 0; i2 < d; ++i2) {
+      GRow r{0, m1 * i2, m1, m1, (int)g->k1.size(), 0};
+      for (int e = ops->hLptr[i2]; e < ops->hLptr[i2 + 1]; ++e) {
+        auto pe = g->poolL.add(HL.data() + (size_t)e * m1 * m1, m1, m1, m1);
+        g->k1.push_back({pe.first, m1 * ops->hLcol[e], m1, pe.second});
+      }
+      r.k1e = (int)g->k1.size();
+      g->rows.push_back(r);
+    }
+    for (int i3 = 0; i3 < d; ++i3) {
+      GCol c{0, m4 * i3, m4, (int)g->k2.size(), 0};
+      for (int e = ops->hRptr[i3]; e < ops->hRptr[i3 + 1]; ++e) {
+        auto pe = g->poolR.add(HR.data() + (size_t)e * m4 * m4, m4, m4, m4);
+        g->k2.push_back({m4 * ops->hRcol[e], pe.first, m4, pe.second});
+      }
+      c.k2e = (int)g->k2.size();
+      g->cols.push_back(c);
+    }
+    st = gp_finalise(ops, g, s);
   }
   if (st == DMRG2D_OK) {
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) st = set_error(DMRG2D_ECUDA, "tc_prepare: %s", cudaGetErrorString(e));
   }
-  ops->tc = T;
   if (st != DMRG2D_OK) return st;
   ops->tc_ok = 1;
+  for (int p = 0; p < 4; ++p) ops->tc_cfg[p] = dense_ok ? -1 : 5;
   return DMRG2D_OK;
 }
 
@@ -495,14 +430,16 @@ void tc_release(dmrg2d_ops* ops) {
   if (T->HLt) cudaFree(T->HLt);
   if (T->HRt) cudaFree(T->HRt);
   if (T->err) cudaFree(T->err);
+  if (T->plan) {
+    gp_release(T->plan);
+    delete T->plan;
+  }
   delete T;
   ops->tc = nullptr;
 }
 
-int launch_hv_tc(const dmrg2d_ops* ops, const void* v, float* y, int precision, cudaStream_t s) {
-  TcState* T = (TcState*)ops->tc;
-  if (!T || !ops->tc_ok) return set_error(DMRG2D_EUNSUPPORTED, "tensor-core path not prepared");
-  const bool bf = precision == DMRG2D_BF16;
+static int launch_dense_kernel(const dmrg2d_ops* ops, const TcState* T, const void* v, float* y,
+                               bool bf, cudaStream_t s) {
   const int b = bf ? 1 : 0;
   const int m1 = ops->m1, m4 = ops->m4, d = ops->d;
   const uint32_t BK = bf ? 64 : 32;
@@ -548,6 +485,29 @@ int launch_hv_tc(const dmrg2d_ops* ops, const void* v, float* y, int precision, 
   hv_tc_kernel<<<grid, TC_THREADS, SMEM_BYTES, s>>>(T->mHL[b], T->mHR[b], mVk, mVm, p);
   D2_CUDA(cudaGetLastError());
   if (ev.second) D2_CUDA(cudaEventRecord(ev.second, s));
+  return DMRG2D_OK;
+}
+
+// H_l V + V H_r^T only (no scalar moves), with an explicit kernel choice
+int tc_gemm(const dmrg2d_ops* ops, const void* v, float* y, int precision, int cfg,
+            cudaStream_t s) {
+  const TcState* T = (const TcState*)ops->tc;
+  if (!T) return set_error(DMRG2D_EUNSUPPORTED, "tensor-core path not prepared");
+  if (cfg < 0) {
+    if (!T->dense_ok) return set_error(DMRG2D_EUNSUPPORTED, "dense kernel unsupported here");
+    return launch_dense_kernel(ops, T, v, y, precision == DMRG2D_BF16, s);
+  }
+  if (!T->plan) return set_error(DMRG2D_EUNSUPPORTED, "grouped kernel unsupported here");
+  return gp_launch(ops, T->plan, v, y, precision, cfg, s);
+}
+
+int launch_hv_tc(const dmrg2d_ops* ops, const void* v, float* y, int precision, cudaStream_t s) {
+  if (ops->sec) return sec_apply(ops, v, y, precision, s);
+  if (!ops->tc || !ops->tc_ok)
+    return set_error(DMRG2D_EUNSUPPORTED, "tensor-core path not prepared");
+  const bool bf = precision == DMRG2D_BF16;
+  const int m1 = ops->m1, m4 = ops->m4, d = ops->d;
+  D2_TRY(tc_gemm(ops, v, y, precision, ops->tc_cfg[precision], s));
   dim3 g2(d * d, (m4 + 7) / 8);
   if (bf)
     k_scalar_moves<__nv_bfloat16><<<g2, 256, 0, s>>>((const __nv_bfloat16*)v, y, ops->dev.Cptr,
@@ -561,12 +521,127 @@ int launch_hv_tc(const dmrg2d_ops* ops, const void* v, float* y, int precision, 
 }
 
 int tc_read_error(const dmrg2d_ops* ops, int* code) {
-  TcState* T = (TcState*)ops->tc;
   *code = 0;
-  if (!T || !T->err) return DMRG2D_OK;
-  D2_CUDA(cudaMemcpy(code, T->err, sizeof(int), cudaMemcpyDeviceToHost));
-  if (*code) D2_CUDA(cudaMemset(T->err, 0, sizeof(int)));
+  const TcState* T = (const TcState*)ops->tc;
+  if (T && T->err) {
+    D2_CUDA(cudaMemcpy(code, T->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (*code) D2_CUDA(cudaMemset(T->err, 0, sizeof(int)));
+  }
+  int c2 = 0;
+  if (T && T->plan) D2_TRY(gp_read_error(T->plan, &c2));
+  if (!*code) *code = c2;
+  int c3 = 0;
+  D2_TRY(sec_read_error(ops, &c3));
+  if (!*code) *code = c3;
   return DMRG2D_OK;
 }
 
 }  // namespace dmrg2d
+
+// ---- tile-configuration autotuner ---------------------------------------------------------
+namespace dmrg2d {
+
+// candidate index: 0 = dense kernel, 1 + c = grouped kernel configuration c
+static bool tc_candidate_ok(const dmrg2d_ops* ops, int idx) {
+  if (idx == 0) {
+    const TcState* T = (const TcState*)ops->tc;
+    return !ops->sec && T && T->dense_ok;
+  }
+  if (idx < 1 || idx > gp_num_configs()) return false;
+  if (ops->sec) return ops->tc_ok != 0;
+  const TcState* T = (const TcState*)ops->tc;
+  return T && T->plan;
+}
+
+static int tc_run_candidate(const dmrg2d_ops* ops, const void* v, float* y, int prec, int idx,
+                            cudaStream_t s) {
+  if (ops->sec) return sec_tc_gemm(ops, v, y, prec, idx - 1, s);
+  return tc_gemm(ops, v, y, prec, idx == 0 ? -1 : idx - 1, s);
+}
+
+}  // namespace dmrg2d
+
+using namespace dmrg2d;
+
+extern "C" const char* dmrg2d_tile_config_name(int index) {
+  if (index == 0) return "dense kernel 128x256 (column-slab raster)";
+  return gp_config_name(index - 1);
+}
+
+extern "C" int dmrg2d_set_tile_config(dmrg2d_ops* ops, int precision, int index) {
+  if (!ops || (precision != DMRG2D_TF32 && precision != DMRG2D_BF16))
+    return set_error(DMRG2D_EINVAL, "set_tile_config: bad argument");
+  if (!tc_candidate_ok(ops, index))
+    return set_error(DMRG2D_EUNSUPPORTED, "tile configuration %d not available here", index);
+  ops->tc_cfg[precision] = index == 0 ? -1 : index - 1;
+  return DMRG2D_OK;
+}
+
+extern "C" int dmrg2d_autotune(dmrg2d_ops* ops, int precision, int* best, double* ms, int n_ms,
+                               void* stream) {
+  if (!ops || (precision != DMRG2D_TF32 && precision != DMRG2D_BF16))
+    return set_error(DMRG2D_EINVAL, "autotune: bad argument");
+  if (!ops->tc_ok) return set_error(DMRG2D_EUNSUPPORTED, "no tensor-core path for these shapes");
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool bf = precision == DMRG2D_BF16;
+  const size_t n = (size_t)ops->n_vec;
+  void* v = nullptr;
+  float* y = nullptr;
+  if (cudaMalloc(&v, n * (bf ? 2 : 4)) != cudaSuccess)
+    return set_error(DMRG2D_ENOMEM, "autotune: cudaMalloc failed");
+  if (cudaMalloc((void**)&y, n * 4) != cudaSuccess) {
+    cudaFree(v);
+    return set_error(DMRG2D_ENOMEM, "autotune: cudaMalloc failed");
+  }
+  struct Free {
+    void* a;
+    void* b;
+    ~Free() {
+      cudaFree(a);
+      cudaFree(b);
+    }
+  } fr{v, y};
+  D2_CUDA(cudaMemsetAsync(v, 0x3C, n * (bf ? 2 : 4), s));  // small positive values
+  cudaEvent_t e0, e1;
+  D2_CUDA(cudaEventCreate(&e0));
+  D2_CUDA(cudaEventCreate(&e1));
+  int chosen = -1;
+  double tbest = 1e300;
+  const int ncand = 1 + gp_num_configs();
+  int st = DMRG2D_OK;
+  for (int c = 0; c < ncand && st == DMRG2D_OK; ++c) {
+    double t = -1.0;
+    if (tc_candidate_ok(ops, c)) {
+      st = tc_run_candidate(ops, v, y, precision, c, s);  // warm-up
+      float tmin = 1e30f;
+      for (int r = 0; r < 3 && st == DMRG2D_OK; ++r) {
+        cudaEventRecord(e0, s);
+        st = tc_run_candidate(ops, v, y, precision, c, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+          st = set_error(DMRG2D_ECUDA, "autotune: launch failed");
+          break;
+        }
+        float x = 0.f;
+        cudaEventElapsedTime(&x, e0, e1);
+        tmin = x < tmin ? x : tmin;
+      }
+      t = tmin;
+      if (st == DMRG2D_OK && t < tbest) {
+        tbest = t;
+        chosen = c;
+      }
+    }
+    if (ms && c < n_ms) ms[c] = t;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != DMRG2D_OK) return st;
+  int derr = 0;
+  D2_TRY(tc_read_error(ops, &derr));
+  if (derr) return set_error(DMRG2D_ETIMEOUT, "tensor-core kernel gave up waiting (site %d)", derr);
+  if (chosen < 0) return set_error(DMRG2D_EUNSUPPORTED, "no tile configuration applies");
+  ops->tc_cfg[precision] = chosen == 0 ? -1 : chosen - 1;
+  if (best) *best = chosen;
+  return DMRG2D_OK;
+}

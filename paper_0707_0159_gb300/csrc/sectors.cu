@@ -23,6 +23,7 @@
 #include <map>
 
 #include "common.h"
+#include "grouped.h"
 
 namespace dmrg2d {
 
@@ -116,6 +117,8 @@ struct SecState {
   long long* d_pad_off = nullptr;
   int* d_pad_cnt = nullptr;
   std::vector<void*> allocs;
+  GroupPlan plan;  // tensor-core form of the same work (pools deduplicated up to sign)
+  bool gp_ok = false;
 
   SecParams params() const {
     return {d_qbase, d_qld, d_rseg, d_cseg, d_k1, d_k2, d_tiles, d_mdst, d_msrc, d_mitems};
@@ -389,6 +392,11 @@ int sec_build(dmrg2d_ops* ops, const dmrg2d_block* L, const dmrg2d_block* R, con
         for (int k = 0; k < dim1[ap]; ++k)
           mx = std::max(mx, std::fabs(blk[(size_t)(off1[a] + i) * m1 + off1[ap] + k]));
       if (mx == 0.0) continue;  // structurally zero sub-block: no work
+      {
+        const auto pe = S->plan.poolL.add(blk + (size_t)off1[a] * m1 + off1[ap], dim1[a],
+                                          dim1[ap], m1);
+        S->plan.k1.push_back({pe.first, S->rseg[it->second].off, dim1[ap], pe.second});
+      }
       K1D k;
       k.a_off = (long long)Lc.size();
       k.a_pool = poolL;
@@ -419,6 +427,11 @@ int sec_build(dmrg2d_ops* ops, const dmrg2d_block* L, const dmrg2d_block* R, con
         for (int k = 0; k < dim4[bp]; ++k)
           mx = std::max(mx, std::fabs(blk[(size_t)(off4[b] + i) * m4 + off4[bp] + k]));
       if (mx == 0.0) continue;
+      {
+        const auto pe = S->plan.poolR.add(blk + (size_t)off4[b] * m4 + off4[bp], dim4[b],
+                                          dim4[bp], m4);
+        S->plan.k2.push_back({S->cseg[it->second].off, pe.first, dim4[bp], pe.second});
+      }
       K2D k;
       k.b_off = (long long)Rc.size();
       k.b_pool = poolR;
@@ -495,12 +508,33 @@ int sec_build(dmrg2d_ops* ops, const dmrg2d_block* L, const dmrg2d_block* R, con
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) st = set_error(DMRG2D_ECUDA, "sector upload: %s", cudaGetErrorString(e));
   }
+  // ---- grouped tensor-core plan over the same segments ----
+  if (st == DMRG2D_OK) {
+    GroupPlan& g = S->plan;
+    g.nQ = S->nQ;
+    g.qbase = S->qbase;
+    g.qld = S->qld;
+    g.qcols = S->qcols;
+    for (const RowSegD& r : S->rseg) g.rows.push_back({r.q, r.off, r.dim, r.dim_pad, r.k1b, r.k1e});
+    for (const ColSegD& c : S->cseg) g.cols.push_back({c.q, c.off, c.dim, c.k2b, c.k2e});
+    const int gs = gp_finalise(ops, &g, s);
+    if (gs == DMRG2D_OK) {
+      S->gp_ok = true;
+      ops->tc_ok = 1;
+      for (int p = 0; p < 4; ++p) ops->tc_cfg[p] = 5;  // 128 x 256 longest-first
+    } else if (gs == DMRG2D_EUNSUPPORTED) {
+      clear_error();  // CUDA-core path only for this sector structure
+    } else {
+      st = gs;
+    }
+  }
   return st;
 }
 
 void sec_release(dmrg2d_ops* ops) {
   SecState* S = (SecState*)ops->sec;
   if (!S) return;
+  gp_release(&S->plan);
   for (void* p : S->allocs) cudaFree(p);
   delete S;
   ops->sec = nullptr;
@@ -523,9 +557,18 @@ int sec_apply(const dmrg2d_ops* ops, const void* v, void* y, int precision, cuda
                                                        S->d_R32, p);
     if (ev.second) D2_CUDA(cudaEventRecord(ev.second, s));
     if (nm) k_sec_moves<float, float><<<nm, 256, 0, s>>>((const float*)v, (float*)y, p, 0);
+  } else if ((precision == DMRG2D_TF32 || precision == DMRG2D_BF16) && S->gp_ok) {
+    D2_TRY(gp_launch(ops, &S->plan, v, (float*)y, precision, ops->tc_cfg[precision], s));
+    if (nm) {
+      if (precision == DMRG2D_BF16)
+        k_sec_moves<__nv_bfloat16, float><<<nm, 256, 0, s>>>((const __nv_bfloat16*)v, (float*)y,
+                                                            p, 0);
+      else
+        k_sec_moves<float, float><<<nm, 256, 0, s>>>((const float*)v, (float*)y, p, 0);
+    }
   } else {
     return set_error(DMRG2D_EUNSUPPORTED,
-                     "sector-restricted H·v: precision %d not built (FP64, FP32)", precision);
+                     "sector-restricted H·v: precision %d not available here", precision);
   }
   D2_CUDA(cudaGetLastError());
   return DMRG2D_OK;
@@ -551,6 +594,20 @@ int sec_dense_index(const dmrg2d_ops* ops, int64_t* out) {
         }
     }
   return DMRG2D_OK;
+}
+
+int sec_read_error(const dmrg2d_ops* ops, int* code) {
+  *code = 0;
+  const SecState* S = (const SecState*)ops->sec;
+  if (!S || !S->gp_ok) return DMRG2D_OK;
+  return gp_read_error(&S->plan, code);
+}
+
+int sec_tc_gemm(const dmrg2d_ops* ops, const void* v, float* y, int precision, int cfg,
+                cudaStream_t s) {
+  const SecState* S = (const SecState*)ops->sec;
+  if (!S || !S->gp_ok) return set_error(DMRG2D_EUNSUPPORTED, "no grouped plan");
+  return gp_launch(ops, &S->plan, v, y, precision, cfg, s);
 }
 
 int sec_count(const dmrg2d_ops* ops) {

@@ -71,6 +71,10 @@ SIGNATURES = {
                                                 C.POINTER(C.c_double), C.POINTER(SolverStats),
                                                 C.c_void_p]),
     "dmrg2d_default_solver_opts": (None, [C.POINTER(SolverOpts)]),
+    "dmrg2d_autotune": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_void_p, C.c_int,
+                                  C.c_void_p]),
+    "dmrg2d_set_tile_config": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "dmrg2d_tile_config_name": (C.c_char_p, [C.c_int]),
     "dmrg2d_free_ops": (None, [C.c_void_p]),
     "dmrg2d_check_device": (C.c_int, [C.c_void_p]),
     "dmrg2d_profile_start": (C.c_int, [C.c_void_p, C.c_int]),
@@ -219,6 +223,28 @@ def profile_stop(ops: Ops):
     ms, n = C.c_double(), C.c_int()
     _check(lib().dmrg2d_profile_stop(ops.ptr, C.byref(ms), C.byref(n)))
     return ms.value, n.value
+
+
+N_TILE_CONFIGS = 7
+
+
+def autotune(ops: Ops, precision, stream=None):
+    """Time every tensor-core tile configuration; keep the fastest. Returns (best, ms list)."""
+    precision = PRECISION.get(precision, precision)
+    ms = (C.c_double * N_TILE_CONFIGS)()
+    best = C.c_int()
+    _check(lib().dmrg2d_autotune(ops.ptr, int(precision), C.byref(best), ms, N_TILE_CONFIGS,
+                                 _stream(stream)))
+    return best.value, list(ms)
+
+
+def set_tile_config(ops: Ops, precision, index: int):
+    precision = PRECISION.get(precision, precision)
+    _check(lib().dmrg2d_set_tile_config(ops.ptr, int(precision), int(index)))
+
+
+def tile_config_name(index: int) -> str:
+    return lib().dmrg2d_tile_config_name(int(index)).decode()
 
 
 def default_solver_opts() -> dict:

@@ -1,0 +1,121 @@
+"""Grouped tensor-core H·v (work list over row x column segments) against the oracle.
+
+Covers every tile configuration on dense superblocks whose block sizes the dense
+kernel cannot take (m not a multiple of 128), the dense kernel against the grouped
+one on the same superblock, sector-restricted superblocks in TF32 and BF16, the
+autotuner, and the sign-deduplicated operator pool (H_l/H_r blocks stored once).
+Tolerances as for the dense tensor-core tests: TF32 <= 1e-3, BF16 <= 6e-3.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle.superblock import Superblock  # noqa: E402
+from paper_0707_0159_gb300 import dmrg2d, synth  # noqa: E402
+
+from test_gpu_sectors import packed_map  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+TOL = {dmrg2d.TF32: 1e-3, dmrg2d.BF16: 6e-3}
+
+
+def make(kind, n_legs, m1, m4, seed=0):
+    mdl = synth.model(kind, n_legs, J_leg=0.8, J_rung=1.1, t=1.0, U=6.0)
+    mk = synth.heisenberg_block if kind == "heisenberg" else synth.hubbard_block
+    return mdl, mk(m1, n_legs, seed + 1), mk(m4, n_legs, seed + 2)
+
+
+def run(ops, v, prec):
+    x = torch.from_numpy(v).cuda()
+    x = x.float() if prec == dmrg2d.TF32 else x.bfloat16()
+    y = torch.full((x.numel(),), 3.0, dtype=torch.float32, device="cuda")
+    dmrg2d.apply_H(ops, x, y, prec)
+    torch.cuda.synchronize()
+    dmrg2d.check_device(ops)
+    return y.double().cpu().numpy()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("case", [("hubbard", 2, 72, 40), ("heisenberg", 3, 136, 264)])
+@pytest.mark.parametrize("prec", [dmrg2d.TF32, dmrg2d.BF16])
+def test_grouped_dense_every_config(case, prec):
+    mdl, left, right = make(*case)
+    ops = dmrg2d.build_ops(mdl, left, right)
+    assert ops.info["tc_ok"] == 1
+    sb = Superblock(mdl, left, right)
+    v = synth.start_vector(sb.n_vec, 3)
+    ref = sb.apply(v)
+    with pytest.raises(dmrg2d.Dmrg2dError):
+        dmrg2d.set_tile_config(ops, prec, 0)   # the dense kernel does not take these shapes
+    for cfg in range(1, dmrg2d.N_TILE_CONFIGS):
+        dmrg2d.set_tile_config(ops, prec, cfg)
+        err = rel(run(ops, v, prec), ref)
+        assert err <= TOL[prec], (cfg, dmrg2d.tile_config_name(cfg), err)
+
+
+@pytest.mark.parametrize("prec", [dmrg2d.TF32, dmrg2d.BF16])
+def test_dense_and_grouped_kernels_agree(prec):
+    mdl, left, right = make("hubbard", 2, 128, 256)
+    ops = dmrg2d.build_ops(mdl, left, right)
+    sb = Superblock(mdl, left, right)
+    v = synth.start_vector(sb.n_vec, 4)
+    ref = sb.apply(v)
+    out = {}
+    for cfg in (0, 1, 4):
+        dmrg2d.set_tile_config(ops, prec, cfg)
+        out[cfg] = run(ops, v, prec)
+        assert rel(out[cfg], ref) <= TOL[prec]
+    # same operands, same K order within a piece: the kernels agree far below the tolerance
+    assert rel(out[1], out[0]) <= 1e-6 and rel(out[4], out[0]) <= 1e-6
+
+
+CASES = {
+    "heisenberg_4leg": lambda: synth.workload_ladder4_heisenberg_sectors(m=48, block_sites=8),
+    "hubbard_3leg": lambda: synth.workload_ladder3_hubbard_sectors(m=25, block_sites=6,
+                                                                    n_up=6, n_dn=6),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("prec", [dmrg2d.TF32, dmrg2d.BF16])
+def test_sector_tensor_core_matches_oracle(name, prec):
+    mdl, left, right, target = CASES[name]()
+    sb = Superblock(mdl, left, right)
+    ops = dmrg2d.build_ops(mdl, left, right, target=target)
+    assert ops.info["tc_ok"] == 1
+    pmap = packed_map(sb, target)
+    valid = pmap >= 0
+    vp = np.where(valid, synth.start_vector(len(pmap), 31), 0.0)
+    vd = np.zeros(sb.n_vec)
+    vd[pmap[valid]] = vp[valid]
+    yd = sb.apply(vd)
+    ref = np.zeros(len(pmap))
+    ref[valid] = yd[pmap[valid]]
+    for cfg in range(1, dmrg2d.N_TILE_CONFIGS):
+        dmrg2d.set_tile_config(ops, prec, cfg)
+        got = run(ops, vp, prec)
+        assert np.all(got[~valid] == 0.0)
+        assert rel(got, ref) <= TOL[prec], (cfg, rel(got, ref))
+
+
+@pytest.mark.parametrize("prec", [dmrg2d.TF32, dmrg2d.BF16])
+def test_autotune_picks_a_working_config(prec):
+    mdl, left, right, target = CASES["heisenberg_4leg"]()
+    ops = dmrg2d.build_ops(mdl, left, right, target=target)
+    best, ms = dmrg2d.autotune(ops, prec)
+    assert 1 <= best < dmrg2d.N_TILE_CONFIGS
+    assert ms[0] == -1.0 and all(t > 0 for t in ms[1:])
+    assert ms[best] == min(t for t in ms if t > 0)
+    sb = Superblock(mdl, left, right)
+    pmap = packed_map(sb, target)
+    valid = pmap >= 0
+    vp = np.where(valid, synth.start_vector(len(pmap), 5), 0.0)
+    vd = np.zeros(sb.n_vec)
+    vd[pmap[valid]] = vp[valid]
+    ref = np.zeros(len(pmap))
+    ref[valid] = sb.apply(vd)[pmap[valid]]
+    assert rel(run(ops, vp, prec), ref) <= TOL[prec]
