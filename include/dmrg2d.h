@@ -244,6 +244,72 @@ int dmrg2d_profile_stop(dmrg2d_ops* ops, double* total_ms, int* launches);
  * Returns OK, ETIMEOUT (flag found and cleared) or ECUDA. */
 int dmrg2d_check_device(const dmrg2d_ops* ops);
 
+/* Diagonal of H in the vector layout of `ops` (dense or packed; 0 on padding rows):
+ * H(i1 i2 i3 i4; same) = H_l diagonal + H_r diagonal + H_c diagonal (Eq. (dec)).
+ * out: caller-owned device double[info.n_vec].  Synchronises the stream. */
+int dmrg2d_diagonal(const dmrg2d_ops* ops, double* out, void* stream);
+
+/* ---- Davidson with a diagonal or learned preconditioner ----------------------------
+ * Lowest eigenpair by Davidson: expand an orthonormal basis V by the preconditioned
+ * residual t = M(theta) r, Rayleigh-Ritz on V^T H V, restart from the Ritz vector when
+ * V holds max_subspace vectors.  Preconditioners: NONE (t = r), JACOBI
+ * (t_i = r_i / (theta - D_i), D = diag H), MLP (t_i = (r_i / s_D) g(x_i), g a trained
+ * dmrg2d_mlp, see below).  With precision TF32/BF16 the basis images H V use the
+ * low-precision H~·v; refine = 1 then finishes with the FP64 outer loop of
+ * dmrg2d_lanczos_ground (tolerance refine_tol, inner_iter CG steps, outer_max steps).
+ * Stops when ||H x - theta x|| <= tol * |theta|.  log_cap > 0 records the first
+ * log_cap Ritz vectors (log_x) and residuals (log_r) — caller-owned device arrays of
+ * log_cap * n_vec doubles, either may be NULL — and theta values (log_theta, host). */
+enum { DMRG2D_PRECOND_NONE = 0, DMRG2D_PRECOND_JACOBI = 1, DMRG2D_PRECOND_MLP = 2 };
+typedef struct dmrg2d_mlp dmrg2d_mlp;
+typedef struct dmrg2d_davidson_opts {
+  int max_iter;
+  int max_subspace;     /* 4..48                                                     */
+  double tol;
+  int precision;
+  int refine;
+  int precond;
+  const dmrg2d_mlp* mlp;
+  int inner_iter, outer_max;
+  double refine_tol;
+  int log_cap;
+  double* log_x;
+  double* log_r;
+  double* log_theta;
+} dmrg2d_davidson_opts;
+void dmrg2d_default_davidson_opts(dmrg2d_davidson_opts* opts);
+int dmrg2d_davidson_ground(const dmrg2d_ops* ops, const dmrg2d_davidson_opts* opts,
+                           double* x_inout, double* energy_out, dmrg2d_solver_stats* stats,
+                           void* stream);
+
+/* ---- the learned preconditioner's network -------------------------------------------
+ * A pointwise MLP, 4 inputs -> hidden (tanh) -> hidden (tanh) -> 1, FP32 parameters in
+ * one device array: W1[hidden][4], b1[hidden], W2[hidden][hidden], b2[hidden],
+ * w3[hidden], b3.  Inputs of component i (d_i = (D_i - theta)/s_D, s_D the RMS of
+ * D - theta): clamp(d_i, +-8), clamp(1/d_i, +-16)/16, clamp of the sector's mean
+ * (D - theta)/s_D, log(sector size)/16.  Trained on weighted least squares
+ *   L = 1/(2B) sum_b (w_b g(X_b) - T_b)^2
+ * with batches built by dmrg2d_mlp_make_batch from a logged Davidson step (x_k, r_k,
+ * theta_k) and the converged vector x_f: w = r_i/(s_D s_t), T = alpha delta_i / s_t,
+ * delta = x_f - (x_k . x_f) x_k, alpha = (delta . t_J)/(delta . delta), t_J the Jacobi
+ * correction and s_t its RMS.  All arrays are device arrays unless noted; X is B x 4.
+ * The Davidson solver evaluates g exactly on 1024 values of d per sector each step and
+ * interpolates linearly in between. */
+int dmrg2d_mlp_create(int hidden, uint64_t seed, dmrg2d_mlp** out);
+void dmrg2d_mlp_free(dmrg2d_mlp* mlp);
+int dmrg2d_mlp_num_params(const dmrg2d_mlp* mlp);
+int dmrg2d_mlp_get_params(const dmrg2d_mlp* mlp, float* host_params);
+int dmrg2d_mlp_set_params(dmrg2d_mlp* mlp, const float* host_params);  /* resets Adam */
+int dmrg2d_mlp_forward(dmrg2d_mlp* mlp, const float* X, float* Y, int B, void* stream);
+int dmrg2d_mlp_loss_grad(dmrg2d_mlp* mlp, const float* X, const float* w, const float* T, int B,
+                         float* grad, float* loss_host, void* stream);
+int dmrg2d_mlp_train_step(dmrg2d_mlp* mlp, const float* X, const float* w, const float* T, int B,
+                          float lr, float* loss_host, void* stream);  /* one Adam step */
+int dmrg2d_mlp_make_batch(const dmrg2d_ops* ops, const double* x_k, const double* r_k,
+                          double theta, const double* x_final, const double* D,
+                          const int64_t* idx, int B, float* X, float* w, float* T,
+                          void* stream);
+
 void dmrg2d_free_ops(dmrg2d_ops* ops);
 
 /* Thread-local text of the last error of this thread ("" if none). */

@@ -386,6 +386,7 @@ extern "C" int dmrg2d_build_ops(const dmrg2d_model* model, const dmrg2d_block* l
     delete ops;
     return st;
   }
+  diag_pieces(ops, HL, HR);
   if (target) {  // sector-restricted: pack the sub-blocks, skip the dense uploads
     st = sec_build(ops, left, right, target, HL, HR, s);
     if (st != DMRG2D_OK) {

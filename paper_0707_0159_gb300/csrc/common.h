@@ -73,6 +73,8 @@ struct dmrg2d_ops {
   std::vector<int> hLptr, hLcol, hRptr, hRcol, hCptr, hCsrc;
   std::vector<double> hCval;
   std::vector<int> hqc;  // column quantum numbers, (N_up, N_dn) per column state
+  // diagonal of H: H_l diagonal per (i1 + m1 i2), H_r per (i4 + m4 i3), H_c per (i2 + d i3)
+  std::vector<double> hdL, hdR, hdC;
   // sector-restricted operation (NULL for the dense superblock), opaque here
   void* sec = nullptr;
   // tensor-core path state (tensor maps of the operator blocks), opaque here
@@ -118,6 +120,30 @@ int sec_dense_index(const dmrg2d_ops* ops, int64_t* out);
 int sec_count(const dmrg2d_ops* ops);
 int sec_tc_gemm(const dmrg2d_ops* ops, const void* v, float* y, int precision, int cfg,
                 cudaStream_t s);
+
+int sec_diag_tables(const dmrg2d_ops* ops, std::vector<long long>& qbase, std::vector<int>& qld,
+                    std::vector<int>& qcols, std::vector<double>& rowD, std::vector<int>& rowI2,
+                    std::vector<double>& colD, std::vector<int>& colI3);
+
+// diag.cu
+void diag_pieces(dmrg2d_ops* ops, const std::vector<double>& HL, const std::vector<double>& HR);
+int diag_apply(const dmrg2d_ops* ops, double* out, cudaStream_t s);
+
+// mlp.cu: learned Davidson preconditioner state
+struct MlpPrecond {
+  int nq = 0;
+  std::vector<double> mean, dmin, dmax, count, hqp;
+  double meanD = 0.0, meanD2 = 0.0;
+  long long* qstart = nullptr;
+  double* qp = nullptr;
+  float* Xg = nullptr;
+  float* table = nullptr;
+};
+int mlp_precond_setup(const dmrg2d_mlp* M, const dmrg2d_ops* ops, const double* D, MlpPrecond* P,
+                      cudaStream_t s);
+int mlp_precond_apply(const dmrg2d_mlp* M, MlpPrecond* P, const double* r, const double* D,
+                      double theta, double* t, int64_t n, cudaStream_t s);
+void mlp_precond_release(MlpPrecond* P);
 
 // vector kernels used by the solvers (solver.cu)
 int convert_f64_to(const double* x, void* out, int precision, int64_t n, cudaStream_t s);

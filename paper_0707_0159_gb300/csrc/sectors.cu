@@ -596,6 +596,44 @@ int sec_dense_index(const dmrg2d_ops* ops, int64_t* out) {
   return DMRG2D_OK;
 }
 
+int sec_diag_tables(const dmrg2d_ops* ops, std::vector<long long>& qbase, std::vector<int>& qld,
+                    std::vector<int>& qcols, std::vector<double>& rowD, std::vector<int>& rowI2,
+                    std::vector<double>& colD, std::vector<int>& colI3) {
+  const SecState* S = (const SecState*)ops->sec;
+  if (!S) return set_error(DMRG2D_EINVAL, "not a sector-restricted ops object");
+  const int m1 = ops->m1, m4 = ops->m4;
+  qbase = S->qbase;
+  qld = S->qld;
+  qcols = S->qcols;
+  for (int q = 0; q < S->nQ; ++q) {
+    const size_t r0 = rowD.size();
+    rowD.resize(r0 + S->qld[q], 0.0);
+    rowI2.resize(r0 + S->qld[q], -1);  // padding rows stay -1
+    for (size_t r = 0; r < S->rseg.size(); ++r) {
+      const RowSegD& rs = S->rseg[r];
+      if (rs.q != q) continue;
+      const int i2 = S->rs_i2[r], a0 = S->a_first[S->rs_a[r]];
+      for (int i = 0; i < rs.dim; ++i) {
+        rowD[r0 + rs.off + i] = ops->hdL[(size_t)(a0 + i) + (size_t)m1 * i2];
+        rowI2[r0 + rs.off + i] = i2;
+      }
+    }
+    const size_t c0 = colD.size();
+    colD.resize(c0 + S->qcols[q], 0.0);
+    colI3.resize(c0 + S->qcols[q], 0);
+    for (size_t c = 0; c < S->cseg.size(); ++c) {
+      const ColSegD& cs = S->cseg[c];
+      if (cs.q != q) continue;
+      const int i3 = S->cs_i3[c], b0 = S->b_first[S->cs_b[c]];
+      for (int j = 0; j < cs.dim; ++j) {
+        colD[c0 + cs.off + j] = ops->hdR[(size_t)(b0 + j) + (size_t)m4 * i3];
+        colI3[c0 + cs.off + j] = i3;
+      }
+    }
+  }
+  return DMRG2D_OK;
+}
+
 int sec_read_error(const dmrg2d_ops* ops, int* code) {
   *code = 0;
   const SecState* S = (const SecState*)ops->sec;

@@ -537,16 +537,24 @@ int convert_f64_to(const double* x, void* out, int precision, int64_t n, cudaStr
 }
 
 // Mixed precision: low-precision Lanczos start, FP64 outer Rayleigh-Ritz + CG corrections.
+static int mixed_outer(Ctx& C, const dmrg2d_solver_opts* o, double* x, double* energy);
+
 static int mixed_solve(Ctx& C, const dmrg2d_solver_opts* o, double* x, double* energy) {
-  const int64_t n = C.n;
-  const int prec = o->precision;
   // 1. low-precision Lanczos for the start vector
   double th0 = 0, r0 = 0;
   int it0 = 0;
-  int st = lanczos(C, prec, x, o->inner_iter, o->inner_iter + 1, 1e-6, 0, 5, &th0, &r0, &it0);
+  int st = lanczos(C, o->precision, x, o->inner_iter, o->inner_iter + 1, 1e-6, 0, 5, &th0, &r0,
+                   &it0);
   if (st != DMRG2D_OK && st != DMRG2D_ENOCONV) return st;
   C.st->iters += it0;
-  // 2. FP64 outer loop on a small subspace
+  // 2. FP64 outer loop
+  return mixed_outer(C, o, x, energy);
+}
+
+// FP64 outer loop on a small subspace, starting from x.
+static int mixed_outer(Ctx& C, const dmrg2d_solver_opts* o, double* x, double* energy) {
+  const int64_t n = C.n;
+  const int prec = o->precision;
   const int smax = 6;
   DevBuf Ub, Wb, xb, hxb, rb, tb, pb, qb, Gb, cb, scb;
   D2_TRY(dmalloc(Ub, sizeof(double) * (size_t)smax * n));
@@ -893,6 +901,218 @@ extern "C" int dmrg2d_lanczos_ground_noalloc(const dmrg2d_ops* ops, const dmrg2d
     st = set_error(DMRG2D_ECUDA, "solver: %s", cudaGetErrorString(e));
   local.iters = iters;
   local.resid = resid;
+  local.elapsed_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  *energy_out = energy;
+  if (stats) *stats = local;
+  return st;
+}
+
+// ---- Davidson with a diagonal (Jacobi) or learned preconditioner ---------------------------
+// The paper's exact diagonalisation names no algorithm; Davidson is the standard
+// alternative to Lanczos for the lowest eigenpair.  Each step expands an orthonormal
+// basis V by the preconditioned residual t = M(theta) r, keeps H V (FP64, or the
+// low-precision H~ V followed by the FP64 outer loop when refine is set) and takes the
+// Rayleigh-Ritz pair of V^T H V.  Jacobi: t_i = r_i / (theta - D_i).
+namespace dmrg2d {
+namespace {
+
+__global__ void k_jacobi(double* __restrict__ t, const double* __restrict__ r,
+                         const double* __restrict__ D, double theta, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * VT + threadIdx.x; e < n; e += (int64_t)gridDim.x * VT) {
+    double den = theta - D[e];
+    if (fabs(den) < 1e-8) den = den < 0 ? -1e-8 : 1e-8;
+    t[e] = r[e] / den;
+  }
+}
+
+}  // namespace
+
+int davidson_solve(Ctx& C, const dmrg2d_davidson_opts* o, double* x, double* energy, double* resid,
+                   int* iters) {
+  const int64_t n = C.n;
+  const int prec = o->precision;
+  int smax = o->max_subspace < 4 ? 4 : (o->max_subspace > 48 ? 48 : o->max_subspace);
+  DevBuf Vb, Wb, xb, hxb, rb, tb, Db, Gb, cb, scb;
+  D2_TRY(dmalloc(Vb, sizeof(double) * (size_t)smax * n));
+  D2_TRY(dmalloc(Wb, sizeof(double) * (size_t)smax * n));
+  D2_TRY(dmalloc(hxb, sizeof(double) * n));
+  D2_TRY(dmalloc(rb, sizeof(double) * n));
+  D2_TRY(dmalloc(tb, sizeof(double) * n));
+  D2_TRY(dmalloc(Db, sizeof(double) * n));
+  D2_TRY(dmalloc(Gb, sizeof(double) * smax * smax));
+  D2_TRY(dmalloc(cb, sizeof(double) * smax));
+  D2_TRY(dmalloc(scb, sizeof(double) * 2 * smax * smax));
+  double *V = (double*)Vb.p, *W = (double*)Wb.p, *hx = (double*)hxb.p, *r = (double*)rb.p;
+  double *t = (double*)tb.p, *D = (double*)Db.p, *G = (double*)Gb.p, *cc = (double*)cb.p;
+  double* scr = (double*)scb.p;
+  double* sc = C.scal;
+  D2_TRY(diag_apply(C.ops, D, C.s));
+  MlpPrecond mp;
+  if (o->precond == DMRG2D_PRECOND_MLP) {
+    if (!o->mlp) return set_error(DMRG2D_EINVAL, "MLP preconditioner requested without a network");
+    D2_TRY(mlp_precond_setup(o->mlp, C.ops, D, &mp, C.s));
+  }
+  D2_TRY(C.nrm(x, sc + 3));
+  D2_TRY(C.scale_inv(V, x, sc + 3));
+  D2_TRY(C.hv(prec, V, W));
+  std::vector<double> Gh((size_t)smax * smax, 0.0);
+  auto update_G_col = [&](int jcol) -> int {
+    D2_TRY(C.multidot(V, n, jcol + 1, W + (int64_t)jcol * n, sc + 8));
+    D2_TRY(C.fetch(sc + 8, jcol + 1));
+    for (int i = 0; i <= jcol; ++i) Gh[i * smax + jcol] = Gh[jcol * smax + i] = C.hscal[i];
+    return DMRG2D_OK;
+  };
+  D2_TRY(update_G_col(0));
+  int s = 1, it = 0, status = DMRG2D_ENOCONV;
+  double theta = 0.0, rn = INFINITY;
+  for (it = 1; it <= o->max_iter; ++it) {
+    D2_CUDA(cudaMemcpyAsync(G, Gh.data(), sizeof(double) * smax * smax, cudaMemcpyHostToDevice, C.s));
+    k_small_eigh<<<1, 1, 0, C.s>>>(G, s, smax, sc + 5, cc, scr);
+    D2_CUDA(cudaGetLastError());
+    D2_TRY(C.combo(x, V, n, s, cc, 0));
+    D2_TRY(C.combo(hx, W, n, s, cc, 0));
+    D2_TRY(C.fetch(sc + 5, 1));
+    theta = C.hscal[0];
+    D2_CUDA(cudaMemcpyAsync(r, hx, sizeof(double) * n, cudaMemcpyDeviceToDevice, C.s));
+    D2_TRY(C.axpby(r, x, -theta, 1.0));
+    D2_TRY(C.nrm(r, sc + 6));
+    D2_TRY(C.fetch(sc + 6, 1));
+    rn = C.hscal[0];
+    if (o->log_cap > 0 && it - 1 < o->log_cap) {  // training data for the learned preconditioner
+      if (o->log_r)
+        D2_CUDA(cudaMemcpyAsync(o->log_r + (int64_t)(it - 1) * n, r, sizeof(double) * n,
+                                cudaMemcpyDeviceToDevice, C.s));
+      if (o->log_x)
+        D2_CUDA(cudaMemcpyAsync(o->log_x + (int64_t)(it - 1) * n, x, sizeof(double) * n,
+                                cudaMemcpyDeviceToDevice, C.s));
+      if (o->log_theta) o->log_theta[it - 1] = theta;
+    }
+    if (!std::isfinite(theta) || !std::isfinite(rn)) {
+      status = set_error(DMRG2D_ENAN, "NaN/Inf in Davidson");
+      break;
+    }
+    if (rn <= o->tol * fabs(theta)) {
+      status = DMRG2D_OK;
+      break;
+    }
+    if (o->precond == DMRG2D_PRECOND_JACOBI) {
+      k_jacobi<<<vgrid(n), VT, 0, C.s>>>(t, r, D, theta, n);
+      D2_CUDA(cudaGetLastError());
+    } else if (o->precond == DMRG2D_PRECOND_MLP) {
+      D2_TRY(mlp_precond_apply(o->mlp, &mp, r, D, theta, t, n, C.s));
+    } else {
+      D2_CUDA(cudaMemcpyAsync(t, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, C.s));
+    }
+    if (s == smax) {  // restart from the Ritz pair
+      D2_CUDA(cudaMemcpyAsync(V, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, C.s));
+      D2_CUDA(cudaMemcpyAsync(W, hx, sizeof(double) * n, cudaMemcpyDeviceToDevice, C.s));
+      s = 1;
+      std::fill(Gh.begin(), Gh.end(), 0.0);
+      Gh[0] = theta;
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+      D2_TRY(C.multidot(V, n, s, t, sc + 8));
+      D2_TRY(C.combo(t, V, n, s, sc + 8, -1));
+    }
+    D2_TRY(C.nrm(t, sc + 4));
+    D2_TRY(C.fetch(sc + 4, 1));
+    if (!(C.hscal[0] > 1e-300)) {
+      set_error(DMRG2D_ENOCONV, "Davidson: correction vanished, residual %.3e", rn);
+      break;
+    }
+    D2_TRY(C.scale_inv(V + (int64_t)s * n, t, sc + 4));
+    D2_TRY(C.hv(prec, V + (int64_t)s * n, W + (int64_t)s * n));
+    D2_TRY(update_G_col(s));
+    ++s;
+  }
+  if (it > o->max_iter) {
+    it = o->max_iter;
+    set_error(DMRG2D_ENOCONV, "Davidson: %d steps, residual %.3e", it, rn);
+  }
+  mlp_precond_release(&mp);
+  *energy = theta;
+  *resid = rn;
+  *iters = it;
+  return status;
+}
+
+}  // namespace dmrg2d
+
+extern "C" void dmrg2d_default_davidson_opts(dmrg2d_davidson_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->max_iter = 500;
+  o->max_subspace = 24;
+  o->tol = 1e-10;
+  o->precision = DMRG2D_FP64;
+  o->refine = 0;
+  o->precond = DMRG2D_PRECOND_JACOBI;
+  o->inner_iter = 40;
+  o->outer_max = 20;
+  o->refine_tol = 1e-10;
+}
+
+extern "C" int dmrg2d_davidson_ground(const dmrg2d_ops* ops, const dmrg2d_davidson_opts* opts,
+                                      double* x_inout, double* energy_out,
+                                      dmrg2d_solver_stats* stats, void* stream) {
+  using namespace dmrg2d;
+  if (!ops || !x_inout || !energy_out || !opts) return set_error(DMRG2D_EINVAL, "NULL argument");
+  clear_error();
+  const dmrg2d_davidson_opts& o = *opts;
+  if (o.max_iter < 1) return set_error(DMRG2D_EINVAL, "max_iter < 1");
+  if (o.precond < DMRG2D_PRECOND_NONE || o.precond > DMRG2D_PRECOND_MLP)
+    return set_error(DMRG2D_EINVAL, "unknown preconditioner %d", o.precond);
+  if ((o.precision == DMRG2D_TF32 || o.precision == DMRG2D_BF16) && !ops->tc_ok)
+    return set_error(DMRG2D_EUNSUPPORTED, "tensor-core path unsupported for these shapes");
+  const auto t0 = std::chrono::steady_clock::now();
+  dmrg2d_solver_stats local{};
+  Ctx C;
+  C.ops = ops;
+  C.s = (cudaStream_t)stream;
+  C.n = ops->n_vec;
+  C.st = &local;
+  DevBuf part, scal, lo, y32;
+  D2_TRY(dmalloc(part, sizeof(double) * (size_t)RED_BLOCKS * 520));
+  D2_TRY(dmalloc(scal, sizeof(double) * 64));
+  C.part = (double*)part.p;
+  C.scal = (double*)scal.p;
+  D2_CUDA(cudaMallocHost(&C.hscal, sizeof(double) * 64));
+  struct PinnedFree {
+    double* p;
+    ~PinnedFree() { cudaFreeHost(p); }
+  } pf{C.hscal};
+  if (o.precision != DMRG2D_FP64) {
+    D2_TRY(dmalloc(lo, (o.precision == DMRG2D_BF16 ? 2 : 4) * (size_t)C.n));
+    D2_TRY(dmalloc(y32, sizeof(float) * (size_t)C.n));
+    C.lo = lo.p;
+    C.y32 = (float*)y32.p;
+  }
+  D2_TRY(sec_zero_padding(ops, x_inout, C.s));
+  double energy = 0.0, resid = 0.0;
+  int iters = 0;
+  int st = davidson_solve(C, &o, x_inout, &energy, &resid, &iters);
+  local.iters = iters;
+  local.resid = resid;
+  if ((st == DMRG2D_OK || st == DMRG2D_ENOCONV) && o.refine && o.precision != DMRG2D_FP64) {
+    // FP64 outer loop from the Davidson vector (same loop as the mixed Lanczos solver)
+    dmrg2d_solver_opts so;
+    dmrg2d_default_solver_opts(&so);
+    so.precision = o.precision;
+    so.refine = 1;
+    so.tol = o.refine_tol;
+    so.inner_iter = o.inner_iter;
+    so.outer_max = o.outer_max;
+    st = mixed_outer(C, &so, x_inout, &energy);
+    local.resid = C.st->resid;
+  }
+  cudaError_t e = cudaStreamSynchronize(C.s);
+  if (e != cudaSuccess && st == DMRG2D_OK)
+    st = set_error(DMRG2D_ECUDA, "solver: %s", cudaGetErrorString(e));
+  int derr = 0;
+  if (tc_read_error(ops, &derr) == DMRG2D_OK && derr && st == DMRG2D_OK)
+    st = set_error(DMRG2D_ETIMEOUT, "tensor-core kernel gave up waiting (site %d)", derr);
+  local.hv_ms = C.hv_ms();
   local.elapsed_ms =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   *energy_out = energy;

@@ -52,6 +52,14 @@ class SolverOpts(C.Structure):
                 ("inner_iter", C.c_int), ("outer_max", C.c_int), ("check_every", C.c_int)]
 
 
+class DavidsonOpts(C.Structure):
+    _fields_ = [("max_iter", C.c_int), ("max_subspace", C.c_int), ("tol", C.c_double),
+                ("precision", C.c_int), ("refine", C.c_int), ("precond", C.c_int),
+                ("mlp", C.c_void_p), ("inner_iter", C.c_int), ("outer_max", C.c_int),
+                ("refine_tol", C.c_double), ("log_cap", C.c_int), ("log_x", C.c_void_p),
+                ("log_r", C.c_void_p), ("log_theta", C.POINTER(C.c_double))]
+
+
 class SolverStats(C.Structure):
     _fields_ = [("iters", C.c_int), ("outer", C.c_int), ("n_hv_fp64", C.c_int),
                 ("n_hv_low", C.c_int), ("resid", C.c_double), ("hv_ms", C.c_double),
@@ -71,6 +79,24 @@ SIGNATURES = {
                                                 C.POINTER(C.c_double), C.POINTER(SolverStats),
                                                 C.c_void_p]),
     "dmrg2d_default_solver_opts": (None, [C.POINTER(SolverOpts)]),
+    "dmrg2d_diagonal": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dmrg2d_default_davidson_opts": (None, [C.POINTER(DavidsonOpts)]),
+    "dmrg2d_davidson_ground": (C.c_int, [C.c_void_p, C.POINTER(DavidsonOpts), C.c_void_p,
+                                         C.POINTER(C.c_double), C.POINTER(SolverStats),
+                                         C.c_void_p]),
+    "dmrg2d_mlp_create": (C.c_int, [C.c_int, C.c_uint64, C.POINTER(C.c_void_p)]),
+    "dmrg2d_mlp_free": (None, [C.c_void_p]),
+    "dmrg2d_mlp_num_params": (C.c_int, [C.c_void_p]),
+    "dmrg2d_mlp_get_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "dmrg2d_mlp_set_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "dmrg2d_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "dmrg2d_mlp_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                       C.c_void_p, C.POINTER(C.c_float), C.c_void_p]),
+    "dmrg2d_mlp_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                        C.c_float, C.POINTER(C.c_float), C.c_void_p]),
+    "dmrg2d_mlp_make_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
+                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
+                                        C.c_void_p, C.c_void_p, C.c_void_p]),
     "dmrg2d_autotune": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_void_p, C.c_int,
                                   C.c_void_p]),
     "dmrg2d_set_tile_config": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
@@ -299,3 +325,114 @@ def lanczos_ground_noalloc(ops: Ops, x, stream=None, **opts):
     if code not in (0, -5):
         _check(code)
     return e.value, {k: getattr(st, k) for k, _ in SolverStats._fields_}, code
+
+
+PRECOND = {"none": 0, "jacobi": 1, "mlp": 2}
+
+
+def diagonal(ops: Ops, out, stream=None):
+    """out (CUDA float64, n_vec) = diagonal of H in the vector layout."""
+    if not out.is_cuda or str(out.dtype) != "torch.float64" or out.numel() != ops.info["n_vec"]:
+        raise ValueError("out must be a CUDA float64 tensor of n_vec elements")
+    _check(lib().dmrg2d_diagonal(ops.ptr, C.c_void_p(out.data_ptr()), _stream(stream)))
+
+
+def davidson_ground(ops: Ops, x, stream=None, mlp=None, log=None, **opts):
+    """Davidson; x (CUDA float64) is the start vector and receives the result.
+
+    log: optional (cap, x_log, r_log) with CUDA float64 tensors of cap*n_vec elements;
+    returns (energy, stats, status[, thetas]).
+    """
+    o = DavidsonOpts()
+    lib().dmrg2d_default_davidson_opts(C.byref(o))
+    for k, v in opts.items():
+        if k == "precision":
+            v = PRECISION.get(v, v)
+        if k == "precond":
+            v = PRECOND.get(v, v)
+        setattr(o, k, v)
+    if mlp is not None:
+        o.mlp = mlp.ptr
+    thetas = None
+    if log is not None:
+        cap, xl, rl = log
+        thetas = (C.c_double * cap)()
+        o.log_cap = cap
+        o.log_x = xl.data_ptr() if xl is not None else None
+        o.log_r = rl.data_ptr() if rl is not None else None
+        o.log_theta = thetas
+    if not x.is_cuda or str(x.dtype) != "torch.float64" or x.numel() != ops.info["n_vec"]:
+        raise ValueError("x must be a CUDA float64 tensor of n_vec elements")
+    e = C.c_double()
+    st = SolverStats()
+    code = lib().dmrg2d_davidson_ground(ops.ptr, C.byref(o), C.c_void_p(x.data_ptr()), C.byref(e),
+                                        C.byref(st), _stream(stream))
+    if code not in (0, -5):
+        _check(code)
+    stats = {k: getattr(st, k) for k, _ in SolverStats._fields_}
+    if thetas is not None:
+        return e.value, stats, code, list(thetas)
+    return e.value, stats, code
+
+
+class MLP:
+    """The learned preconditioner's network (device parameters, FP32)."""
+
+    def __init__(self, hidden=256, seed=0):
+        p = C.c_void_p()
+        _check(lib().dmrg2d_mlp_create(int(hidden), int(seed), C.byref(p)))
+        self._p = p
+        self.hidden = hidden
+        self.n_params = lib().dmrg2d_mlp_num_params(p)
+
+    @property
+    def ptr(self):
+        return self._p
+
+    def free(self):
+        if self._p:
+            lib().dmrg2d_mlp_free(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def get_params(self) -> np.ndarray:
+        h = np.empty(self.n_params, dtype=np.float32)
+        _check(lib().dmrg2d_mlp_get_params(self._p, h.ctypes.data_as(C.c_void_p)))
+        return h
+
+    def set_params(self, h):
+        h = np.ascontiguousarray(h, dtype=np.float32)
+        assert h.size == self.n_params
+        _check(lib().dmrg2d_mlp_set_params(self._p, h.ctypes.data_as(C.c_void_p)))
+
+    def forward(self, X, Y, stream=None):
+        _check(lib().dmrg2d_mlp_forward(self._p, C.c_void_p(X.data_ptr()), C.c_void_p(Y.data_ptr()),
+                                        int(Y.numel()), _stream(stream)))
+
+    def loss_grad(self, X, w, T, grad, stream=None):
+        loss = C.c_float()
+        _check(lib().dmrg2d_mlp_loss_grad(self._p, C.c_void_p(X.data_ptr()), C.c_void_p(w.data_ptr()),
+                                          C.c_void_p(T.data_ptr()), int(T.numel()),
+                                          C.c_void_p(grad.data_ptr()), C.byref(loss),
+                                          _stream(stream)))
+        return loss.value
+
+    def train_step(self, X, w, T, lr, stream=None):
+        loss = C.c_float()
+        _check(lib().dmrg2d_mlp_train_step(self._p, C.c_void_p(X.data_ptr()), C.c_void_p(w.data_ptr()),
+                                           C.c_void_p(T.data_ptr()), int(T.numel()), float(lr),
+                                           C.byref(loss), _stream(stream)))
+        return loss.value
+
+
+def mlp_make_batch(ops: Ops, x_k, r_k, theta, x_final, D, idx, X, w, T, stream=None):
+    _check(lib().dmrg2d_mlp_make_batch(
+        ops.ptr, C.c_void_p(x_k.data_ptr()), C.c_void_p(r_k.data_ptr()), float(theta),
+        C.c_void_p(x_final.data_ptr()), C.c_void_p(D.data_ptr()), C.c_void_p(idx.data_ptr()),
+        int(idx.numel()), C.c_void_p(X.data_ptr()), C.c_void_p(w.data_ptr()),
+        C.c_void_p(T.data_ptr()), _stream(stream)))
