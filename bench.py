@@ -282,7 +282,7 @@ def run_ours(args):
                       "n_vec": n, "flops_per_hv": flops, "parallelism": f"replicas{world}",
                       "l2": "inputs larger than L2 (no flush)"},
            "clocks": clocks, "e2e": e2e,
-           "gpu_launches": k_n if prec == dmrg2d.FP64 or prec == dmrg2d.FP32 else 2 * k_n,
+           "gpu_launches": k_n,
            "roofline": roof}
 
     if args.tte and rank == 0:

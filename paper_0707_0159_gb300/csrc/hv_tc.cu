@@ -6,13 +6,14 @@
 // For one piece the K loop runs over
 //   phase 1 (H_l V):   A = HL[i2,i2'] rows, K-major       B = V(i2' rows, i3 cols), K-major
 //   phase 2 (V H_r^T): A = V(i2 rows, i3' cols), MN-major  B = HR[i3,i3'] rows, K-major
-// into ONE accumulator, so Y is written once.  A second, memory-bound kernel then adds
-// the scalar tile moves (H_c, off-diagonal column terms): Y(i2,i3) += c V(i2',i3').
+// into ONE accumulator, so Y is written once.  The epilogue adds the scalar tile moves
+// (H_c, off-diagonal column terms), Y(i2,i3) += c V(i2',i3'), reading the source rows
+// from L2 while the MMAs of the next piece run in the other accumulator.
 //
 // Kernel organisation (one persistent CTA per SM, 192 threads):
 //   warp 0   TMA producer: 4-stage ring of 48 KB (A 16 KB + B up to 32 KB), 128B swizzle
 //   warp 1   TMEM owner (512 columns = two 128 x 256 FP32 accumulators) and MMA issuer
-//   warps 2-5 epilogue: tcgen05.ld of the finished accumulator, coalesced FP32 stores
+//   warps 2-5 epilogue: tcgen05.ld of the finished accumulator, scalar moves, FP32 stores
 // Every mbarrier wait is bounded (globaltimer); on timeout the CTA raises an error flag,
 // stops issuing work, releases its tensor memory and returns.
 #include <cuda.h>
@@ -28,7 +29,8 @@ namespace {
 
 using namespace tc;
 
-constexpr int TC_THREADS = 192;
+constexpr int TC_THREADS = 320;  // producer, MMA issuer, 8 epilogue warps
+constexpr int EPI_WARPS = 8;
 constexpr int STAGES = 4;
 constexpr int BM = 128;
 constexpr uint32_t STAGE_A = 16384;
@@ -56,6 +58,12 @@ struct TcParams {
   int a2_boxes, a2_box_rows;
   uint32_t tx_bytes;
   int bf16;
+  // scalar tile moves fused into the epilogue (H_c and off-diagonal column terms)
+  int fuse;
+  const void* v;
+  const int* Cptr;
+  const int* Csrc;
+  const float* Cval;
 };
 
 struct TileCoord {
@@ -89,7 +97,7 @@ hv_tc_kernel(const __grid_constant__ CUtensorMap mHL, const __grid_constant__ CU
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull(b), 1);
-      mbar_init(tempty(b), 4);
+      mbar_init(tempty(b), EPI_WARPS);
     }
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -208,7 +216,8 @@ hv_tc_kernel(const __grid_constant__ CUtensorMap mHL, const __grid_constant__ CU
     }
   } else if (warp >= 2) {
     // ------------------------------- epilogue -----------------------------------
-    const int q = warp & 3;  // TMEM lane quadrant this warp may access
+    const int q = warp & 3;             // TMEM lane quadrant this warp may access
+    const int half = (warp - 2) >> 2;   // two warps per quadrant split the column chunks
     int acc = 0;
     uint32_t aphase = 0;
     for (int t = blockIdx.x; t < p.tiles; t += gridDim.x) {
@@ -221,12 +230,53 @@ hv_tc_kernel(const __grid_constant__ CUtensorMap mHL, const __grid_constant__ CU
       const int row = 32 * q + lane;
       const int64_t r = (int64_t)c.i2 * p.m1 + c.mt * BM + row;
       const int64_t col0 = (int64_t)c.i3 * p.m4 + (int64_t)c.nt * p.BN;
-      for (int ch = 0; ch < p.BN / 32; ++ch) {
+      const int tt = c.i2 + p.d * c.i3;
+      const int e0 = p.fuse ? p.Cptr[tt] : 0, e1 = p.fuse ? p.Cptr[tt + 1] : 0;
+      const int nch = p.BN / 32;
+      for (int ch = half * (nch / 2); ch < (half + 1) * (nch / 2); ++ch) {
         uint32_t v[32];
         tmem_ld32(tmem_base + ((uint32_t)(32 * q) << 16) + acc * ACC_COLS + ch * 32, v);
+        float o[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) o[j] = __uint_as_float(v[j]);
+        // scalar tile moves of this piece: Y(i2,i3) += c V(i2',i3') on the same rows and
+        // columns of the source tile; a warp reads 32 consecutive rows per column, two
+        // moves at a time to keep more loads in flight
+        for (int e = e0; e < e1; e += 2) {
+          const bool two = e + 1 < e1;
+          const int sa = p.Csrc[e], sb = two ? p.Csrc[e + 1] : sa;
+          const float ca = p.Cval[e], cb = two ? p.Cval[e + 1] : 0.f;
+          const int64_t ra = (int64_t)(sa % p.d) * p.m1 + c.mt * BM + row;
+          const int64_t rb = (int64_t)(sb % p.d) * p.m1 + c.mt * BM + row;
+          const int64_t ka = (int64_t)(sa / p.d) * p.m4 + (int64_t)c.nt * p.BN + ch * 32;
+          const int64_t kb = (int64_t)(sb / p.d) * p.m4 + (int64_t)c.nt * p.BN + ch * 32;
+          if (p.bf16) {
+            const __nv_bfloat16* A = (const __nv_bfloat16*)p.v + ra + p.ld * ka;
+            const __nv_bfloat16* B = (const __nv_bfloat16*)p.v + rb + p.ld * kb;
+            float va[32], vb[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              va[j] = __bfloat162float(A[p.ld * j]);
+              vb[j] = __bfloat162float(B[p.ld * j]);
+            }
+#pragma unroll
+            for (int j = 0; j < 32; ++j) o[j] += ca * va[j] + cb * vb[j];
+          } else {
+            const float* A = (const float*)p.v + ra + p.ld * ka;
+            const float* B = (const float*)p.v + rb + p.ld * kb;
+            float va[32], vb[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              va[j] = __ldg(A + p.ld * j);
+              vb[j] = __ldg(B + p.ld * j);
+            }
+#pragma unroll
+            for (int j = 0; j < 32; ++j) o[j] += ca * va[j] + cb * vb[j];
+          }
+        }
         float* yp = p.y + r + p.ld * (col0 + ch * 32);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) yp[p.ld * j] = __uint_as_float(v[j]);
+        for (int j = 0; j < 32; ++j) yp[p.ld * j] = o[j];
       }
       tc_fence_before();
       __syncwarp();
@@ -439,7 +489,7 @@ void tc_release(dmrg2d_ops* ops) {
 }
 
 static int launch_dense_kernel(const dmrg2d_ops* ops, const TcState* T, const void* v, float* y,
-                               bool bf, cudaStream_t s) {
+                               bool bf, bool fuse_moves, cudaStream_t s) {
   const int b = bf ? 1 : 0;
   const int m1 = ops->m1, m4 = ops->m4, d = ops->d;
   const uint32_t BK = bf ? 64 : 32;
@@ -474,6 +524,11 @@ static int launch_dense_kernel(const dmrg2d_ops* ops, const TcState* T, const vo
   p.a2_sbo = bf ? 1024u : 512u;
   p.tx_bytes = STAGE_A + (uint32_t)T->BN * 128;
   p.bf16 = bf ? 1 : 0;
+  p.fuse = fuse_moves ? 1 : 0;
+  p.v = v;
+  p.Cptr = ops->dev.Cptr;
+  p.Csrc = ops->dev.Csrc;
+  p.Cval = ops->dev.Cval32;
   CUtensorMap mVk, mVm;
   const uint64_t rows = (uint64_t)ops->ld, cols = (uint64_t)d * m4;
   D2_TRY(make_map(&mVk, v, bf, rows, cols, BK, T->BN));
@@ -495,7 +550,7 @@ int tc_gemm(const dmrg2d_ops* ops, const void* v, float* y, int precision, int c
   if (!T) return set_error(DMRG2D_EUNSUPPORTED, "tensor-core path not prepared");
   if (cfg < 0) {
     if (!T->dense_ok) return set_error(DMRG2D_EUNSUPPORTED, "dense kernel unsupported here");
-    return launch_dense_kernel(ops, T, v, y, precision == DMRG2D_BF16, s);
+    return launch_dense_kernel(ops, T, v, y, precision == DMRG2D_BF16, false, s);
   }
   if (!T->plan) return set_error(DMRG2D_EUNSUPPORTED, "grouped kernel unsupported here");
   return gp_launch(ops, T->plan, v, y, precision, cfg, s);
@@ -507,6 +562,9 @@ int launch_hv_tc(const dmrg2d_ops* ops, const void* v, float* y, int precision, 
     return set_error(DMRG2D_EUNSUPPORTED, "tensor-core path not prepared");
   const bool bf = precision == DMRG2D_BF16;
   const int m1 = ops->m1, m4 = ops->m4, d = ops->d;
+  if (ops->tc_cfg[precision] < 0) {  // dense kernel: the moves run in its epilogue
+    return launch_dense_kernel(ops, (const TcState*)ops->tc, v, y, bf, true, s);
+  }
   D2_TRY(tc_gemm(ops, v, y, precision, ops->tc_cfg[precision], s));
   dim3 g2(d * d, (m4 + 7) / 8);
   if (bf)
