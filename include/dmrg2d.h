@@ -215,7 +215,9 @@ int dmrg2d_lanczos_ground_noalloc(const dmrg2d_ops* ops, const dmrg2d_solver_opt
  * dense kernel (dense superblocks with m1 % 128 == 0 and m4 = 128 or m4 % 256 == 0);
  * index 1 + c is the grouped kernel (any sector structure; dense superblocks with
  * m1 % 8 == 0) with pieces of 128 x 128 (c = 0..2) or 128 x 256 (c = 3..5) in
- * column-slab, row-slab or longest-first order.  dmrg2d_autotune times every
+ * column-slab, row-slab or longest-first order; index 7 is the dense kernel reading
+ * each distinct operator block once (up to sign) from a small replicated pool.
+ * dmrg2d_autotune times a complete H·v (scalar moves included) with every
  * configuration that applies (one warm-up and three timed launches each, on scratch
  * buffers it allocates and frees), keeps the fastest for later apply_H and solver
  * calls at `precision` (TF32 or BF16), and returns its index in *best; ms[i]

@@ -68,7 +68,7 @@ struct GDev {
   float* pR32 = nullptr;
   __nv_bfloat16* pL16 = nullptr;
   __nv_bfloat16* pR16 = nullptr;
-  int KPL = 0, KPR = 0, prL = 0, prR = 0;
+  int KPL = 0, KPR = 0, prL = 0, prR = 0, copies = 1;
   CUtensorMap mL[2], mR[2][2];  // [precision][piece width 128/256]
   int* err = nullptr;
   int sms = 0;
@@ -418,12 +418,15 @@ int gp_finalise(dmrg2d_ops* ops, GroupPlan* g, cudaStream_t s) {
   layout(g->poolR, D->KPR, D->prR, fR);
   for (auto& k : g->k1) k.a_pool = fL[k.a_pool];
   for (auto& k : g->k2) k.b_pool = fR[k.b_pool];
-  auto fill = [](const BlockPool& P, int KP, int prow, const std::vector<int>& first) {
-    std::vector<double> h((size_t)std::max(prow, 1) * KP, 0.0);
-    for (size_t i = 0; i < P.ent.size(); ++i)
-      for (int r = 0; r < P.ent[i].rows; ++r)
-        for (int c = 0; c < P.ent[i].cols; ++c)
-          h[(size_t)(first[i] + r) * KP + c] = P.ent[i].a[(size_t)r * P.ent[i].cols + c];
+  const int copies = std::max(1, g->copies);
+  auto fill = [copies](const BlockPool& P, int KP, int prow, const std::vector<int>& first) {
+    std::vector<double> h((size_t)copies * std::max(prow, 1) * KP, 0.0);
+    for (int cp = 0; cp < copies; ++cp)
+      for (size_t i = 0; i < P.ent.size(); ++i)
+        for (int r = 0; r < P.ent[i].rows; ++r)
+          for (int c = 0; c < P.ent[i].cols; ++c)
+            h[((size_t)cp * prow + first[i] + r) * KP + c] =
+                P.ent[i].a[(size_t)r * P.ent[i].cols + c];
     return h;
   };
   std::vector<double> hL = fill(g->poolL, D->KPL, D->prL, fL);
@@ -507,7 +510,8 @@ int gp_finalise(dmrg2d_ops* ops, GroupPlan* g, cudaStream_t s) {
       st = set_error(DMRG2D_ECUDA, "memset failed");
   }
   if (st == DMRG2D_OK) {
-    const int rowsL = std::max(D->prL, 1), rowsR = std::max(D->prR, 1);
+    const int rowsL = std::max(D->prL, 1) * copies, rowsR = std::max(D->prR, 1) * copies;
+    D->copies = copies;
     st = map2d(&D->mL[0], D->pL32, false, D->KPL, rowsL, 32, G_BM, CU_TENSOR_MAP_SWIZZLE_128B);
     if (st == DMRG2D_OK)
       st = map2d(&D->mL[1], D->pL16, true, D->KPL, rowsL, 64, G_BM, CU_TENSOR_MAP_SWIZZLE_128B);
@@ -598,6 +602,19 @@ int gp_launch(const dmrg2d_ops* ops, const GroupPlan* g, const void* v, float* y
   hv_tc_grouped_kernel<<<grid, G_THREADS, G_SMEM, s>>>(maps, p);
   D2_CUDA(cudaGetLastError());
   if (ev.second) D2_CUDA(cudaEventRecord(ev.second, s));
+  return DMRG2D_OK;
+}
+
+int gp_pool_views(const GroupPlan* g, int precision, int bn, const CUtensorMap** mL,
+                  const CUtensorMap** mR, const GK1** k1, const GK2** k2, int* rowsL, int* rowsR,
+                  int* copies) {
+  const GDev* D = g ? (const GDev*)g->dev : nullptr;
+  if (!D) return set_error(DMRG2D_EUNSUPPORTED, "grouped plan not prepared");
+  const int pi = precision == DMRG2D_BF16 ? 1 : 0;
+  *mL = &D->mL[pi];
+  *mR = &D->mR[pi][bn == 256 ? 1 : 0];
+  *k1 = D->k1;
+  *k2 = D->k2;
   return DMRG2D_OK;
 }
 

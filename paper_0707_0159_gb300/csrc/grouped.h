@@ -9,6 +9,7 @@
 // segment's phase-2 list one entry per H_r block (A = columns of V_q, B = pool block).
 // The pool stores every distinct operator block once; an entry may use it negated.
 #pragma once
+#include <cuda.h>
 #include <cstdint>
 #include <vector>
 
@@ -53,6 +54,7 @@ struct GroupPlan {
   std::vector<GK1> k1;  // a_pool holds the pool ENTRY index until finalise()
   std::vector<GK2> k2;
   BlockPool poolL, poolR;
+  int copies = 1;       // pool replicas (CTAs read replica blockIdx % copies: no L2 hot spot)
   void* dev = nullptr;  // device state (grouped.cu)
 };
 
@@ -64,6 +66,10 @@ void gp_release(GroupPlan* g);
 int gp_launch(const dmrg2d_ops* ops, const GroupPlan* g, const void* v, float* y, int precision,
               int cfg, cudaStream_t s);
 int gp_read_error(const GroupPlan* g, int* code);
+// pool tensor maps and per-block entries (CSR order of the build) for another kernel
+int gp_pool_views(const GroupPlan* g, int precision, int bn, const CUtensorMap** mL,
+                  const CUtensorMap** mR, const GK1** k1, const GK2** k2, int* rowsL, int* rowsR,
+                  int* copies);
 int gp_num_configs();
 const char* gp_config_name(int cfg);
 

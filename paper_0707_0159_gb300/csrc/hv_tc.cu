@@ -53,11 +53,17 @@ struct TcParams {
   const int* Rcol;
   float* y;
   int* err;
-  uint32_t idesc1, idesc2;
+  uint32_t idesc1[2], idesc2[2];  // [negate the operator block]
   uint32_t a2_lbo, a2_sbo, a2_kstep, a2_layout;
   int a2_boxes, a2_box_rows;
   uint32_t tx_bytes;
   int bf16;
+  // operator blocks from the deduplicated pool: entry e of H_l / H_r reads pool rows
+  // k1[e].a_pool / k2[e].b_pool, negated when .neg is set (pooled = 0: block e itself)
+  int pooled;
+  const GK1* k1;
+  const GK2* k2;
+  int poolL_rows, poolR_rows, copies;  // rows of one pool replica; replicas
   // scalar tile moves fused into the epilogue (H_c and off-diagonal column terms)
   int fuse;
   const void* v;
@@ -138,13 +144,19 @@ hv_tc_kernel(const __grid_constant__ CUtensorMap mHL, const __grid_constant__ CU
             const uint32_t b_s = a_s + STAGE_A;
             mbar_expect_tx(full(stage), p.tx_bytes);
             if (ph == 0) {
-              tma_load_2d(a_s, &mHL, full(stage), kc * p.BK, e * p.m1 + c.mt * BM);
+              tma_load_2d(a_s, &mHL, full(stage), kc * p.BK,
+                          (p.pooled ? p.k1[e].a_pool + (int)(blockIdx.x % p.copies) * p.poolL_rows
+                                    : e * p.m1) +
+                              c.mt * BM);
               tma_load_2d(b_s, &mVk, full(stage), nb * p.m1 + kc * p.BK, c0);
             } else {
               for (int b = 0; b < p.a2_boxes; ++b)
                 tma_load_2d(a_s + b * p.a2_lbo, &mVm, full(stage), r0 + b * p.a2_box_rows,
                             nb * p.m4 + kc * p.BK);
-              tma_load_2d(b_s, &mHR, full(stage), kc * p.BK, e * p.m4 + c.nt * p.BN);
+              tma_load_2d(b_s, &mHR, full(stage), kc * p.BK,
+                          (p.pooled ? p.k2[e].b_pool + (int)(blockIdx.x % p.copies) * p.poolR_rows
+                                    : e * p.m4) +
+                              c.nt * p.BN);
             }
             if (++stage == STAGES) {
               stage = 0;
@@ -185,16 +197,18 @@ hv_tc_kernel(const __grid_constant__ CUtensorMap mHL, const __grid_constant__ CU
           tc_fence_after();
           const uint32_t a_s = smem_u32(smem + stage * STAGE_BYTES);
           const uint32_t b_s = a_s + STAGE_A;
+          const int eb = e0 + st / kb;  // operator block of this K step
+          const int neg = p.pooled ? (ph == 0 ? p.k1[eb].neg : p.k2[eb].neg) : 0;
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             uint64_t ad, bd;
             uint32_t id;
             if (ph == 0) {
               ad = sdesc(a_s + k * 32, 16, 1024);
-              id = p.idesc1;
+              id = p.idesc1[neg];
             } else {
               ad = sdesc(a_s + k * p.a2_kstep, p.a2_lbo, p.a2_sbo, p.a2_layout);
-              id = p.idesc2;
+              id = p.idesc2[neg];
             }
             bd = sdesc(b_s + k * 32, 16, 1024);
             umma(dt, ad, bd, id, accum, p.bf16);
@@ -440,6 +454,7 @@ int tc_prepare(dmrg2d_ops* ops, cudaStream_t s, const std::vector<double>& HL,
     // operator blocks stored once up to sign
     GroupPlan* g = new GroupPlan();
     T->plan = g;
+    g->copies = 8;
     g->nQ = 1;
     g->qbase = {0};
     g->qld = {(int)ops->ld};
@@ -489,7 +504,7 @@ void tc_release(dmrg2d_ops* ops) {
 }
 
 static int launch_dense_kernel(const dmrg2d_ops* ops, const TcState* T, const void* v, float* y,
-                               bool bf, bool fuse_moves, cudaStream_t s) {
+                               bool bf, bool fuse_moves, bool use_pool, cudaStream_t s) {
   const int b = bf ? 1 : 0;
   const int m1 = ops->m1, m4 = ops->m4, d = ops->d;
   const uint32_t BK = bf ? 64 : 32;
@@ -512,8 +527,21 @@ static int launch_dense_kernel(const dmrg2d_ops* ops, const TcState* T, const vo
   p.y = y;
   p.err = T->err;
   const int fmt = bf ? 1 : 2;
-  p.idesc1 = make_idesc(fmt, 0, BM, T->BN);
-  p.idesc2 = make_idesc(fmt, 1, BM, T->BN);
+  for (int n = 0; n < 2; ++n) {
+    p.idesc1[n] = make_idesc(fmt, 0, BM, T->BN, n, 0);
+    p.idesc2[n] = make_idesc(fmt, 1, BM, T->BN, 0, n);
+  }
+  const CUtensorMap* mA = &T->mHL[b];
+  const CUtensorMap* mB = &T->mHR[b];
+  p.pooled = 0;
+  p.k1 = nullptr;
+  p.k2 = nullptr;
+  p.poolL_rows = p.poolR_rows = 0;
+  p.copies = 1;
+  if (use_pool && T->plan &&
+      gp_pool_views(T->plan, bf ? DMRG2D_BF16 : DMRG2D_TF32, T->BN, &mA, &mB, &p.k1, &p.k2,
+                    &p.poolL_rows, &p.poolR_rows, &p.copies) == DMRG2D_OK)
+    p.pooled = 1;
   p.a2_box_rows = bf ? 64 : 32;
   p.a2_boxes = BM / p.a2_box_rows;
   p.a2_lbo = (uint32_t)p.a2_box_rows * BK * (bf ? 2 : 4);  // bytes of one {rows, BK} box
@@ -537,7 +565,7 @@ static int launch_dense_kernel(const dmrg2d_ops* ops, const TcState* T, const vo
   const int grid = p.tiles < T->sms ? p.tiles : T->sms;
   auto ev = prof_slot(ops);
   if (ev.first) D2_CUDA(cudaEventRecord(ev.first, s));
-  hv_tc_kernel<<<grid, TC_THREADS, SMEM_BYTES, s>>>(T->mHL[b], T->mHR[b], mVk, mVm, p);
+  hv_tc_kernel<<<grid, TC_THREADS, SMEM_BYTES, s>>>(*mA, *mB, mVk, mVm, p);
   D2_CUDA(cudaGetLastError());
   if (ev.second) D2_CUDA(cudaEventRecord(ev.second, s));
   return DMRG2D_OK;
@@ -550,7 +578,7 @@ int tc_gemm(const dmrg2d_ops* ops, const void* v, float* y, int precision, int c
   if (!T) return set_error(DMRG2D_EUNSUPPORTED, "tensor-core path not prepared");
   if (cfg < 0) {
     if (!T->dense_ok) return set_error(DMRG2D_EUNSUPPORTED, "dense kernel unsupported here");
-    return launch_dense_kernel(ops, T, v, y, precision == DMRG2D_BF16, false, s);
+    return launch_dense_kernel(ops, T, v, y, precision == DMRG2D_BF16, false, cfg == -2, s);
   }
   if (!T->plan) return set_error(DMRG2D_EUNSUPPORTED, "grouped kernel unsupported here");
   return gp_launch(ops, T->plan, v, y, precision, cfg, s);
@@ -563,7 +591,8 @@ int launch_hv_tc(const dmrg2d_ops* ops, const void* v, float* y, int precision, 
   const bool bf = precision == DMRG2D_BF16;
   const int m1 = ops->m1, m4 = ops->m4, d = ops->d;
   if (ops->tc_cfg[precision] < 0) {  // dense kernel: the moves run in its epilogue
-    return launch_dense_kernel(ops, (const TcState*)ops->tc, v, y, bf, true, s);
+    return launch_dense_kernel(ops, (const TcState*)ops->tc, v, y, bf, true,
+                               ops->tc_cfg[precision] == -2, s);
   }
   D2_TRY(tc_gemm(ops, v, y, precision, ops->tc_cfg[precision], s));
   dim3 g2(d * d, (m4 + 7) / 8);
@@ -599,11 +628,12 @@ int tc_read_error(const dmrg2d_ops* ops, int* code) {
 // ---- tile-configuration autotuner ---------------------------------------------------------
 namespace dmrg2d {
 
-// candidate index: 0 = dense kernel, 1 + c = grouped kernel configuration c
+// candidate index: 0 = dense kernel, 1 + c = grouped kernel configuration c, 7 = dense
+// kernel reading the deduplicated (replicated) operator pool
 static bool tc_candidate_ok(const dmrg2d_ops* ops, int idx) {
-  if (idx == 0) {
+  if (idx == 0 || idx == 7) {
     const TcState* T = (const TcState*)ops->tc;
-    return !ops->sec && T && T->dense_ok;
+    return !ops->sec && T && T->dense_ok && (idx == 0 || T->plan);
   }
   if (idx < 1 || idx > gp_num_configs()) return false;
   if (ops->sec) return ops->tc_ok != 0;
@@ -611,10 +641,14 @@ static bool tc_candidate_ok(const dmrg2d_ops* ops, int idx) {
   return T && T->plan;
 }
 
-static int tc_run_candidate(const dmrg2d_ops* ops, const void* v, float* y, int prec, int idx,
+// one full H·v (operator blocks and scalar moves) with candidate idx
+static int tc_run_candidate(dmrg2d_ops* ops, const void* v, float* y, int prec, int idx,
                             cudaStream_t s) {
-  if (ops->sec) return sec_tc_gemm(ops, v, y, prec, idx - 1, s);
-  return tc_gemm(ops, v, y, prec, idx == 0 ? -1 : idx - 1, s);
+  const int saved = ops->tc_cfg[prec];
+  ops->tc_cfg[prec] = idx == 0 ? -1 : (idx == 7 ? -2 : idx - 1);
+  const int st = launch_hv_tc(ops, v, y, prec, s);
+  ops->tc_cfg[prec] = saved;
+  return st;
 }
 
 }  // namespace dmrg2d
@@ -623,6 +657,7 @@ using namespace dmrg2d;
 
 extern "C" const char* dmrg2d_tile_config_name(int index) {
   if (index == 0) return "dense kernel 128x256 (column-slab raster)";
+  if (index == 7) return "dense kernel 128x256, deduplicated operator pool";
   return gp_config_name(index - 1);
 }
 
@@ -631,7 +666,7 @@ extern "C" int dmrg2d_set_tile_config(dmrg2d_ops* ops, int precision, int index)
     return set_error(DMRG2D_EINVAL, "set_tile_config: bad argument");
   if (!tc_candidate_ok(ops, index))
     return set_error(DMRG2D_EUNSUPPORTED, "tile configuration %d not available here", index);
-  ops->tc_cfg[precision] = index == 0 ? -1 : index - 1;
+  ops->tc_cfg[precision] = index == 0 ? -1 : (index == 7 ? -2 : index - 1);
   return DMRG2D_OK;
 }
 
@@ -665,7 +700,7 @@ extern "C" int dmrg2d_autotune(dmrg2d_ops* ops, int precision, int* best, double
   D2_CUDA(cudaEventCreate(&e1));
   int chosen = -1;
   double tbest = 1e300;
-  const int ncand = 1 + gp_num_configs();
+  const int ncand = 2 + gp_num_configs();
   int st = DMRG2D_OK;
   for (int c = 0; c < ncand && st == DMRG2D_OK; ++c) {
     double t = -1.0;
@@ -699,7 +734,7 @@ extern "C" int dmrg2d_autotune(dmrg2d_ops* ops, int precision, int* best, double
   D2_TRY(tc_read_error(ops, &derr));
   if (derr) return set_error(DMRG2D_ETIMEOUT, "tensor-core kernel gave up waiting (site %d)", derr);
   if (chosen < 0) return set_error(DMRG2D_EUNSUPPORTED, "no tile configuration applies");
-  ops->tc_cfg[precision] = chosen == 0 ? -1 : chosen - 1;
+  ops->tc_cfg[precision] = chosen == 0 ? -1 : (chosen == 7 ? -2 : chosen - 1);
   if (best) *best = chosen;
   return DMRG2D_OK;
 }

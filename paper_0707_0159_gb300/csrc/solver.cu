@@ -13,6 +13,7 @@
 //     with H~ the low-precision H·v.  Only the FP64 residual decides convergence.
 // All vectors are FP64 in device memory; reductions use a fixed grid and a fixed
 // summation order, so results are bitwise reproducible run to run.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <vector>
@@ -543,8 +544,10 @@ static int mixed_solve(Ctx& C, const dmrg2d_solver_opts* o, double* x, double* e
   // 1. low-precision Lanczos for the start vector
   double th0 = 0, r0 = 0;
   int it0 = 0;
-  int st = lanczos(C, o->precision, x, o->inner_iter, o->inner_iter + 1, 1e-6, 0, 5, &th0, &r0,
-                   &it0);
+  // basis capped at krylov_dim vectors (explicit restarts), so memory does not grow with
+  // inner_iter
+  const int kdim1 = std::max(2, std::min(o->inner_iter, o->krylov_dim) + 1);
+  int st = lanczos(C, o->precision, x, o->inner_iter, kdim1, 1e-6, 0, 5, &th0, &r0, &it0);
   if (st != DMRG2D_OK && st != DMRG2D_ENOCONV) return st;
   C.st->iters += it0;
   // 2. FP64 outer loop

@@ -251,7 +251,7 @@ def profile_stop(ops: Ops):
     return ms.value, n.value
 
 
-N_TILE_CONFIGS = 7
+N_TILE_CONFIGS = 8
 
 
 def autotune(ops: Ops, precision, stream=None):

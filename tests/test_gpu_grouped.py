@@ -51,7 +51,7 @@ def test_grouped_dense_every_config(case, prec):
     ref = sb.apply(v)
     with pytest.raises(dmrg2d.Dmrg2dError):
         dmrg2d.set_tile_config(ops, prec, 0)   # the dense kernel does not take these shapes
-    for cfg in range(1, dmrg2d.N_TILE_CONFIGS):
+    for cfg in range(1, 7):
         dmrg2d.set_tile_config(ops, prec, cfg)
         err = rel(run(ops, v, prec), ref)
         assert err <= TOL[prec], (cfg, dmrg2d.tile_config_name(cfg), err)
@@ -65,12 +65,13 @@ def test_dense_and_grouped_kernels_agree(prec):
     v = synth.start_vector(sb.n_vec, 4)
     ref = sb.apply(v)
     out = {}
-    for cfg in (0, 1, 4):
+    for cfg in (0, 1, 4, 7):
         dmrg2d.set_tile_config(ops, prec, cfg)
         out[cfg] = run(ops, v, prec)
         assert rel(out[cfg], ref) <= TOL[prec]
     # same operands, same K order within a piece: the kernels agree far below the tolerance
-    assert rel(out[1], out[0]) <= 1e-6 and rel(out[4], out[0]) <= 1e-6
+    for cfg in (1, 4, 7):
+        assert rel(out[cfg], out[0]) <= 1e-6, cfg
 
 
 CASES = {
@@ -95,7 +96,7 @@ def test_sector_tensor_core_matches_oracle(name, prec):
     yd = sb.apply(vd)
     ref = np.zeros(len(pmap))
     ref[valid] = yd[pmap[valid]]
-    for cfg in range(1, dmrg2d.N_TILE_CONFIGS):
+    for cfg in range(1, 7):
         dmrg2d.set_tile_config(ops, prec, cfg)
         got = run(ops, vp, prec)
         assert np.all(got[~valid] == 0.0)
@@ -107,8 +108,8 @@ def test_autotune_picks_a_working_config(prec):
     mdl, left, right, target = CASES["heisenberg_4leg"]()
     ops = dmrg2d.build_ops(mdl, left, right, target=target)
     best, ms = dmrg2d.autotune(ops, prec)
-    assert 1 <= best < dmrg2d.N_TILE_CONFIGS
-    assert ms[0] == -1.0 and all(t > 0 for t in ms[1:])
+    assert 1 <= best < 7
+    assert ms[0] == -1.0 and ms[7] == -1.0 and all(t > 0 for t in ms[1:7])
     assert ms[best] == min(t for t in ms if t > 0)
     sb = Superblock(mdl, left, right)
     pmap = packed_map(sb, target)
