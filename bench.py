@@ -167,6 +167,23 @@ def run_reference(args):
     return 0
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The slowest rank's time (every rank gets it); x itself on a single process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_tflops(flops_per_rank_step: float, ms: float, world: int) -> float:
+    """Whole-job throughput: every rank does one H·v of its own replica per step, the job
+    step takes the slowest rank's time."""
+    return world * flops_per_rank_step / (ms * 1e-3) / 1e12
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -196,6 +213,16 @@ def run_ours(args):
     v = v_host.to(dev)
     y = torch.empty(n, dtype=out_dt, device=dev)
     stream = torch.cuda.current_stream()
+    tune = None
+    if prec in (dmrg2d.TF32, dmrg2d.BF16) and args.tile_config is not None:
+        dmrg2d.set_tile_config(ops, prec, args.tile_config)
+        tune = {"chosen": args.tile_config, "name": dmrg2d.tile_config_name(args.tile_config),
+                "ms": None}
+    elif prec in (dmrg2d.TF32, dmrg2d.BF16):
+        # tile configuration chosen by the library's autotuner (outside the timed region)
+        best, tms = dmrg2d.autotune(ops, prec)
+        tune = {"chosen": best, "name": dmrg2d.tile_config_name(best),
+                "ms": [round(t, 4) for t in tms]}
 
     def barrier():
         if world > 1:
@@ -219,12 +246,8 @@ def run_ours(args):
     k_ms, k_n = dmrg2d.profile_stop(ops)
     clocks = clk.stop()
     barrier()
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * flops / (ms * 1e-3) / 1e12
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dev)
+    value = job_tflops(flops, ms, world)
 
     # ---- end to end through the same call: pinned host -> device -> H·v -> host ----
     vh = v_host.pin_memory()
@@ -244,12 +267,8 @@ def run_ours(args):
         yh.copy_(y, non_blocking=True)
     e3.record(stream)
     torch.cuda.synchronize()
-    ms_e2e = e2.elapsed_time(e3) / ke
-    if world > 1:
-        t = torch.tensor([ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
-    e2e = {"value": world * flops / (ms_e2e * 1e-3) / 1e12, "unit": "TFLOP/s",
+    ms_e2e = max_over_ranks(e2.elapsed_time(e3) / ke, dev)
+    e2e = {"value": job_tflops(flops, ms_e2e, world), "unit": "TFLOP/s",
            "h2d_bytes_per_step": vh.numel() * vh.element_size(),
            "d2h_bytes_per_step": yh.numel() * yh.element_size()}
 
@@ -280,7 +299,7 @@ def run_ours(args):
            "data": "synthetic (seeded blocks and vector, numpy default_rng)",
            "config": {"workload": WORKLOAD, "m": 256, "d": 64, "n_legs": 3, "t": 1.0, "U": 8.0,
                       "n_vec": n, "flops_per_hv": flops, "parallelism": f"replicas{world}",
-                      "l2": "inputs larger than L2 (no flush)"},
+                      "l2": "inputs larger than L2 (no flush)", "tile_config": tune},
            "clocks": clocks, "e2e": e2e,
            "gpu_launches": k_n,
            "roofline": roof}
@@ -297,25 +316,30 @@ def run_ours(args):
 
 
 def time_to_energy(ops, n, prec, args, dev):
+    """Ground energy to a residual of tol*|E| from the same start vector: the mixed
+    solver (low-precision H·v + FP64 outer loop) and, with --tte-fp64, plain FP64 Lanczos."""
     import torch
     from paper_0707_0159_gb300 import dmrg2d, synth
     v0 = torch.from_numpy(synth.start_vector(n, 3)).to(dev)
-    res = {}
+    res = {"tol_rel_residual": args.tte_tol}
     x = v0.clone()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e_mp, st_mp, c_mp = dmrg2d.lanczos_ground(ops, x, precision=prec, refine=1, tol=args.tte_tol,
-                                              inner_iter=40, outer_max=15)
+                                              inner_iter=200, krylov_dim=40, outer_max=40)
     torch.cuda.synchronize()
-    res["mixed"] = {"seconds": time.perf_counter() - t0, "energy": e_mp, "status": c_mp, **st_mp}
+    res["mixed"] = {"precision": args.precision, "seconds": time.perf_counter() - t0,
+                    "energy": e_mp, "status": c_mp, **st_mp}
     if args.tte_fp64:
         x = v0.clone()
         t0 = time.perf_counter()
         e64, st64, c64 = dmrg2d.lanczos_ground(ops, x, precision=dmrg2d.FP64, tol=args.tte_tol,
-                                               max_iter=400, krylov_dim=100, check_every=5)
+                                               max_iter=args.tte_fp64_max_iter, krylov_dim=100,
+                                               check_every=5)
         torch.cuda.synchronize()
         res["fp64"] = {"seconds": time.perf_counter() - t0, "energy": e64, "status": c64, **st64}
-        res["rel_diff"] = abs(e_mp - e64) / abs(e64)
+        res["energy_rel_diff"] = abs(e_mp - e64) / abs(e64)
+        res["speedup"] = res["fp64"]["seconds"] / res["mixed"]["seconds"]
     return res
 
 
@@ -330,7 +354,10 @@ def main():
     ap.add_argument("--tte", action="store_true", help="also time the ground-state solve")
     ap.add_argument("--tte-fp64", action="store_true", help="with --tte: also the plain FP64 solve")
     ap.add_argument("--tte-tol", type=float, default=1e-7)
+    ap.add_argument("--tte-fp64-max-iter", type=int, default=900)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile-config", type=int, default=None,
+                    help="tensor-core tile configuration index instead of the autotuner")
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     args = ap.parse_args()
     if args.impl == "reference":
