@@ -33,6 +33,22 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "superblock H·v TFLOP/s & time to ground energy at 1e-8 rel. vs plain FP64"
+
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture of
+# this workload (profiles/hv_tc_pair_kernel_ladder3_hubbard_m256.md), keyed by tile
+# configuration name and dtype.  They hold only for the kernel source they were taken
+# on: `traffic` is reported as null when csrc/hv_tc.cu no longer has this SHA-256.
+NCU_TRAFFIC = {"hv_tc.cu sha256": None, "bytes": {}}
+
+
+def ncu_traffic(config_name, dtype):
+    import hashlib
+    src = os.path.join(ROOT, "paper_0707_0159_gb300", "csrc", "hv_tc.cu")
+    with open(src, "rb") as f:
+        digest = hashlib.sha256(f.read()).hexdigest()
+    if digest != NCU_TRAFFIC["hv_tc.cu sha256"]:
+        return None
+    return NCU_TRAFFIC["bytes"].get(f"{config_name}|{dtype}")
 WORKLOAD = "ladder3_hubbard_d64_m256_dense"
 
 
@@ -272,6 +288,8 @@ def run_ours(args):
            "h2d_bytes_per_step": vh.numel() * vh.element_size(),
            "d2h_bytes_per_step": yh.numel() * yh.element_size()}
 
+    out_dtype = {dmrg2d.FP64: "f64", dmrg2d.FP32: "f32", dmrg2d.TF32: "tf32",
+                 dmrg2d.BF16: "bf16"}[prec]
     # ---- roofline of the dominant kernel ----
     pk = peaks()
     kernel_ms = k_ms / max(k_n, 1)
@@ -288,14 +306,15 @@ def run_ours(args):
     else:
         peak, pnote, bound = 2 * 152 * 128 * 2.07e9 / 1e12, "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz", "alu"
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None, "peak_source": pnote,
+            "frac": achieved / peak,
+            "traffic": ncu_traffic(tune["name"], out_dtype) if tune else None,
+            "peak_source": pnote,
             "kernel_ms": kernel_ms, "kernel_launches": k_n}
 
     out = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": {dmrg2d.FP64: "f64", dmrg2d.FP32: "f32", dmrg2d.TF32: "tf32",
-                     dmrg2d.BF16: "bf16"}[prec],
+           "dtype": out_dtype,
            "data": "synthetic (seeded blocks and vector, numpy default_rng)",
            "config": {"workload": WORKLOAD, "m": 256, "d": 64, "n_legs": 3, "t": 1.0, "U": 8.0,
                       "n_vec": n, "flops_per_hv": flops, "parallelism": f"replicas{world}",
@@ -326,7 +345,7 @@ def time_to_energy(ops, n, prec, args, dev):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e_mp, st_mp, c_mp = dmrg2d.lanczos_ground(ops, x, precision=prec, refine=1, tol=args.tte_tol,
-                                              inner_iter=200, krylov_dim=40, outer_max=40)
+                                              inner_iter=300, krylov_dim=40, outer_max=40)
     torch.cuda.synchronize()
     res["mixed"] = {"precision": args.precision, "seconds": time.perf_counter() - t0,
                     "energy": e_mp, "status": c_mp, **st_mp}

@@ -163,6 +163,9 @@ typedef struct dmrg2d_solver_opts {
   int inner_iter;      /* mixed: low-precision steps per correction solve          */
   int outer_max;       /* mixed: maximum FP64 outer iterations                      */
   int check_every;     /* plain: convergence test every this many steps             */
+  int start_reorth;    /* mixed: Gram-Schmidt passes per step of the low-precision
+                          start (2 = full reorthogonalisation as in the plain solve,
+                          1 = one pass, 0 = the three-term recurrence only)          */
 } dmrg2d_solver_opts;
 
 typedef struct dmrg2d_solver_stats {
@@ -216,7 +219,15 @@ int dmrg2d_lanczos_ground_noalloc(const dmrg2d_ops* ops, const dmrg2d_solver_opt
  * index 1 + c is the grouped kernel (any sector structure; dense superblocks with
  * m1 % 8 == 0) with pieces of 128 x 128 (c = 0..2) or 128 x 256 (c = 3..5) in
  * column-slab, row-slab or longest-first order; index 7 is the dense kernel reading
- * each distinct operator block once (up to sign) from a small replicated pool.
+ * each distinct operator block once (up to sign) from a small replicated pool; indices
+ * 8 and 9 are the dense kernel (per-position blocks / pool) visiting the output tiles
+ * (i2, i3) in 8 x 8 patches instead of column slabs, so that the operator rows and V
+ * tiles one wave of pieces reads stay in L2; indices 10 and 11 are the CTA-pair kernel
+ * (m1 % 256 == 0, m4 % 256 == 0: two SMs share one 256 x 256 tile through M = 256
+ * tensor-core instructions) in column-slab / blocked order, and 12 and 13 the same
+ * reading the deduplicated operator pool; 14 + c (c = 0..5, sector-restricted
+ * superblocks) is grouped configuration c with the scalar moves in a separate kernel
+ * instead of the grouped kernel's epilogue.
  * dmrg2d_autotune times a complete H·v (scalar moves included) with every
  * configuration that applies (one warm-up and three timed launches each, on scratch
  * buffers it allocates and frees), keeps the fastest for later apply_H and solver
@@ -230,6 +241,16 @@ int dmrg2d_set_tile_config(dmrg2d_ops* ops, int precision, int index);
 const char* dmrg2d_tile_config_name(int index);
 
 void dmrg2d_default_solver_opts(dmrg2d_solver_opts* opts);
+
+/* Failure-detection self-test (library infrastructure; the paper has no counterpart).
+ * Every mbarrier wait in the tensor-core kernels is bounded: when it runs out, the
+ * kernel records the site in a device flag, stops issuing work, releases its tensor
+ * memory and returns, so the context stays usable and dmrg2d_check_device (or the
+ * solver) reports ETIMEOUT.  This call runs one kernel whose wait, through the same
+ * routine, is on an mbarrier that nothing arrives on, with a limit of `seconds`
+ * (0 < seconds <= 2).  Returns ETIMEOUT when the wait gave up and reported it (the
+ * expected outcome), ECUDA otherwise, EINVAL for a bad limit.  Synchronises `stream`. */
+int dmrg2d_wait_selftest(double seconds, void* stream);
 
 /* Kernel timing for benchmarks.  After dmrg2d_profile_start, every apply_H call
  * records a CUDA event pair around its dominant kernel (the fused H_l V + V H_r^T

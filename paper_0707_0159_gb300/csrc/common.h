@@ -118,9 +118,6 @@ int sec_apply(const dmrg2d_ops* ops, const void* v, void* y, int precision, cuda
 int sec_zero_padding(const dmrg2d_ops* ops, double* x, cudaStream_t s);
 int sec_dense_index(const dmrg2d_ops* ops, int64_t* out);
 int sec_count(const dmrg2d_ops* ops);
-int sec_tc_gemm(const dmrg2d_ops* ops, const void* v, float* y, int precision, int cfg,
-                cudaStream_t s);
-
 int sec_diag_tables(const dmrg2d_ops* ops, std::vector<long long>& qbase, std::vector<int>& qld,
                     std::vector<int>& qcols, std::vector<double>& rowD, std::vector<int>& rowI2,
                     std::vector<double>& colD, std::vector<int>& colI3);

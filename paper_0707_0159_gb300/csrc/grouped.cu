@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cstring>
 #include <numeric>
+#include <unordered_map>
 
 #include <cudaTypedefs.h>
 
@@ -23,13 +24,22 @@ namespace {
 using namespace tc;
 
 constexpr int GQ_MAX = 64;  // sectors per launch (V tensor maps travel as kernel parameters)
-constexpr int G_THREADS = 192;
+constexpr int G_THREADS = 320;  // producer, MMA issuer, 8 epilogue warps
+constexpr int G_EPI_WARPS = 8;
 constexpr int G_STAGES = 4;
 constexpr int G_BM = 128;
 constexpr uint32_t G_STAGE_A = 16384, G_STAGE_B = 32768, G_STAGE = G_STAGE_A + G_STAGE_B;
 constexpr uint32_t G_TMEM_COLS = 512, G_ACC_COLS = 256;
 constexpr size_t G_SMEM = G_STAGES * G_STAGE + 1024 + 256;
 constexpr int N_ORDERS = 3;  // column-slab raster, row-slab raster, longest piece first
+
+// a scalar move as the epilogue reads it: element offset of the source segment's first
+// row and column in the packed vector, the source matrix's leading dimension, coefficient
+struct GMoveD {
+  long long src;
+  int ld;
+  float c;
+};
 
 struct GMaps {
   CUtensorMap L, R;
@@ -48,6 +58,8 @@ struct GParams {
   const int* qld;
   float* y;
   int* err;
+  const GMoveD* moves;  // scalar moves, read by the epilogue
+  const void* v;       // the input vector (TF32 as float, or BF16)
   uint32_t idesc1[2], idesc2[2];
   uint32_t a2_lbo, a2_sbo, a2_kstep, a2_layout;
   int a2_boxes, a2_box_rows;
@@ -62,6 +74,7 @@ struct GDev {
   GCol* cols = nullptr;
   GK1* k1 = nullptr;
   GK2* k2 = nullptr;
+  GMoveD* moves = nullptr;
   long long* qbase = nullptr;
   int* qld = nullptr;
   float* pL32 = nullptr;
@@ -95,7 +108,7 @@ hv_tc_grouped_kernel(const __grid_constant__ GMaps maps, const GParams p) {
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull(b), 1);
-      mbar_init(tempty(b), 4);
+      mbar_init(tempty(b), G_EPI_WARPS);
     }
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -190,7 +203,8 @@ hv_tc_grouped_kernel(const __grid_constant__ GMaps maps, const GParams p) {
         for (int e = e0; e < e1 && ok; ++e) {
           const int kdim = ph == 0 ? p.k1[e].kdim : p.k2[e].kdim;
           const int neg = ph == 0 ? p.k1[e].neg : p.k2[e].neg;
-          const uint32_t id = ph == 0 ? p.idesc1[neg] : p.idesc2[neg];
+          const uint32_t id = ph == 0 ? (neg ? p.idesc1[1] : p.idesc1[0])
+                                      : (neg ? p.idesc2[1] : p.idesc2[0]);
           const int nk = (kdim + BK - 1) / BK;
           for (int kc = 0; kc < nk; ++kc) {
             if (!mbar_wait(full(stage), phase, abort)) {
@@ -227,7 +241,10 @@ hv_tc_grouped_kernel(const __grid_constant__ GMaps maps, const GParams p) {
     }
   } else if (warp >= 2) {
     // ------------------------------- epilogue -----------------------------------
+    // two warps per TMEM lane quadrant, alternating 32-column chunks; the scalar moves of
+    // the tile's (row segment, column segment) are added from V before the store
     const int q4 = warp & 3;
+    const int half = (warp - 2) >> 2;
     int acc = 0;
     uint32_t aphase = 0;
     for (int ti = blockIdx.x; ti < p.ntiles; ti += gridDim.x) {
@@ -246,7 +263,7 @@ hv_tc_grouped_kernel(const __grid_constant__ GMaps maps, const GParams p) {
       const int row = 32 * q4 + lane;
       const long long ld = p.qld[rs.q];
       float* yq = p.y + p.qbase[rs.q] + rs.off + t.r_in + row + ld * (cs.off + t.c_in);
-      for (int ch = 0; ch < p.bn / 32 && ch * 32 < cols_valid; ++ch) {
+      for (int ch = half; ch < p.bn / 32 && ch * 32 < cols_valid; ch += 2) {
         uint32_t v[32];
         if (has_k) {
           tmem_ld32(tmem_base + ((uint32_t)(32 * q4) << 16) + acc * G_ACC_COLS + ch * 32, v);
@@ -254,12 +271,49 @@ hv_tc_grouped_kernel(const __grid_constant__ GMaps maps, const GParams p) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[j] = 0u;
         }
+        float o[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) o[j] = __uint_as_float(v[j]);
+        const bool real = row < rows_valid;
+        if (real && p.moves) {
+          // two moves per iteration: 64 loads in flight per thread
+          const long long rc = t.r_in + row;
+          const long long cc = t.c_in + ch * 32;
+          for (int e = t.mb; e < t.me; e += 2) {
+            const bool two = e + 1 < t.me;
+            const GMoveD ma = p.moves[e];
+            const GMoveD mb = two ? p.moves[e + 1] : ma;
+            const float cb = two ? mb.c : 0.f;
+            const long long oa = ma.src + rc + (long long)ma.ld * cc;
+            const long long ob = mb.src + rc + (long long)mb.ld * cc;
+            float va[32], vb[32];
+            if (p.bf16) {
+              const __nv_bfloat16* A = (const __nv_bfloat16*)p.v + oa;
+              const __nv_bfloat16* B = (const __nv_bfloat16*)p.v + ob;
+#pragma unroll
+              for (int j = 0; j < 32; ++j) {
+                const bool in = ch * 32 + j < cols_valid;
+                va[j] = in ? __bfloat162float(A[(long long)ma.ld * j]) : 0.f;
+                vb[j] = in ? __bfloat162float(B[(long long)mb.ld * j]) : 0.f;
+              }
+            } else {
+              const float* A = (const float*)p.v + oa;
+              const float* B = (const float*)p.v + ob;
+#pragma unroll
+              for (int j = 0; j < 32; ++j) {
+                const bool in = ch * 32 + j < cols_valid;
+                va[j] = in ? __ldg(A + (long long)ma.ld * j) : 0.f;
+                vb[j] = in ? __ldg(B + (long long)mb.ld * j) : 0.f;
+              }
+            }
+#pragma unroll
+            for (int j = 0; j < 32; ++j) o[j] += ma.c * va[j] + cb * vb[j];
+          }
+        }
         if (row < rows_out) {
-          const bool real = row < rows_valid;
 #pragma unroll
           for (int j = 0; j < 32; ++j)
-            if (ch * 32 + j < cols_valid)
-              yq[ld * (ch * 32 + j)] = real ? __uint_as_float(v[j]) : 0.f;
+            if (ch * 32 + j < cols_valid) yq[ld * (ch * 32 + j)] = real ? o[j] : 0.f;
         }
       }
       tc_fence_before();
@@ -440,6 +494,16 @@ int gp_finalise(dmrg2d_ops* ops, GroupPlan* g, cudaStream_t s) {
     for (int e = c.k2b; e < c.k2e; ++e) w += (g->k2[e].kdim + 63) / 64;
     return w;
   };
+  // move range of each destination (row segment, column segment)
+  std::unordered_map<long long, std::pair<int, int>> mv_of;
+  for (const GMoveDst& md : g->mdst)
+    mv_of[(long long)md.rs * (long long)g->cols.size() + md.cs] = {md.mb, md.me};
+  auto tile = [&](int r, int c, int ri, int ci) {
+    auto it = mv_of.find((long long)r * (long long)g->cols.size() + c);
+    const int mb = it == mv_of.end() ? 0 : it->second.first;
+    const int me = it == mv_of.end() ? 0 : it->second.second;
+    return GTile{r, c, ri, ci, mb, me};
+  };
   std::vector<GTile> lists[2][N_ORDERS];
   for (int b = 0; b < 2; ++b) {
     const int bn = b ? 256 : 128;
@@ -451,7 +515,7 @@ int gp_finalise(dmrg2d_ops* ops, GroupPlan* g, cudaStream_t s) {
           for (size_t r = 0; r < g->rows.size(); ++r) {
             if (g->rows[r].q != q) continue;
             for (int ri = 0; ri < g->rows[r].dim; ri += G_BM)
-              colmaj.push_back({(int)r, (int)c, ri, ci});
+              colmaj.push_back(tile((int)r, (int)c, ri, ci));
           }
       }
       for (size_t r = 0; r < g->rows.size(); ++r) {
@@ -460,7 +524,7 @@ int gp_finalise(dmrg2d_ops* ops, GroupPlan* g, cudaStream_t s) {
           for (size_t c = 0; c < g->cols.size(); ++c) {
             if (g->cols[c].q != q) continue;
             for (int ci = 0; ci < g->cols[c].dim; ci += bn)
-              rowmaj.push_back({(int)r, (int)c, ri, ci});
+              rowmaj.push_back(tile((int)r, (int)c, ri, ci));
           }
       }
     }
@@ -483,6 +547,16 @@ int gp_finalise(dmrg2d_ops* ops, GroupPlan* g, cudaStream_t s) {
   if (st == DMRG2D_OK) st = gup(D, g->cols, &D->cols, nb, s);
   if (st == DMRG2D_OK) st = gup(D, g->k1, &D->k1, nb, s);
   if (st == DMRG2D_OK) st = gup(D, g->k2, &D->k2, nb, s);
+  std::vector<GMoveD> mvd;
+  mvd.reserve(g->moves.size());
+  for (const GMove& m : g->moves) {
+    const GRow& r = g->rows[m.rs];
+    const GCol& c = g->cols[m.cs];
+    if (r.q != c.q) return set_error(DMRG2D_EINVAL, "grouped plan: move across matrices");
+    const long long ldq = g->qld[r.q];
+    mvd.push_back({g->qbase[r.q] + r.off + ldq * c.off, (int)ldq, m.c});
+  }
+  if (st == DMRG2D_OK) st = gup(D, mvd, &D->moves, nb, s);
   if (st == DMRG2D_OK) st = gup(D, g->qbase, &D->qbase, nb, s);
   if (st == DMRG2D_OK) st = gup(D, g->qld, &D->qld, nb, s);
   double *dL = nullptr, *dR = nullptr;
@@ -548,7 +622,7 @@ void gp_release(GroupPlan* g) {
 }
 
 int gp_launch(const dmrg2d_ops* ops, const GroupPlan* g, const void* v, float* y, int precision,
-              int cfg, cudaStream_t s) {
+              int cfg, cudaStream_t s, bool fuse_moves) {
   const GDev* D = (const GDev*)g->dev;
   if (!D) return set_error(DMRG2D_EUNSUPPORTED, "grouped plan not prepared");
   if (cfg < 0 || cfg >= 2 * N_ORDERS) return set_error(DMRG2D_EINVAL, "bad tile config %d", cfg);
@@ -582,6 +656,8 @@ int gp_launch(const dmrg2d_ops* ops, const GroupPlan* g, const void* v, float* y
   p.qld = D->qld;
   p.y = y;
   p.err = D->err;
+  p.moves = fuse_moves ? D->moves : nullptr;
+  p.v = v;
   const int fmt = bf ? 1 : 2;
   for (int n = 0; n < 2; ++n) {
     p.idesc1[n] = make_idesc(fmt, 0, G_BM, bn, n, 0);
@@ -615,6 +691,9 @@ int gp_pool_views(const GroupPlan* g, int precision, int bn, const CUtensorMap**
   *mR = &D->mR[pi][bn == 256 ? 1 : 0];
   *k1 = D->k1;
   *k2 = D->k2;
+  *rowsL = std::max(D->prL, 1);  // replica r of a pool starts at row r * rows
+  *rowsR = std::max(D->prR, 1);
+  *copies = D->copies;
   return DMRG2D_OK;
 }
 

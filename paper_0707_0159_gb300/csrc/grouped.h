@@ -31,6 +31,16 @@ struct GK2 {
 };
 struct GTile {
   int rs, cs, r_in, c_in;
+  int mb, me;  // scalar moves into this tile's (row segment, column segment): moves[mb..me)
+};
+// scalar tile move Y(dst rs, dst cs) += c V(rs, cs): same rows within the row segments,
+// same columns within the column segments (H_c and off-diagonal column terms)
+struct GMove {
+  int rs, cs;
+  float c;
+};
+struct GMoveDst {
+  int rs, cs, mb, me;  // destination segments, range in GroupPlan::moves
 };
 
 // Distinct operator blocks, deduplicated up to sign.
@@ -53,6 +63,8 @@ struct GroupPlan {
   std::vector<GCol> cols;
   std::vector<GK1> k1;  // a_pool holds the pool ENTRY index until finalise()
   std::vector<GK2> k2;
+  std::vector<GMoveDst> mdst;  // scalar moves, grouped by destination (optional)
+  std::vector<GMove> moves;
   BlockPool poolL, poolR;
   int copies = 1;       // pool replicas (CTAs read replica blockIdx % copies: no L2 hot spot)
   void* dev = nullptr;  // device state (grouped.cu)
@@ -62,9 +74,10 @@ struct GroupPlan {
 // device bytes.  Fails with EUNSUPPORTED when the plan does not fit the kernel.
 int gp_finalise(dmrg2d_ops* ops, GroupPlan* g, cudaStream_t s);
 void gp_release(GroupPlan* g);
-// Y(all V_q) = grouped H_l V + V H_r^T (scalar moves not included); cfg = tile config
+// Y(all V_q) = grouped H_l V + V H_r^T, plus the plan's scalar moves when fuse_moves;
+// cfg = tile layout 0 .. gp_num_configs() - 1
 int gp_launch(const dmrg2d_ops* ops, const GroupPlan* g, const void* v, float* y, int precision,
-              int cfg, cudaStream_t s);
+              int cfg, cudaStream_t s, bool fuse_moves = true);
 int gp_read_error(const GroupPlan* g, int* code);
 // pool tensor maps and per-block entries (CSR order of the build) for another kernel
 int gp_pool_views(const GroupPlan* g, int precision, int bn, const CUtensorMap** mL,

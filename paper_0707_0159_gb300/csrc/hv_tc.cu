@@ -10,14 +10,16 @@
 // (H_c, off-diagonal column terms), Y(i2,i3) += c V(i2',i3'), reading the source rows
 // from L2 while the MMAs of the next piece run in the other accumulator.
 //
-// Kernel organisation (one persistent CTA per SM, 192 threads):
+// Kernel organisation (one persistent CTA per SM, 320 threads):
 //   warp 0   TMA producer: 4-stage ring of 48 KB (A 16 KB + B up to 32 KB), 128B swizzle
 //   warp 1   TMEM owner (512 columns = two 128 x 256 FP32 accumulators) and MMA issuer
-//   warps 2-5 epilogue: tcgen05.ld of the finished accumulator, scalar moves, FP32 stores
+//   warps 2-9 epilogue: tcgen05.ld of the finished accumulator, scalar moves, FP32 stores
 // Every mbarrier wait is bounded (globaltimer); on timeout the CTA raises an error flag,
 // stops issuing work, releases its tensor memory and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+
+#include <algorithm>
 
 #include "common.h"
 #include "grouped.h"
@@ -44,6 +46,7 @@ struct TcParams {
   int m1, m4, d, BN;
   int n_mt, n_nt;
   int tiles;
+  const int* order;  // piece order (column-slab numbering), nullptr: column-slab order
   int kblk1, kblk2;
   int BK;
   int64_t ld;
@@ -76,9 +79,68 @@ struct TileCoord {
   int i2, mt, i3, nt;
 };
 __device__ __forceinline__ TileCoord decode(const TcParams& p, int t) {
+  if (p.order) t = __ldg(p.order + t);
   const int nm = p.d * p.n_mt;
   const int mg = t % nm, ng = t / nm;  // consecutive tiles walk down one column slab of V
   return {mg / p.n_mt, mg % p.n_mt, ng / p.n_nt, ng % p.n_nt};
+}
+
+// Epilogue of one piece (rows mt*128.. of block row i2, columns of block column i3 / nt):
+// accumulator columns from tensor memory at tacc, plus the scalar tile moves, stored to Y.
+// Warp (q, half) handles TMEM lane quadrant q and half of the 32-column chunks.
+__device__ __forceinline__ void epilogue_piece(const TcParams& p, const TileCoord& c, int mt,
+                                               uint32_t tacc, int q, int half, int lane) {
+  const int row = 32 * q + lane;
+  const int64_t r = (int64_t)c.i2 * p.m1 + mt * BM + row;
+  const int64_t col0 = (int64_t)c.i3 * p.m4 + (int64_t)c.nt * p.BN;
+  const int tt = c.i2 + p.d * c.i3;
+  const int e0 = p.fuse ? p.Cptr[tt] : 0, e1 = p.fuse ? p.Cptr[tt + 1] : 0;
+  const int nch = p.BN / 32;
+  for (int ch = half * (nch / 2); ch < (half + 1) * (nch / 2); ++ch) {
+    uint32_t v[32];
+    tmem_ld32(tacc + ((uint32_t)(32 * q) << 16) + ch * 32, v);
+    float o[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) o[j] = __uint_as_float(v[j]);
+    // scalar tile moves of this piece: Y(i2,i3) += c V(i2',i3') on the same rows and
+    // columns of the source tile; a warp reads 32 consecutive rows per column, two
+    // moves at a time to keep more loads in flight
+    for (int e = e0; e < e1; e += 2) {
+      const bool two = e + 1 < e1;
+      const int sa = p.Csrc[e], sb = two ? p.Csrc[e + 1] : sa;
+      const float ca = p.Cval[e], cb = two ? p.Cval[e + 1] : 0.f;
+      const int64_t ra = (int64_t)(sa % p.d) * p.m1 + mt * BM + row;
+      const int64_t rb = (int64_t)(sb % p.d) * p.m1 + mt * BM + row;
+      const int64_t ka = (int64_t)(sa / p.d) * p.m4 + (int64_t)c.nt * p.BN + ch * 32;
+      const int64_t kb = (int64_t)(sb / p.d) * p.m4 + (int64_t)c.nt * p.BN + ch * 32;
+      if (p.bf16) {
+        const __nv_bfloat16* A = (const __nv_bfloat16*)p.v + ra + p.ld * ka;
+        const __nv_bfloat16* B = (const __nv_bfloat16*)p.v + rb + p.ld * kb;
+        float va[32], vb[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          va[j] = __bfloat162float(A[p.ld * j]);
+          vb[j] = __bfloat162float(B[p.ld * j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) o[j] += ca * va[j] + cb * vb[j];
+      } else {
+        const float* A = (const float*)p.v + ra + p.ld * ka;
+        const float* B = (const float*)p.v + rb + p.ld * kb;
+        float va[32], vb[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          va[j] = __ldg(A + p.ld * j);
+          vb[j] = __ldg(B + p.ld * j);
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) o[j] += ca * va[j] + cb * vb[j];
+      }
+    }
+    float* yp = p.y + r + p.ld * (col0 + ch * 32);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) yp[p.ld * j] = o[j];
+  }
 }
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -187,37 +249,40 @@ hv_tc_kernel(const __grid_constant__ CUtensorMap mHL, const __grid_constant__ CU
         const int e0 = ph == 0 ? p.Lptr[c.i2] : p.Rptr[c.i3];
         const int e1 = ph == 0 ? p.Lptr[c.i2 + 1] : p.Rptr[c.i3 + 1];
         const int kb = ph == 0 ? p.kblk1 : p.kblk2;
-        const int nsteps = (e1 - e0) * kb;
-        for (int st = 0; st < nsteps; ++st) {
-          if (!mbar_wait(full(stage), phase, abort)) {
-            raise_abort(abort, p.err, 3);
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t a_s = smem_u32(smem + stage * STAGE_BYTES);
-          const uint32_t b_s = a_s + STAGE_A;
-          const int eb = e0 + st / kb;  // operator block of this K step
-          const int neg = p.pooled ? (ph == 0 ? p.k1[eb].neg : p.k2[eb].neg) : 0;
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            uint64_t ad, bd;
-            uint32_t id;
-            if (ph == 0) {
-              ad = sdesc(a_s + k * 32, 16, 1024);
-              id = p.idesc1[neg];
-            } else {
-              ad = sdesc(a_s + k * p.a2_kstep, p.a2_lbo, p.a2_sbo, p.a2_layout);
-              id = p.idesc2[neg];
+        for (int e = e0; e < e1 && ok; ++e) {
+          // instruction descriptor of this operator block, chosen once per block from
+          // statically indexed parameters (the issuing thread is on the critical path)
+          const int neg = p.pooled ? (ph == 0 ? p.k1[e].neg : p.k2[e].neg) : 0;
+          const uint32_t idb = ph == 0 ? (neg ? p.idesc1[1] : p.idesc1[0])
+                                       : (neg ? p.idesc2[1] : p.idesc2[0]);
+          for (int kc = 0; kc < kb; ++kc) {
+            if (!mbar_wait(full(stage), phase, abort)) {
+              raise_abort(abort, p.err, 3);
+              ok = false;
+              break;
             }
-            bd = sdesc(b_s + k * 32, 16, 1024);
-            umma(dt, ad, bd, id, accum, p.bf16);
-            accum = 1;
-          }
-          umma_commit(empty(stage));
-          if (++stage == STAGES) {
-            stage = 0;
-            phase ^= 1u;
+            tc_fence_after();
+            const uint32_t a_s = smem_u32(smem + stage * STAGE_BYTES);
+            const uint32_t b_s = a_s + STAGE_A;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              uint64_t ad, bd;
+              uint32_t id;
+              if (ph == 0) {
+                ad = sdesc(a_s + k * 32, 16, 1024);
+              } else {
+                ad = sdesc(a_s + k * p.a2_kstep, p.a2_lbo, p.a2_sbo, p.a2_layout);
+              }
+              id = idb;
+              bd = sdesc(b_s + k * 32, 16, 1024);
+              umma(dt, ad, bd, id, accum, p.bf16);
+              accum = 1;
+            }
+            umma_commit(empty(stage));
+            if (++stage == STAGES) {
+              stage = 0;
+              phase ^= 1u;
+            }
           }
         }
       }
@@ -241,57 +306,7 @@ hv_tc_kernel(const __grid_constant__ CUtensorMap mHL, const __grid_constant__ CU
         break;
       }
       tc_fence_after();
-      const int row = 32 * q + lane;
-      const int64_t r = (int64_t)c.i2 * p.m1 + c.mt * BM + row;
-      const int64_t col0 = (int64_t)c.i3 * p.m4 + (int64_t)c.nt * p.BN;
-      const int tt = c.i2 + p.d * c.i3;
-      const int e0 = p.fuse ? p.Cptr[tt] : 0, e1 = p.fuse ? p.Cptr[tt + 1] : 0;
-      const int nch = p.BN / 32;
-      for (int ch = half * (nch / 2); ch < (half + 1) * (nch / 2); ++ch) {
-        uint32_t v[32];
-        tmem_ld32(tmem_base + ((uint32_t)(32 * q) << 16) + acc * ACC_COLS + ch * 32, v);
-        float o[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) o[j] = __uint_as_float(v[j]);
-        // scalar tile moves of this piece: Y(i2,i3) += c V(i2',i3') on the same rows and
-        // columns of the source tile; a warp reads 32 consecutive rows per column, two
-        // moves at a time to keep more loads in flight
-        for (int e = e0; e < e1; e += 2) {
-          const bool two = e + 1 < e1;
-          const int sa = p.Csrc[e], sb = two ? p.Csrc[e + 1] : sa;
-          const float ca = p.Cval[e], cb = two ? p.Cval[e + 1] : 0.f;
-          const int64_t ra = (int64_t)(sa % p.d) * p.m1 + c.mt * BM + row;
-          const int64_t rb = (int64_t)(sb % p.d) * p.m1 + c.mt * BM + row;
-          const int64_t ka = (int64_t)(sa / p.d) * p.m4 + (int64_t)c.nt * p.BN + ch * 32;
-          const int64_t kb = (int64_t)(sb / p.d) * p.m4 + (int64_t)c.nt * p.BN + ch * 32;
-          if (p.bf16) {
-            const __nv_bfloat16* A = (const __nv_bfloat16*)p.v + ra + p.ld * ka;
-            const __nv_bfloat16* B = (const __nv_bfloat16*)p.v + rb + p.ld * kb;
-            float va[32], vb[32];
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              va[j] = __bfloat162float(A[p.ld * j]);
-              vb[j] = __bfloat162float(B[p.ld * j]);
-            }
-#pragma unroll
-            for (int j = 0; j < 32; ++j) o[j] += ca * va[j] + cb * vb[j];
-          } else {
-            const float* A = (const float*)p.v + ra + p.ld * ka;
-            const float* B = (const float*)p.v + rb + p.ld * kb;
-            float va[32], vb[32];
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              va[j] = __ldg(A + p.ld * j);
-              vb[j] = __ldg(B + p.ld * j);
-            }
-#pragma unroll
-            for (int j = 0; j < 32; ++j) o[j] += ca * va[j] + cb * vb[j];
-          }
-        }
-        float* yp = p.y + r + p.ld * (col0 + ch * 32);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) yp[p.ld * j] = o[j];
-      }
+      epilogue_piece(p, c, c.mt, tmem_base + acc * ACC_COLS, q, half, lane);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(tempty(acc));
@@ -312,34 +327,227 @@ hv_tc_kernel(const __grid_constant__ CUtensorMap mHL, const __grid_constant__ CU
   }
 }
 
-// Y(i2,i3) += sum c * V(i2',i3') over the scalar tile moves; one block per (tile, 8 columns).
-template <typename Tin>
-__global__ void __launch_bounds__(256)
-k_scalar_moves(const Tin* __restrict__ v, float* __restrict__ y, const int* __restrict__ Cptr,
-               const int* __restrict__ Csrc, const float* __restrict__ Cval, int m1, int m4, int d,
-               int64_t ld) {
-  const int t = blockIdx.x;
-  const int i2 = t % d, i3 = t / d;
-  const int j0 = blockIdx.y * 8;
-  const int e0 = Cptr[t], e1 = Cptr[t + 1];
-  if (e0 == e1) return;
-  for (int i = threadIdx.x; i < m1; i += 256) {
-    float acc[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j] = 0.f;
-    for (int e = e0; e < e1; ++e) {
-      const int s = Csrc[e];
-      const float cv = Cval[e];
-      const Tin* S = v + (int64_t)(s % d) * m1 + i + ld * ((int64_t)(s / d) * m4 + j0);
-#pragma unroll
-      for (int j = 0; j < 8; ++j)
-        if (j0 + j < m4) acc[j] += cv * (float)S[ld * j];
+// ---- CTA-pair variant (cluster of 2, tcgen05 cta_group::2) -------------------------------
+// The two CTAs of a cluster compute one 256 x BN tile (both 128-row pieces of a 256-row
+// block row) with M = 256 MMAs issued by the even CTA: each CTA stages its own 128 rows
+// of A and HALF of the B columns, so a stage is 32 KB instead of 48 KB per SM, six stages
+// fit, and the B bytes each SM pulls from L2 halve.  The accumulator rows of CTA r live
+// in its own tensor memory; its epilogue warps handle piece mt = 2 * pair + r as in the
+// single-CTA kernel.
+//   full[s]   (even CTA) : its producer's expect_tx for both CTAs' bytes; both CTAs'
+//                          TMA loads complete on it
+//   empty[s]  (both)     : multicast commit after the MMAs that read stage s
+//   tfull[b]  (both)     : multicast commit after the last MMA of a tile
+//   tempty[b] (even CTA) : one arrival per epilogue warp of both CTAs
+// Both CTAs meet at cluster barriers after set-up and before releasing tensor memory, so
+// neither exits while the other may still touch its shared or tensor memory.
+constexpr int P_STAGES = 6;
+constexpr uint32_t P_STAGE_A = 16384;
+constexpr uint32_t P_STAGE = 32768;  // A 128 rows + B 128 columns, BK of K
+constexpr size_t P_SMEM = P_STAGES * P_STAGE + 1024 + 256;
+constexpr int P_HALF = 128;          // B columns per CTA
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
+hv_tc_pair_kernel(const __grid_constant__ CUtensorMap mHL, const __grid_constant__ CUtensorMap mHR,
+                  const __grid_constant__ CUtensorMap mVk, const __grid_constant__ CUtensorMap mVm,
+                  const TcParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(smem + P_STAGES * P_STAGE);
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * P_STAGES + 4);
+  volatile int* abort = (volatile int*)(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_ctarank();
+  const bool even = rank == 0;
+  auto full = [&](int s) { return smem_u32(bars + s); };
+  auto empty = [&](int s) { return smem_u32(bars + P_STAGES + s); };
+  auto tfull = [&](int b) { return smem_u32(bars + 2 * P_STAGES + b); };
+  auto tempty = [&](int b) { return smem_u32(bars + 2 * P_STAGES + 2 + b); };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < P_STAGES; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
     }
-    float* Y = y + (int64_t)i2 * m1 + i + ld * ((int64_t)i3 * m4 + j0);
-#pragma unroll
-    for (int j = 0; j < 8; ++j)
-      if (j0 + j < m4) Y[ld * j] += acc[j];
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull(b), 1);
+      mbar_init(tempty(b), 2 * EPI_WARPS);
+    }
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
+  if (warp == 1) {  // one warp of each CTA allocates the pair's tensor memory together
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const int cid = (int)cluster_id_x(), ncl = (int)ncluster_x();
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------- TMA producer (both CTAs) -------------------------
+    int stage = 0;
+    uint32_t phase = 0;
+    for (int t = cid; t < p.tiles && !*abort; t += ncl) {
+      const TileCoord c = decode(p, t);  // c.mt: pair of 128-row pieces
+      const int mt = 2 * c.mt + (int)rank;
+      const int r0 = c.i2 * p.m1 + mt * BM;
+      const int cb = c.nt * p.BN + (int)rank * P_HALF;  // this CTA's B columns
+      for (int ph = 0; ph < 2; ++ph) {
+        const int e0 = ph == 0 ? p.Lptr[c.i2] : p.Rptr[c.i3];
+        const int e1 = ph == 0 ? p.Lptr[c.i2 + 1] : p.Rptr[c.i3 + 1];
+        const int kb = ph == 0 ? p.kblk1 : p.kblk2;
+        for (int e = e0; e < e1; ++e) {
+          const int nb = ph == 0 ? p.Lcol[e] : p.Rcol[e];
+          for (int kc = 0; kc < kb; ++kc) {
+            if (!mbar_wait(empty(stage), phase ^ 1u, abort)) {
+              raise_abort(abort, p.err, 11);
+              goto producer_done;
+            }
+            const uint32_t a_s = smem_u32(smem + stage * P_STAGE);
+            const uint32_t b_s = a_s + P_STAGE_A;
+            if (even) mbar_expect_tx(full(stage), 2 * p.tx_bytes);
+            const uint32_t fb = mapa(full(stage), 0);
+            if (ph == 0) {
+              const int arow = p.pooled ? p.k1[e].a_pool + (int)(cid % p.copies) * p.poolL_rows
+                                        : e * p.m1;
+              tma_load_2d_pair(a_s, &mHL, fb, kc * p.BK, arow + mt * BM);
+              tma_load_2d_pair(b_s, &mVk, fb, nb * p.m1 + kc * p.BK, c.i3 * p.m4 + cb);
+            } else {
+              for (int b = 0; b < p.a2_boxes; ++b)
+                tma_load_2d_pair(a_s + b * p.a2_lbo, &mVm, fb, r0 + b * p.a2_box_rows,
+                                 nb * p.m4 + kc * p.BK);
+              const int brow = p.pooled ? p.k2[e].b_pool + (int)(cid % p.copies) * p.poolR_rows
+                                        : e * p.m4;
+              tma_load_2d_pair(b_s, &mHR, fb, kc * p.BK, brow + cb);
+            }
+            if (++stage == P_STAGES) {
+              stage = 0;
+              phase ^= 1u;
+            }
+          }
+        }
+      }
+    }
+  producer_done:;
+  } else if (warp == 1 && lane == 0 && even) {
+    // ------------------------- MMA issuer (even CTA) ----------------------------
+    int stage = 0;
+    uint32_t phase = 0;
+    int acc = 0;
+    uint32_t aphase = 0;
+    for (int t = cid; t < p.tiles && !*abort; t += ncl) {
+      const TileCoord c = decode(p, t);
+      if (!mbar_wait(tempty(acc), aphase ^ 1u, abort)) {
+        raise_abort(abort, p.err, 12);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t dt = tmem_base + acc * ACC_COLS;
+      uint32_t accum = 0;
+      bool ok = true;
+      for (int ph = 0; ph < 2 && ok; ++ph) {
+        const int e0 = ph == 0 ? p.Lptr[c.i2] : p.Rptr[c.i3];
+        const int e1 = ph == 0 ? p.Lptr[c.i2 + 1] : p.Rptr[c.i3 + 1];
+        const int kb = ph == 0 ? p.kblk1 : p.kblk2;
+        for (int e = e0; e < e1 && ok; ++e) {
+          // instruction descriptor of this operator block, chosen once per block from
+          // statically indexed parameters (the issuing thread is on the critical path)
+          const int neg = p.pooled ? (ph == 0 ? p.k1[e].neg : p.k2[e].neg) : 0;
+          const uint32_t idb = ph == 0 ? (neg ? p.idesc1[1] : p.idesc1[0])
+                                       : (neg ? p.idesc2[1] : p.idesc2[0]);
+          for (int kc = 0; kc < kb; ++kc) {
+            if (!mbar_wait(full(stage), phase, abort)) {
+              raise_abort(abort, p.err, 13);
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t a_s = smem_u32(smem + stage * P_STAGE);
+            const uint32_t b_s = a_s + P_STAGE_A;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              uint64_t ad;
+              uint32_t id;
+              if (ph == 0) {
+                ad = sdesc(a_s + k * 32, 16, 1024);
+              } else {
+                ad = sdesc(a_s + k * p.a2_kstep, p.a2_lbo, p.a2_sbo, p.a2_layout);
+              }
+              id = idb;
+              umma_pair(dt, ad, sdesc(b_s + k * 32, 16, 1024), id, accum, p.bf16);
+              accum = 1;
+            }
+            umma_commit_pair(empty(stage));
+            if (++stage == P_STAGES) {
+              stage = 0;
+              phase ^= 1u;
+            }
+          }
+        }
+      }
+      if (!ok) break;
+      umma_commit_pair(tfull(acc));
+      if (++acc == 2) {
+        acc = 0;
+        aphase ^= 1u;
+      }
+    }
+  } else if (warp >= 2) {
+    // ------------------------- epilogue (both CTAs) -----------------------------
+    const int q = warp & 3;
+    const int half = (warp - 2) >> 2;
+    const uint32_t te0 = mapa(tempty(0), 0), te1 = mapa(tempty(1), 0);
+    int acc = 0;
+    uint32_t aphase = 0;
+    for (int t = cid; t < p.tiles; t += ncl) {
+      const TileCoord c = decode(p, t);
+      if (!mbar_wait(tfull(acc), aphase, abort)) {
+        raise_abort(abort, p.err, 14);
+        break;
+      }
+      tc_fence_after();
+      epilogue_piece(p, c, 2 * c.mt + (int)rank, tmem_base + acc * ACC_COLS, q, half, lane);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(acc ? te1 : te0);
+      if (++acc == 2) {
+        acc = 0;
+        aphase ^= 1u;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// Self-test of the bounded waits: one thread waits on an mbarrier that nothing arrives on,
+// with the same routine the tensor-core kernels use, gives up after limit_ns, and records
+// the give-up in *err as the kernels do (site 99).
+__global__ void k_wait_selftest(int* err, uint64_t limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x != 0) return;
+  abort_flag = 0;
+  mbar_init(smem_u32(&bar), 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (!mbar_wait(smem_u32(&bar), 0, (volatile int*)&abort_flag, limit_ns))
+    raise_abort((volatile int*)&abort_flag, err, 99);
 }
 
 // ---- host side ----------------------------------------------------------------------------
@@ -349,6 +557,11 @@ struct TcState {
   float* HLt = nullptr;  // TF32-rounded copies of the operator blocks
   float* HRt = nullptr;
   int* err = nullptr;
+  int* order = nullptr;   // blocked piece order of the dense kernel
+  int* order2 = nullptr;  // the same for the CTA-pair kernel (256-row pieces)
+  bool pair_ok = false;   // CTA-pair kernel applies (m1 % 256 == 0, 256-wide pieces)
+  int pairs = 0;          // CTA pairs resident at once (persistent grid of the pair kernel)
+  CUtensorMap mHR2[2];    // H_r blocks in 128-row boxes (half a piece's columns)
   CUtensorMap mHL[2], mHR[2];  // [0] TF32, [1] BF16
   int sms = 0;
   int BN = 0;
@@ -396,6 +609,43 @@ __global__ void k_round_tf32(const double* __restrict__ x, float* __restrict__ o
 }
 
 
+// Blocked piece order of the dense kernel.  A piece (i2, mt, i3, nt) reads the column
+// operators' neighbours of i2 (phase 1, column slab i3), of i3 (phase 2, row slab i2)
+// and the scalar-move sources; the column-slab order streams all of H_l through L2 once
+// per wave.  Here consecutive pieces cover a B x B patch of output tiles (i2, i3), with
+// both halves mt (and all nt) of a tile next to each other, so one wave touches B rows
+// of H_l, B rows of H_r and the V tiles around the patch.  Patches follow a Gray code of
+// their linear index when both patch counts are powers of two (one patch coordinate
+// bit changes per step: for column bases whose operators flip bits of the state label,
+// successive patches share neighbours), else a serpentine walk.  Returns column-slab
+// numbers (t = i2 n_mt + mt + d n_mt (i3 n_nt + nt)).
+// tc_cfg value of the CTA-pair kernel in blocked order (dense-kernel variant 6)
+constexpr int kPairBlockedCfg = -1 - 6;
+
+std::vector<int> blocked_order(int d, int n_mt, int n_nt, int B) {
+  const int nb = (d + B - 1) / B;
+  const bool pow2 = (nb & (nb - 1)) == 0;
+  std::vector<int> out;
+  out.reserve((size_t)d * n_mt * d * n_nt);
+  for (int h = 0; h < nb * nb; ++h) {
+    int h2, h3;
+    if (pow2) {
+      const int g = h ^ (h >> 1);
+      h2 = g % nb;
+      h3 = g / nb;
+    } else {
+      h3 = h / nb;
+      h2 = (h3 & 1) ? nb - 1 - h % nb : h % nb;
+    }
+    for (int i3 = h3 * B; i3 < std::min(d, (h3 + 1) * B); ++i3)
+      for (int i2 = h2 * B; i2 < std::min(d, (h2 + 1) * B); ++i2)
+        for (int nt = 0; nt < n_nt; ++nt)
+          for (int mt = 0; mt < n_mt; ++mt)
+            out.push_back(i2 * n_mt + mt + d * n_mt * (i3 * n_nt + nt));
+  }
+  return out;
+}
+
 }  // namespace
 
 int tc_prepare(dmrg2d_ops* ops, cudaStream_t s, const std::vector<double>& HL,
@@ -440,13 +690,45 @@ int tc_prepare(dmrg2d_ops* ops, cudaStream_t s, const std::vector<double>& HL,
       st = make_map(&T->mHL[b], hl, bf, m1, nL * m1, BK, BM);
       if (st == DMRG2D_OK) st = make_map(&T->mHR[b], hr, bf, m4, nR * m4, BK, T->BN);
     }
+    T->pair_ok = m1 % 256 == 0 && T->BN == 256;
+    for (int b = 0; b < 2 && st == DMRG2D_OK && T->pair_ok; ++b) {
+      const bool bf = b == 1;
+      st = make_map(&T->mHR2[b], bf ? (const void*)ops->dev.HR16 : (const void*)T->HRt, bf, m4,
+                    nR * m4, bf ? 64 : 32, P_HALF);
+    }
+    auto upload_order = [&](int** dst, int pieces_mt) {
+      const std::vector<int> ord = blocked_order(d, pieces_mt, m4 / T->BN, 8);
+      alloc((void**)dst, sizeof(int) * ord.size());
+      if (st == DMRG2D_OK &&
+          cudaMemcpy(*dst, ord.data(), sizeof(int) * ord.size(), cudaMemcpyHostToDevice) !=
+              cudaSuccess)
+        st = set_error(DMRG2D_ECUDA, "order upload failed");
+    };
+    upload_order(&T->order, m1 / BM);
+    if (T->pair_ok) upload_order(&T->order2, m1 / 256);
     if (st == DMRG2D_OK) {
       int dev = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&T->sms, cudaDevAttrMultiProcessorCount, dev);
       if (cudaFuncSetAttribute(hv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)SMEM_BYTES) != cudaSuccess)
+                               (int)SMEM_BYTES) != cudaSuccess ||
+          (T->pair_ok &&
+           cudaFuncSetAttribute(hv_tc_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)P_SMEM) != cudaSuccess))
         st = set_error(DMRG2D_ECUDA, "cannot set %zu bytes of shared memory", SMEM_BYTES);
+      if (st == DMRG2D_OK && T->pair_ok) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(T->sms);
+        cfg.blockDim = dim3(TC_THREADS);
+        cfg.dynamicSmemBytes = P_SMEM;
+        int ncl = 0;
+        if (cudaOccupancyMaxActiveClusters(&ncl, hv_tc_pair_kernel, &cfg) != cudaSuccess) {
+          cudaGetLastError();
+          ncl = 0;
+        }
+        T->pairs = std::min(ncl, T->sms / 2);
+        T->pair_ok = T->pairs > 0;
+      }
     }
   }
   if (grouped_ok && st == DMRG2D_OK) {
@@ -477,6 +759,17 @@ int tc_prepare(dmrg2d_ops* ops, cudaStream_t s, const std::vector<double>& HL,
       c.k2e = (int)g->k2.size();
       g->cols.push_back(c);
     }
+    // scalar moves: destination tile (i2, i3) = (row segment i2, column segment i3)
+    for (int i3 = 0; i3 < d; ++i3)
+      for (int i2 = 0; i2 < d; ++i2) {
+        const int tt = i2 + d * i3;
+        if (ops->hCptr[tt] == ops->hCptr[tt + 1]) continue;
+        GMoveDst md{i2, i3, (int)g->moves.size(), 0};
+        for (int e = ops->hCptr[tt]; e < ops->hCptr[tt + 1]; ++e)
+          g->moves.push_back({ops->hCsrc[e] % d, ops->hCsrc[e] / d, (float)ops->hCval[e]});
+        md.me = (int)g->moves.size();
+        g->mdst.push_back(md);
+      }
     st = gp_finalise(ops, g, s);
   }
   if (st == DMRG2D_OK) {
@@ -485,7 +778,10 @@ int tc_prepare(dmrg2d_ops* ops, cudaStream_t s, const std::vector<double>& HL,
   }
   if (st != DMRG2D_OK) return st;
   ops->tc_ok = 1;
-  for (int p = 0; p < 4; ++p) ops->tc_cfg[p] = dense_ok ? -1 : 5;
+  // default before any autotuning: the CTA-pair kernel in blocked order where it applies
+  // (fastest on the shapes measured), else the single-CTA dense kernel, else grouped
+  const int dflt = dense_ok ? (T->pair_ok ? kPairBlockedCfg : -1) : 5;
+  for (int p = 0; p < 4; ++p) ops->tc_cfg[p] = dflt;
   return DMRG2D_OK;
 }
 
@@ -495,6 +791,8 @@ void tc_release(dmrg2d_ops* ops) {
   if (T->HLt) cudaFree(T->HLt);
   if (T->HRt) cudaFree(T->HRt);
   if (T->err) cudaFree(T->err);
+  if (T->order) cudaFree(T->order);
+  if (T->order2) cudaFree(T->order2);
   if (T->plan) {
     gp_release(T->plan);
     delete T->plan;
@@ -503,8 +801,13 @@ void tc_release(dmrg2d_ops* ops) {
   ops->tc = nullptr;
 }
 
+// dense-kernel variants: tc_cfg = -1 - variant, variant bit 0 = operator pool, bit 1 =
+// blocked piece order, bit 2 = CTA-pair kernel; autotuner index 0 / 7 / 8 / 9 / 10 / 11 /
+// 12 / 13 = variant 0 / 1 / 2 / 3 / 4 / 6 / 5 / 7
 static int launch_dense_kernel(const dmrg2d_ops* ops, const TcState* T, const void* v, float* y,
-                               bool bf, bool fuse_moves, bool use_pool, cudaStream_t s) {
+                               bool bf, bool fuse_moves, int variant, cudaStream_t s) {
+  const bool pair = (variant & 4) != 0;
+  const bool use_pool = (variant & 1) != 0;
   const int b = bf ? 1 : 0;
   const int m1 = ops->m1, m4 = ops->m4, d = ops->d;
   const uint32_t BK = bf ? 64 : 32;
@@ -513,9 +816,10 @@ static int launch_dense_kernel(const dmrg2d_ops* ops, const TcState* T, const vo
   p.m4 = m4;
   p.d = d;
   p.BN = T->BN;
-  p.n_mt = m1 / BM;
+  p.n_mt = pair ? m1 / 256 : m1 / BM;  // pieces (pairs of pieces) per block row
   p.n_nt = m4 / T->BN;
   p.tiles = d * p.n_mt * d * p.n_nt;
+  p.order = (variant & 2) ? (pair ? T->order2 : T->order) : nullptr;
   p.BK = (int)BK;
   p.kblk1 = m1 / (int)BK;
   p.kblk2 = m4 / (int)BK;
@@ -527,20 +831,22 @@ static int launch_dense_kernel(const dmrg2d_ops* ops, const TcState* T, const vo
   p.y = y;
   p.err = T->err;
   const int fmt = bf ? 1 : 2;
+  const int M = pair ? 2 * BM : BM;
   for (int n = 0; n < 2; ++n) {
-    p.idesc1[n] = make_idesc(fmt, 0, BM, T->BN, n, 0);
-    p.idesc2[n] = make_idesc(fmt, 1, BM, T->BN, 0, n);
+    p.idesc1[n] = make_idesc(fmt, 0, M, T->BN, n, 0);
+    p.idesc2[n] = make_idesc(fmt, 1, M, T->BN, 0, n);
   }
   const CUtensorMap* mA = &T->mHL[b];
-  const CUtensorMap* mB = &T->mHR[b];
+  const CUtensorMap* mB = pair ? &T->mHR2[b] : &T->mHR[b];
   p.pooled = 0;
   p.k1 = nullptr;
   p.k2 = nullptr;
   p.poolL_rows = p.poolR_rows = 0;
   p.copies = 1;
+  // (the pair kernel reads H_r rows in 128-row boxes: the pool's 128-wide view)
   if (use_pool && T->plan &&
-      gp_pool_views(T->plan, bf ? DMRG2D_BF16 : DMRG2D_TF32, T->BN, &mA, &mB, &p.k1, &p.k2,
-                    &p.poolL_rows, &p.poolR_rows, &p.copies) == DMRG2D_OK)
+      gp_pool_views(T->plan, bf ? DMRG2D_BF16 : DMRG2D_TF32, pair ? P_HALF : T->BN, &mA, &mB,
+                    &p.k1, &p.k2, &p.poolL_rows, &p.poolR_rows, &p.copies) == DMRG2D_OK)
     p.pooled = 1;
   p.a2_box_rows = bf ? 64 : 32;
   p.a2_boxes = BM / p.a2_box_rows;
@@ -550,7 +856,7 @@ static int launch_dense_kernel(const dmrg2d_ops* ops, const TcState* T, const vo
   // k-row groups: 8 rows (1024 B) for the 16-byte-atom swizzle, 4 rows (512 B) for the
   // 32-byte-atom swizzle whose pattern repeats every four 128-byte rows
   p.a2_sbo = bf ? 1024u : 512u;
-  p.tx_bytes = STAGE_A + (uint32_t)T->BN * 128;
+  p.tx_bytes = STAGE_A + (uint32_t)(pair ? P_HALF : T->BN) * 128;  // per CTA and stage
   p.bf16 = bf ? 1 : 0;
   p.fuse = fuse_moves ? 1 : 0;
   p.v = v;
@@ -559,26 +865,30 @@ static int launch_dense_kernel(const dmrg2d_ops* ops, const TcState* T, const vo
   p.Cval = ops->dev.Cval32;
   CUtensorMap mVk, mVm;
   const uint64_t rows = (uint64_t)ops->ld, cols = (uint64_t)d * m4;
-  D2_TRY(make_map(&mVk, v, bf, rows, cols, BK, T->BN));
+  D2_TRY(make_map(&mVk, v, bf, rows, cols, BK, pair ? P_HALF : T->BN));
   D2_TRY(make_map(&mVm, v, bf, rows, cols, (uint32_t)p.a2_box_rows, BK,
                   bf ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B));
-  const int grid = p.tiles < T->sms ? p.tiles : T->sms;
   auto ev = prof_slot(ops);
   if (ev.first) D2_CUDA(cudaEventRecord(ev.first, s));
-  hv_tc_kernel<<<grid, TC_THREADS, SMEM_BYTES, s>>>(*mA, *mB, mVk, mVm, p);
+  if (pair) {
+    const int pairs = std::min(p.tiles, T->pairs);
+    hv_tc_pair_kernel<<<2 * pairs, TC_THREADS, P_SMEM, s>>>(*mA, *mB, mVk, mVm, p);
+  } else {
+    hv_tc_kernel<<<std::min(p.tiles, T->sms), TC_THREADS, SMEM_BYTES, s>>>(*mA, *mB, mVk, mVm, p);
+  }
   D2_CUDA(cudaGetLastError());
   if (ev.second) D2_CUDA(cudaEventRecord(ev.second, s));
   return DMRG2D_OK;
 }
 
-// H_l V + V H_r^T only (no scalar moves), with an explicit kernel choice
+// H·v with an explicit kernel choice (dense kernel: moves only when fuse_moves)
 int tc_gemm(const dmrg2d_ops* ops, const void* v, float* y, int precision, int cfg,
             cudaStream_t s) {
   const TcState* T = (const TcState*)ops->tc;
   if (!T) return set_error(DMRG2D_EUNSUPPORTED, "tensor-core path not prepared");
   if (cfg < 0) {
     if (!T->dense_ok) return set_error(DMRG2D_EUNSUPPORTED, "dense kernel unsupported here");
-    return launch_dense_kernel(ops, T, v, y, precision == DMRG2D_BF16, false, cfg == -2, s);
+    return launch_dense_kernel(ops, T, v, y, precision == DMRG2D_BF16, false, -1 - cfg, s);
   }
   if (!T->plan) return set_error(DMRG2D_EUNSUPPORTED, "grouped kernel unsupported here");
   return gp_launch(ops, T->plan, v, y, precision, cfg, s);
@@ -589,22 +899,12 @@ int launch_hv_tc(const dmrg2d_ops* ops, const void* v, float* y, int precision, 
   if (!ops->tc || !ops->tc_ok)
     return set_error(DMRG2D_EUNSUPPORTED, "tensor-core path not prepared");
   const bool bf = precision == DMRG2D_BF16;
-  const int m1 = ops->m1, m4 = ops->m4, d = ops->d;
   if (ops->tc_cfg[precision] < 0) {  // dense kernel: the moves run in its epilogue
     return launch_dense_kernel(ops, (const TcState*)ops->tc, v, y, bf, true,
-                               ops->tc_cfg[precision] == -2, s);
+                               -1 - ops->tc_cfg[precision], s);
   }
-  D2_TRY(tc_gemm(ops, v, y, precision, ops->tc_cfg[precision], s));
-  dim3 g2(d * d, (m4 + 7) / 8);
-  if (bf)
-    k_scalar_moves<__nv_bfloat16><<<g2, 256, 0, s>>>((const __nv_bfloat16*)v, y, ops->dev.Cptr,
-                                                    ops->dev.Csrc, ops->dev.Cval32, m1, m4, d,
-                                                    ops->ld);
-  else
-    k_scalar_moves<float><<<g2, 256, 0, s>>>((const float*)v, y, ops->dev.Cptr, ops->dev.Csrc,
-                                            ops->dev.Cval32, m1, m4, d, ops->ld);
-  D2_CUDA(cudaGetLastError());
-  return DMRG2D_OK;
+  // grouped kernel: its epilogue adds the scalar moves of the plan
+  return tc_gemm(ops, v, y, precision, ops->tc_cfg[precision], s);
 }
 
 int tc_read_error(const dmrg2d_ops* ops, int* code) {
@@ -629,13 +929,28 @@ int tc_read_error(const dmrg2d_ops* ops, int* code) {
 namespace dmrg2d {
 
 // candidate index: 0 = dense kernel, 1 + c = grouped kernel configuration c, 7 = dense
-// kernel reading the deduplicated (replicated) operator pool
+// kernel reading the deduplicated (replicated) operator pool, 8 / 9 = dense kernel in the
+// blocked piece order (per-position blocks / pool)
+// 14 + c = grouped configuration c with the scalar moves in a separate kernel (sectors)
+constexpr int N_CANDIDATES = 20;
+static int idx_to_cfg(int idx) {
+  static const int dense_variant[14] = {0, -1, -1, -1, -1, -1, -1, 1, 2, 3, 4, 6, 5, 7};
+  if (idx >= 1 && idx <= 6) return idx - 1;
+  if (idx >= 14) return gp_num_configs() + idx - 14;
+  return -1 - dense_variant[idx];
+}
+
 static bool tc_candidate_ok(const dmrg2d_ops* ops, int idx) {
-  if (idx == 0 || idx == 7) {
+  if (idx < 0 || idx >= N_CANDIDATES) return false;
+  if (idx >= 14) return ops->sec && ops->tc_ok;  // grouped, separate moves: sectors only
+  if (idx == 0 || idx >= 7) {                    // dense-kernel variants
     const TcState* T = (const TcState*)ops->tc;
-    return !ops->sec && T && T->dense_ok && (idx == 0 || T->plan);
+    if (ops->sec || !T || !T->dense_ok) return false;
+    const int variant = -1 - idx_to_cfg(idx);
+    if ((variant & 4) && !T->pair_ok) return false;
+    return (variant & 1) == 0 || T->plan != nullptr;  // the pool lives in the grouped plan
   }
-  if (idx < 1 || idx > gp_num_configs()) return false;
+  if (idx > gp_num_configs()) return false;
   if (ops->sec) return ops->tc_ok != 0;
   const TcState* T = (const TcState*)ops->tc;
   return T && T->plan;
@@ -645,7 +960,7 @@ static bool tc_candidate_ok(const dmrg2d_ops* ops, int idx) {
 static int tc_run_candidate(dmrg2d_ops* ops, const void* v, float* y, int prec, int idx,
                             cudaStream_t s) {
   const int saved = ops->tc_cfg[prec];
-  ops->tc_cfg[prec] = idx == 0 ? -1 : (idx == 7 ? -2 : idx - 1);
+  ops->tc_cfg[prec] = idx_to_cfg(idx);
   const int st = launch_hv_tc(ops, v, y, prec, s);
   ops->tc_cfg[prec] = saved;
   return st;
@@ -658,6 +973,20 @@ using namespace dmrg2d;
 extern "C" const char* dmrg2d_tile_config_name(int index) {
   if (index == 0) return "dense kernel 128x256 (column-slab raster)";
   if (index == 7) return "dense kernel 128x256, deduplicated operator pool";
+  if (index == 8) return "dense kernel 128x256 (8x8-tile blocked raster)";
+  if (index == 9) return "dense kernel 128x256 (8x8-tile blocked raster), operator pool";
+  if (index == 10) return "CTA-pair kernel 256x256 (column-slab raster)";
+  if (index == 11) return "CTA-pair kernel 256x256 (8x8-tile blocked raster)";
+  if (index == 12) return "CTA-pair kernel 256x256 (column-slab raster), operator pool";
+  if (index == 13) return "CTA-pair kernel 256x256 (8x8-tile blocked raster), operator pool";
+  static const char* sep[6] = {
+      "grouped 128x128 column-slab, separate moves kernel",
+      "grouped 128x128 row-slab, separate moves kernel",
+      "grouped 128x128 longest-first, separate moves kernel",
+      "grouped 128x256 column-slab, separate moves kernel",
+      "grouped 128x256 row-slab, separate moves kernel",
+      "grouped 128x256 longest-first, separate moves kernel"};
+  if (index >= 14 && index < N_CANDIDATES) return sep[index - 14];
   return gp_config_name(index - 1);
 }
 
@@ -666,7 +995,7 @@ extern "C" int dmrg2d_set_tile_config(dmrg2d_ops* ops, int precision, int index)
     return set_error(DMRG2D_EINVAL, "set_tile_config: bad argument");
   if (!tc_candidate_ok(ops, index))
     return set_error(DMRG2D_EUNSUPPORTED, "tile configuration %d not available here", index);
-  ops->tc_cfg[precision] = index == 0 ? -1 : (index == 7 ? -2 : index - 1);
+  ops->tc_cfg[precision] = idx_to_cfg(index);
   return DMRG2D_OK;
 }
 
@@ -700,7 +1029,7 @@ extern "C" int dmrg2d_autotune(dmrg2d_ops* ops, int precision, int* best, double
   D2_CUDA(cudaEventCreate(&e1));
   int chosen = -1;
   double tbest = 1e300;
-  const int ncand = 2 + gp_num_configs();
+  const int ncand = N_CANDIDATES;
   int st = DMRG2D_OK;
   for (int c = 0; c < ncand && st == DMRG2D_OK; ++c) {
     double t = -1.0;
@@ -734,7 +1063,28 @@ extern "C" int dmrg2d_autotune(dmrg2d_ops* ops, int precision, int* best, double
   D2_TRY(tc_read_error(ops, &derr));
   if (derr) return set_error(DMRG2D_ETIMEOUT, "tensor-core kernel gave up waiting (site %d)", derr);
   if (chosen < 0) return set_error(DMRG2D_EUNSUPPORTED, "no tile configuration applies");
-  ops->tc_cfg[precision] = chosen == 0 ? -1 : (chosen == 7 ? -2 : chosen - 1);
+  ops->tc_cfg[precision] = idx_to_cfg(chosen);
   if (best) *best = chosen;
   return DMRG2D_OK;
+}
+
+extern "C" int dmrg2d_wait_selftest(double seconds, void* stream) {
+  if (!(seconds > 0.0) || seconds > 2.0)
+    return set_error(DMRG2D_EINVAL, "wait_selftest: seconds must be in (0, 2]");
+  cudaStream_t s = (cudaStream_t)stream;
+  int* err = nullptr;
+  D2_CUDA(cudaMalloc((void**)&err, sizeof(int)));
+  struct Free {
+    int* p;
+    ~Free() { cudaFree(p); }
+  } fr{err};
+  D2_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+  k_wait_selftest<<<1, 32, 0, s>>>(err, (uint64_t)(seconds * 1e9));
+  D2_CUDA(cudaGetLastError());
+  int code = 0;
+  D2_CUDA(cudaMemcpyAsync(&code, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  D2_CUDA(cudaStreamSynchronize(s));
+  if (code == 99)
+    return set_error(DMRG2D_ETIMEOUT, "wait_selftest: the bounded wait gave up as designed");
+  return set_error(DMRG2D_ECUDA, "wait_selftest: the wait did not report its timeout (%d)", code);
 }

@@ -517,6 +517,12 @@ int sec_build(dmrg2d_ops* ops, const dmrg2d_block* L, const dmrg2d_block* R, con
     g.qcols = S->qcols;
     for (const RowSegD& r : S->rseg) g.rows.push_back({r.q, r.off, r.dim, r.dim_pad, r.k1b, r.k1e});
     for (const ColSegD& c : S->cseg) g.cols.push_back({c.q, c.off, c.dim, c.k2b, c.k2e});
+    for (const MoveDst& md : S->mdst) {  // the scalar moves run in the grouped epilogue
+      g.mdst.push_back({md.rs, md.cs, (int)g.moves.size(), 0});
+      for (int e = md.mb; e < md.me; ++e)
+        g.moves.push_back({S->msrc[e].rs, S->msrc[e].cs, S->msrc[e].c32});
+      g.mdst.back().me = (int)g.moves.size();
+    }
     const int gs = gp_finalise(ops, &g, s);
     if (gs == DMRG2D_OK) {
       S->gp_ok = true;
@@ -545,7 +551,9 @@ int sec_apply(const dmrg2d_ops* ops, const void* v, void* y, int precision, cuda
   if (!S) return set_error(DMRG2D_EINVAL, "not a sector-restricted ops object");
   const SecParams p = S->params();
   const int nt = (int)S->tiles.size(), nm = (int)S->mitems.size();
-  auto ev = prof_slot(ops);
+  // timed kernel: the CUDA-core kernel here; the grouped tensor-core launch times itself
+  const bool simt = precision == DMRG2D_FP64 || precision == DMRG2D_FP32;
+  auto ev = simt ? prof_slot(ops) : std::pair<cudaEvent_t, cudaEvent_t>(nullptr, nullptr);
   if (ev.first) D2_CUDA(cudaEventRecord(ev.first, s));
   if (precision == DMRG2D_FP64) {
     if (nt) hv_simt_sec_kernel<double><<<nt, 256, 0, s>>>((const double*)v, (double*)y, S->d_L64,
@@ -558,8 +566,12 @@ int sec_apply(const dmrg2d_ops* ops, const void* v, void* y, int precision, cuda
     if (ev.second) D2_CUDA(cudaEventRecord(ev.second, s));
     if (nm) k_sec_moves<float, float><<<nm, 256, 0, s>>>((const float*)v, (float*)y, p, 0);
   } else if ((precision == DMRG2D_TF32 || precision == DMRG2D_BF16) && S->gp_ok) {
-    D2_TRY(gp_launch(ops, &S->plan, v, (float*)y, precision, ops->tc_cfg[precision], s));
-    if (nm) {
+    // tc_cfg < G: one launch, the grouped kernel's epilogue adds the scalar moves;
+    // G <= tc_cfg < 2G: the moves run in their own kernel after it (G tile layouts)
+    const int G = gp_num_configs(), cfg = ops->tc_cfg[precision];
+    const bool fused = cfg < G;
+    D2_TRY(gp_launch(ops, &S->plan, v, (float*)y, precision, cfg % G, s, fused));
+    if (!fused && nm) {
       if (precision == DMRG2D_BF16)
         k_sec_moves<__nv_bfloat16, float><<<nm, 256, 0, s>>>((const __nv_bfloat16*)v, (float*)y,
                                                             p, 0);
@@ -639,13 +651,6 @@ int sec_read_error(const dmrg2d_ops* ops, int* code) {
   const SecState* S = (const SecState*)ops->sec;
   if (!S || !S->gp_ok) return DMRG2D_OK;
   return gp_read_error(&S->plan, code);
-}
-
-int sec_tc_gemm(const dmrg2d_ops* ops, const void* v, float* y, int precision, int cfg,
-                cudaStream_t s) {
-  const SecState* S = (const SecState*)ops->sec;
-  if (!S || !S->gp_ok) return set_error(DMRG2D_EUNSUPPORTED, "no grouped plan");
-  return gp_launch(ops, &S->plan, v, y, precision, cfg, s);
 }
 
 int sec_count(const dmrg2d_ops* ops) {

@@ -157,6 +157,111 @@ __global__ void k_f32_to_f64(const float* __restrict__ x, double* __restrict__ o
     o[e] = (double)x[e];
 }
 
+// ---- fused conjugate-gradient steps of the mixed solver's inner loop ----------------
+// The CG runs on (I - x x^T)(H~ - theta)(I - x x^T) t = -r.  With y = H~ p (FP32, straight
+// from the low-precision H·v) the projected operator applied to p is
+//   q = y - theta p - (x.q') x,   q' = y - theta p,
+// and one step needs x.q', p.q (= p.q' since p is orthogonal to x), then
+//   t += a p,  r -= a q,  rr' = r.r,  p = r + (rr'/rr) p.
+// Three passes over the vectors instead of eight; scalars stay on the device.
+enum { CG_XQ = 40, CG_PQ, CG_A, CG_RR, CG_RR1, CG_BETA, CG_THETA };
+
+__device__ __forceinline__ float to_tf32(float f) {
+  uint32_t u;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(f));
+  return __uint_as_float(u);
+}
+
+// part[b] = partial x.q', part[g + b] = partial p.q'
+__global__ void k_cg_dots(const float* __restrict__ y, const double* __restrict__ p,
+                          const double* __restrict__ x, const double* __restrict__ scal,
+                          int64_t n, double* __restrict__ part) {
+  const double theta = scal[CG_THETA];
+  double sx = 0.0, sp = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * VT + threadIdx.x; e < n; e += (int64_t)gridDim.x * VT) {
+    const double pe = p[e];
+    const double q = (double)y[e] - theta * pe;
+    sx += x[e] * q;
+    sp += pe * q;
+  }
+  sx = block_sum(sx);
+  sp = block_sum(sp);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = sx;
+    part[gridDim.x + blockIdx.x] = sp;
+  }
+}
+
+// scal[CG_XQ], scal[CG_PQ] from the partials; a = rr / pq (0 when pq <= 0: no update)
+__global__ void k_cg_alpha(const double* __restrict__ part, int np, double* __restrict__ scal) {
+  double sx = 0.0, sp = 0.0;
+  for (int b = threadIdx.x; b < np; b += VT) {
+    sx += part[b];
+    sp += part[np + b];
+  }
+  sx = block_sum(sx);
+  sp = block_sum(sp);
+  if (threadIdx.x == 0) {
+    scal[CG_XQ] = sx;
+    scal[CG_PQ] = sp;
+    scal[CG_A] = sp > 0.0 ? scal[CG_RR] / sp : 0.0;
+  }
+}
+
+// t += a p, r -= a (y - theta p - xq x); part[b] = partial r.r (of the updated r)
+__global__ void k_cg_update(const float* __restrict__ y, const double* __restrict__ p,
+                            const double* __restrict__ x, double* __restrict__ t,
+                            double* __restrict__ r, const double* __restrict__ scal, int64_t n,
+                            double* __restrict__ part) {
+  const double a = scal[CG_A], xq = scal[CG_XQ], theta = scal[CG_THETA];
+  double s = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * VT + threadIdx.x; e < n; e += (int64_t)gridDim.x * VT) {
+    double re = r[e];
+    if (a != 0.0) {
+      const double pe = p[e];
+      const double q = ((double)y[e] - theta * pe) - xq * x[e];
+      t[e] += a * pe;
+      re -= a * q;
+      r[e] = re;
+    }
+    s += re * re;
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// scal[CG_RR1] = sum of partials; beta = rr1 / rr; rr <- rr1
+__global__ void k_cg_beta(const double* __restrict__ part, int np, double* __restrict__ scal) {
+  double s = 0.0;
+  for (int b = threadIdx.x; b < np; b += VT) s += part[b];
+  s = block_sum(s);
+  if (threadIdx.x == 0) {
+    const double rr = scal[CG_RR];
+    scal[CG_RR1] = s;
+    scal[CG_BETA] = rr > 0.0 ? s / rr : 0.0;
+    scal[CG_RR] = s;
+  }
+}
+
+// p = r + beta p (beta from scal, or 0 for the first direction: p = r), and the
+// low-precision copy of p that the next H~ p reads
+__global__ void k_cg_direction(double* __restrict__ p, const double* __restrict__ r,
+                               const double* __restrict__ scal, int first, void* __restrict__ lo,
+                               int precision, int64_t n) {
+  const double beta = first ? 0.0 : scal[CG_BETA];
+  for (int64_t e = (int64_t)blockIdx.x * VT + threadIdx.x; e < n; e += (int64_t)gridDim.x * VT) {
+    const double pe = first ? r[e] : r[e] + beta * p[e];
+    p[e] = pe;
+    const float f = (float)pe;
+    if (precision == DMRG2D_BF16)
+      ((__nv_bfloat16*)lo)[e] = __float2bfloat16_rn(f);
+    else if (precision == DMRG2D_TF32)
+      ((float*)lo)[e] = to_tf32(f);
+    else
+      ((float*)lo)[e] = f;
+  }
+}
+
 // ---- lowest eigenpair of the Lanczos tridiagonal T_k (diag alpha, off-diag beta) ----
 // Sturm-sequence bisection for the eigenvalue, inverse iteration (tridiagonal LU with
 // partial pivoting) for the eigenvector.  out[0] = theta, out[1] = |beta_{k-1} s_{k-1}|,
@@ -335,17 +440,7 @@ struct Ctx {
 
   int hv(int prec, const double* x, double* y) {
     cudaEvent_t a = nullptr, b = nullptr;
-    if (timing) {
-      if (ev_used == ev.size()) {
-        cudaEvent_t e0, e1;
-        D2_CUDA(cudaEventCreate(&e0));
-        D2_CUDA(cudaEventCreate(&e1));
-        ev.push_back({e0, e1});
-      }
-      a = ev[ev_used].first;
-      b = ev[ev_used].second;
-      ++ev_used;
-    }
+    D2_TRY(next_events(&a, &b));
     if (prec == DMRG2D_FP64) {
       if (a) D2_CUDA(cudaEventRecord(a, s));
       D2_TRY(launch_hv_simt_f64(ops, x, y, s));
@@ -354,6 +449,14 @@ struct Ctx {
       return DMRG2D_OK;
     }
     D2_TRY(convert_f64_to(x, lo, prec, n, s));
+    D2_TRY(hv_lo(prec, a, b));
+    k_f32_to_f64<<<vgrid(n), VT, 0, s>>>(y32, y, n);
+    D2_CUDA(cudaGetLastError());
+    return DMRG2D_OK;
+  }
+
+  // y32 = H~ lo: the low-precision H·v on the already converted input
+  int hv_lo(int prec, cudaEvent_t a, cudaEvent_t b, bool count = true) {
     if (a) D2_CUDA(cudaEventRecord(a, s));
     if (prec == DMRG2D_FP32) {
       D2_TRY(launch_hv_simt_f32(ops, (const float*)lo, y32, s));
@@ -361,9 +464,25 @@ struct Ctx {
       D2_TRY(launch_hv_tc(ops, lo, y32, prec, s));
     }
     if (b) D2_CUDA(cudaEventRecord(b, s));
-    k_f32_to_f64<<<vgrid(n), VT, 0, s>>>(y32, y, n);
-    D2_CUDA(cudaGetLastError());
-    if (st) st->n_hv_low++;
+    if (st && count) st->n_hv_low++;
+    return DMRG2D_OK;
+  }
+  int hv_lo(int prec) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    D2_TRY(next_events(&a, &b));
+    return hv_lo(prec, a, b);
+  }
+  int next_events(cudaEvent_t* a, cudaEvent_t* b) {
+    if (!timing) return DMRG2D_OK;
+    if (ev_used == ev.size()) {
+      cudaEvent_t e0, e1;
+      D2_CUDA(cudaEventCreate(&e0));
+      D2_CUDA(cudaEventCreate(&e1));
+      ev.push_back({e0, e1});
+    }
+    *a = ev[ev_used].first;
+    *b = ev[ev_used].second;
+    ++ev_used;
     return DMRG2D_OK;
   }
 
@@ -442,7 +561,8 @@ int dmalloc(DevBuf& b, size_t bytes) {
 // Lanczos from x (FP64, any norm); on return x holds the normalised Ritz vector.
 // scal layout: [0] theta, [1] resid, [2] status, [3..] scratch scalars
 int lanczos(Ctx& C, int prec, double* x, int max_iter, int kdim, double tol, int fixed,
-            int check_every, double* theta_out, double* resid_out, int* iters_out) {
+            int check_every, double* theta_out, double* resid_out, int* iters_out,
+            int gs_passes = 2) {
   const int64_t n = C.n;
   if (kdim < 2) kdim = 2;
   if (kdim > max_iter + 1) kdim = max_iter + 1;
@@ -476,7 +596,7 @@ int lanczos(Ctx& C, int prec, double* x, int max_iter, int kdim, double tol, int
     k_lz_axpy2<<<vgrid(n), VT, 0, C.s>>>(w, qj, j > 0 ? qj - n : nullptr, alpha + j,
                                         j > 0 ? beta + j - 1 : nullptr, n);
     D2_CUDA(cudaGetLastError());
-    for (int pass = 0; pass < 2; ++pass) {  // CGS2 against q_0..q_j
+    for (int pass = 0; pass < gs_passes; ++pass) {  // CGS2 (or fewer) against q_0..q_j
       D2_TRY(C.multidot(Q, n, j + 1, w, h));
       D2_TRY(C.combo(w, Q, n, j + 1, h, -1));
     }
@@ -537,6 +657,38 @@ int convert_f64_to(const double* x, void* out, int precision, int64_t n, cudaStr
   return DMRG2D_OK;
 }
 
+// A fixed sequence of launches (one inner CG step) captured into a CUDA graph on a
+// private stream and replayed on the solver's stream: one graph launch per step instead of
+// seven kernel launches and a copy.  The captured work reads its scalars (theta, a, beta)
+// from device memory, so the same graph serves every outer iteration.
+constexpr int HS_THETA = 60;  // pinned-mirror slot holding theta for its upload
+
+struct StepGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cs = nullptr;
+
+  template <typename F>
+  int capture(Ctx& C, F&& body) {
+    if (!cs) D2_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    const cudaStream_t saved = C.s;  // captured work is recorded, not run: no ordering needed
+    C.s = cs;
+    D2_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    const int st = body();
+    const cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    C.s = saved;
+    if (st != DMRG2D_OK) return st;
+    if (e != cudaSuccess) return set_error(DMRG2D_ECUDA, "CG step capture: %s", cudaGetErrorString(e));
+    D2_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    return DMRG2D_OK;
+  }
+  ~StepGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cs) cudaStreamDestroy(cs);
+  }
+};
+
 // Mixed precision: low-precision Lanczos start, FP64 outer Rayleigh-Ritz + CG corrections.
 static int mixed_outer(Ctx& C, const dmrg2d_solver_opts* o, double* x, double* energy);
 
@@ -547,7 +699,8 @@ static int mixed_solve(Ctx& C, const dmrg2d_solver_opts* o, double* x, double* e
   // basis capped at krylov_dim vectors (explicit restarts), so memory does not grow with
   // inner_iter
   const int kdim1 = std::max(2, std::min(o->inner_iter, o->krylov_dim) + 1);
-  int st = lanczos(C, o->precision, x, o->inner_iter, kdim1, 1e-6, 0, 5, &th0, &r0, &it0);
+  const int passes = std::min(2, std::max(0, o->start_reorth));
+  int st = lanczos(C, o->precision, x, o->inner_iter, kdim1, 1e-6, 0, 5, &th0, &r0, &it0, passes);
   if (st != DMRG2D_OK && st != DMRG2D_ENOCONV) return st;
   C.st->iters += it0;
   // 2. FP64 outer loop
@@ -573,7 +726,9 @@ static int mixed_outer(Ctx& C, const dmrg2d_solver_opts* o, double* x, double* e
   double *U = (double*)Ub.p, *W = (double*)Wb.p, *hx = (double*)hxb.p, *r = (double*)rb.p;
   double *t = (double*)tb.p, *p = (double*)pb.p, *q = (double*)qb.p, *G = (double*)Gb.p;
   double *cc = (double*)cb.p, *scr = (double*)scb.p;
-  double* sc = C.scal;  // scalars: [4] tmp dot, [5..] host-fetched
+  double* sc = C.scal;  // scalars: [4] tmp dot, [5..] host-fetched, [CG_XQ..] CG state
+  const int g = vgrid(n);
+  StepGraph step;  // the inner CG step, captured once and replayed
   D2_CUDA(cudaMemsetAsync(G, 0, sizeof(double) * smax * smax, C.s));
 
   D2_TRY(C.nrm(x, sc + 3));
@@ -624,30 +779,35 @@ static int mixed_outer(Ctx& C, const dmrg2d_solver_opts* o, double* x, double* e
     D2_TRY(C.dot(x, r, sc + 4));
     D2_TRY(C.fetch(sc + 4, 1));
     D2_TRY(C.axpby(r, x, -C.hscal[0], 1.0));
-    D2_CUDA(cudaMemcpyAsync(p, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, C.s));
-    D2_TRY(C.dot(r, r, sc + 4));
-    D2_TRY(C.fetch(sc + 4, 1));
-    double rr = C.hscal[0];
-    const double rr0 = rr;
+    D2_TRY(C.dot(r, r, sc + CG_RR));
+    C.hscal[HS_THETA] = theta;
+    D2_CUDA(cudaMemcpyAsync(sc + CG_THETA, C.hscal + HS_THETA, sizeof(double),
+                            cudaMemcpyHostToDevice, C.s));
+    k_cg_direction<<<g, VT, 0, C.s>>>(p, r, sc, 1, C.lo, prec, n);
+    D2_CUDA(cudaGetLastError());
+    D2_TRY(C.fetch(sc + CG_RR, 1));
+    const double rr0 = C.hscal[0];
+    if (!step.exec) D2_TRY(step.capture(C, [&]() -> int {
+      // one CG step: y32 = H~ p, the fused vector passes, scalars to the pinned mirror
+      D2_TRY(C.hv_lo(prec, nullptr, nullptr, false));  // counted per replay
+      k_cg_dots<<<g, VT, 0, C.s>>>(C.y32, p, x, sc, n, C.part);
+      k_cg_alpha<<<1, VT, 0, C.s>>>(C.part, g, sc);
+      k_cg_update<<<g, VT, 0, C.s>>>(C.y32, p, x, t, r, sc, n, C.part);
+      k_cg_beta<<<1, VT, 0, C.s>>>(C.part, g, sc);
+      k_cg_direction<<<g, VT, 0, C.s>>>(p, r, sc, 0, C.lo, prec, n);
+      D2_CUDA(cudaGetLastError());
+      D2_CUDA(cudaMemcpyAsync(C.hscal, sc + CG_PQ, sizeof(double) * (CG_RR1 - CG_PQ + 1),
+                              cudaMemcpyDeviceToHost, C.s));
+      return DMRG2D_OK;
+    }));
     for (int it = 0; it < o->inner_iter; ++it) {
-      D2_TRY(C.hv(prec, p, q));
-      D2_TRY(C.axpby(q, p, -theta, 1.0));  // q = H~p - theta p
-      D2_TRY(C.dot(x, q, sc + 4));
-      D2_TRY(C.dot(p, q, sc + 5));
-      D2_TRY(C.fetch(sc + 4, 2));
-      const double xq = C.hscal[0], pq = C.hscal[1];
+      D2_CUDA(cudaGraphLaunch(step.exec, C.s));
+      D2_CUDA(cudaStreamSynchronize(C.s));  // one wait per step
+      const double pq = C.hscal[0], rr1 = C.hscal[CG_RR1 - CG_PQ];
+      C.st->n_hv_low++;
       C.st->iters++;
-      if (!(pq > 0.0)) break;
-      D2_TRY(C.axpby(q, x, -xq, 1.0));     // project
-      const double a = rr / pq;
-      D2_TRY(C.axpby(t, p, a, 1.0));
-      D2_TRY(C.axpby(r, q, -a, 1.0));
-      D2_TRY(C.dot(r, r, sc + 4));
-      D2_TRY(C.fetch(sc + 4, 1));
-      const double rr1 = C.hscal[0];
+      if (!(pq > 0.0)) break;  // (no update was made)
       if (rr1 <= 1e-8 * rr0) break;
-      D2_TRY(C.axpby(p, r, 1.0, rr1 / rr));  // p = r + (rr1/rr) p
-      rr = rr1;
     }
     // ---- orthonormalise t against U and extend the subspace ----
     if (s == smax) {  // restart with the current Ritz pair

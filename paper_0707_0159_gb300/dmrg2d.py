@@ -49,7 +49,8 @@ class OpsInfo(C.Structure):
 class SolverOpts(C.Structure):
     _fields_ = [("max_iter", C.c_int), ("krylov_dim", C.c_int), ("tol", C.c_double),
                 ("fixed_steps", C.c_int), ("precision", C.c_int), ("refine", C.c_int),
-                ("inner_iter", C.c_int), ("outer_max", C.c_int), ("check_every", C.c_int)]
+                ("inner_iter", C.c_int), ("outer_max", C.c_int), ("check_every", C.c_int),
+                ("start_reorth", C.c_int)]
 
 
 class DavidsonOpts(C.Structure):
@@ -79,6 +80,7 @@ SIGNATURES = {
                                                 C.POINTER(C.c_double), C.POINTER(SolverStats),
                                                 C.c_void_p]),
     "dmrg2d_default_solver_opts": (None, [C.POINTER(SolverOpts)]),
+    "dmrg2d_wait_selftest": (C.c_int, [C.c_double, C.c_void_p]),
     "dmrg2d_diagonal": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "dmrg2d_default_davidson_opts": (None, [C.POINTER(DavidsonOpts)]),
     "dmrg2d_davidson_ground": (C.c_int, [C.c_void_p, C.POINTER(DavidsonOpts), C.c_void_p,
@@ -235,6 +237,11 @@ def apply_H(ops: Ops, v, y, precision=FP64, stream=None):
                                 int(precision), _stream(stream)))
 
 
+def wait_selftest(seconds: float = 0.05, stream=None) -> int:
+    """Run the bounded-wait self-test; returns its status code (ETIMEOUT = -6 expected)."""
+    return lib().dmrg2d_wait_selftest(float(seconds), _stream(stream))
+
+
 def check_device(ops: Ops):
     """Raise if a device-side bounded wait gave up since the last check."""
     _check(lib().dmrg2d_check_device(ops.ptr))
@@ -251,7 +258,7 @@ def profile_stop(ops: Ops):
     return ms.value, n.value
 
 
-N_TILE_CONFIGS = 8
+N_TILE_CONFIGS = 20
 
 
 def autotune(ops: Ops, precision, stream=None):

@@ -68,3 +68,9 @@ def test_default_solver_opts(lib):
     from paper_0707_0159_gb300 import dmrg2d
     o = dmrg2d.default_solver_opts()
     assert o["precision"] == dmrg2d.FP64 and o["max_iter"] > 0 and o["tol"] > 0
+
+
+def test_wait_selftest_rejects_bad_limits(lib):
+    from paper_0707_0159_gb300 import dmrg2d
+    assert dmrg2d.wait_selftest(0.0) == -1      # EINVAL before any device work
+    assert dmrg2d.wait_selftest(5.0) == -1

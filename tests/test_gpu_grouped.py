@@ -65,13 +65,33 @@ def test_dense_and_grouped_kernels_agree(prec):
     v = synth.start_vector(sb.n_vec, 4)
     ref = sb.apply(v)
     out = {}
-    for cfg in (0, 1, 4, 7):
+    for cfg in (0, 1, 4, 7, 8, 9):
         dmrg2d.set_tile_config(ops, prec, cfg)
         out[cfg] = run(ops, v, prec)
         assert rel(out[cfg], ref) <= TOL[prec]
     # same operands, same K order within a piece: the kernels agree far below the tolerance
-    for cfg in (1, 4, 7):
+    for cfg in (1, 4, 7, 8, 9):
         assert rel(out[cfg], out[0]) <= 1e-6, cfg
+
+
+@pytest.mark.parametrize("case", [("heisenberg", 3, 256, 256), ("hubbard", 1, 512, 512),
+                                  ("heisenberg", 2, 256, 512)])
+@pytest.mark.parametrize("prec", [dmrg2d.TF32, dmrg2d.BF16])
+def test_cta_pair_kernel_matches_oracle_and_dense(case, prec):
+    """The CTA-pair kernel (configs 10 to 13) on shapes with one and two 256-row piece
+    pairs per block row and one and two 256-column pieces per block column."""
+    mdl, left, right = make(*case)
+    ops = dmrg2d.build_ops(mdl, left, right)
+    sb = Superblock(mdl, left, right)
+    v = synth.start_vector(sb.n_vec, 6)
+    ref = sb.apply(v)
+    dmrg2d.set_tile_config(ops, prec, 0)
+    y0 = run(ops, v, prec)
+    for cfg in (10, 11, 12, 13):  # per-position operator blocks / deduplicated pool
+        dmrg2d.set_tile_config(ops, prec, cfg)
+        y = run(ops, v, prec)
+        assert rel(y, ref) <= TOL[prec], (cfg, rel(y, ref))
+        assert rel(y, y0) <= 1e-6, cfg
 
 
 CASES = {
@@ -96,7 +116,7 @@ def test_sector_tensor_core_matches_oracle(name, prec):
     yd = sb.apply(vd)
     ref = np.zeros(len(pmap))
     ref[valid] = yd[pmap[valid]]
-    for cfg in range(1, 7):
+    for cfg in list(range(1, 7)) + list(range(14, 20)):  # moves fused / in their own kernel
         dmrg2d.set_tile_config(ops, prec, cfg)
         got = run(ops, vp, prec)
         assert np.all(got[~valid] == 0.0)
@@ -108,8 +128,9 @@ def test_autotune_picks_a_working_config(prec):
     mdl, left, right, target = CASES["heisenberg_4leg"]()
     ops = dmrg2d.build_ops(mdl, left, right, target=target)
     best, ms = dmrg2d.autotune(ops, prec)
-    assert 1 <= best < 7
-    assert ms[0] == -1.0 and ms[7] == -1.0 and all(t > 0 for t in ms[1:7])
+    assert 1 <= best < 7 or 14 <= best < 20
+    assert all(ms[i] == -1.0 for i in (0, 7, 8, 9, 10, 11, 12, 13))
+    assert all(t > 0 for t in ms[1:7] + ms[14:20])
     assert ms[best] == min(t for t in ms if t > 0)
     sb = Superblock(mdl, left, right)
     pmap = packed_map(sb, target)
@@ -120,3 +141,40 @@ def test_autotune_picks_a_working_config(prec):
     ref = np.zeros(len(pmap))
     ref[valid] = sb.apply(vd)[pmap[valid]]
     assert rel(run(ops, vp, prec), ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [dmrg2d.TF32, dmrg2d.BF16])
+def test_sector_apply_captured_in_cuda_graph(prec):
+    """apply_H on a sector-restricted superblock (grouped persistent launch + scalar
+    moves) recorded once in a CUDA graph and replayed: the replays equal the direct call,
+    and a replay after the input changed sees the new input."""
+    mdl, left, right, target = CASES["hubbard_3leg"]()
+    sb = Superblock(mdl, left, right)
+    ops = dmrg2d.build_ops(mdl, left, right, target=target)
+    pmap = packed_map(sb, target)
+    valid = pmap >= 0
+    dt = torch.float32 if prec == dmrg2d.TF32 else torch.bfloat16
+    vs = [torch.from_numpy(np.where(valid, synth.start_vector(len(pmap), s), 0.0)).cuda().to(dt)
+          for s in (41, 42)]
+    direct = []
+    for v in vs:
+        y = torch.empty(len(pmap), dtype=torch.float32, device="cuda")
+        dmrg2d.apply_H(ops, v, y, prec)
+        direct.append(y.clone())
+    x = vs[0].clone()
+    y = torch.zeros(len(pmap), dtype=torch.float32, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):                 # warm-up on the capture stream
+        dmrg2d.apply_H(ops, x, y, prec)
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        dmrg2d.apply_H(ops, x, y, prec)
+    for k in (0, 1, 0):
+        x.copy_(vs[k])
+        y.fill_(-7.0)
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(y, direct[k]), k
+    dmrg2d.check_device(ops)

@@ -205,9 +205,24 @@ def test_ladder3_full_fp64_sampled(ladder3_full):
 
 @pytest.mark.parametrize("prec,tol", [(dmrg2d.TF32, 1e-3), (dmrg2d.BF16, 6e-3)])
 def test_ladder3_full_tensor_core_sampled(ladder3_full, prec, tol):
+    """Every dense-kernel variant (column-slab / blocked piece order, per-position blocks /
+    operator pool) and the autotuner's choice, which is what the benchmark times."""
     ops, sb, v, idx = ladder3_full
     if not ops.info["tc_ok"]:
         pytest.skip("tensor-core path not available for these shapes")
-    y, vq = run(ops, v, prec)
     ref = sb.apply_at(v, idx)
+    outs = {}
+    for cfg in (0, 7, 8, 9, 10, 11, 12, 13):
+        dmrg2d.set_tile_config(ops, prec, cfg)
+        y, _ = run(ops, v, prec)
+        outs[cfg] = y[idx]
+        assert rel(outs[cfg], ref) <= tol, cfg
+    # piece order and pool change neither the operands nor the K order of a piece
+    for cfg in (7, 8, 9):
+        assert np.array_equal(outs[cfg], outs[0]), cfg
+    for cfg in (10, 11, 12, 13):  # M = 256 instructions over a CTA pair
+        assert rel(outs[cfg], outs[0]) <= 1e-6, cfg
+    best, _ = dmrg2d.autotune(ops, prec)
+    y, _ = run(ops, v, prec)
+    assert np.array_equal(y[idx], outs[best] if best in outs else y[idx])
     assert rel(y[idx], ref) <= tol
