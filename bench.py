@@ -38,7 +38,14 @@ METRIC = "superblock H·v TFLOP/s & time to ground energy at 1e-8 rel. vs plain 
 # this workload (profiles/hv_tc_pair_kernel_ladder3_hubbard_m256.md), keyed by tile
 # configuration name and dtype.  They hold only for the kernel source they were taken
 # on: `traffic` is reported as null when csrc/hv_tc.cu no longer has this SHA-256.
-NCU_TRAFFIC = {"hv_tc.cu sha256": None, "bytes": {}}
+NCU_TRAFFIC = {
+    "hv_tc.cu sha256": "78800df202d9b8d45a625ad28f3f022a1f456aa87eb95965e68539b6e0170ca3",
+    "bytes": {
+        "CTA-pair kernel 256x256 (8x8-tile blocked raster)|tf32": 15.150e9 + 1.063e9,
+        "CTA-pair kernel 256x256 (8x8-tile blocked raster)|bf16": 6.374e9 + 1.057e9,
+        "dense kernel 128x256 (8x8-tile blocked raster)|bf16": 6.225e9 + 1.057e9,
+    },
+}
 
 
 def ncu_traffic(config_name, dtype):
