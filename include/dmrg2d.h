@@ -335,6 +335,55 @@ int dmrg2d_mlp_make_batch(const dmrg2d_ops* ops, const double* x_k, const double
 
 void dmrg2d_free_ops(dmrg2d_ops* ops);
 
+/* ---- finite-system direct 2-D DMRG around the superblock H·v ----------------------------
+ * The paper's algorithm (its description around Fig. 2): a DMRG step takes the
+ * superblock block 1 + column 2 + column 3 + block 4, finds its ground state (HMED:
+ * dmrg2d_lanczos_ground on dmrg2d_build_ops), forms the reduced density matrix of the
+ * half that grows (DMF: rho_L = V V^T over (i1, i2), or rho_R = V^T V over (i3, i4)),
+ * diagonalises it (DMD) and keeps its m leading eigenvectors U as the basis of the new
+ * block, into which the block Hamiltonian and the boundary-column operators are
+ * transformed (U^T O U).  Blocks grow by one whole column.  The infinite-system warm-up
+ * grows block 1 and its mirror image block 4 together until the superblock spans the
+ * lattice; each finite sweep then moves to the right end, to the left end and back to
+ * the middle.
+ * Supported: Heisenberg ladders (model->kind == DMRG2D_HEISENBERG), open along the
+ * legs, n_columns even and >= 4, superblocks without quantum-number sectors.
+ * Density matrices and their eigenvectors are FP64 on the GPU (cuBLAS DSYRK, cuSOLVER
+ * dsyevd); ties in the density-matrix spectrum keep the eigenvectors dsyevd returns last.
+ * Ground states: `precision` FP64 runs the plain Lanczos; TF32/BF16 the mixed solver
+ * with FP64 refinement where the tensor-core path supports the superblock's shapes
+ * (plain FP64 otherwise).  Each step starts from a seeded random vector.
+ * report: caller-owned arrays of `cap` entries receive, per step in order, the
+ * superblock ground energy, the truncation error 1 - (kept weight), the number of
+ * columns in block 1 and the sweep index (-1 for the warm-up); n_steps counts all
+ * steps (entries beyond cap are not stored).  Synchronises `stream`.
+ * Errors: EINVAL (bad options), EUNSUPPORTED (model), solver and CUDA errors. */
+typedef struct dmrg2d_sweep_opts {
+  int n_columns;       /* L: columns of the ladder (even, >= 4)                       */
+  int m_warmup;        /* states kept during the warm-up                              */
+  int n_sweeps;        /* finite sweeps                                               */
+  const int* m_sweep;  /* states kept in sweep s (n_sweeps entries)                  */
+  int precision;       /* H·v precision of the ground-state solves                    */
+  double tol;          /* ground-state residual tolerance (relative to |E|)           */
+  int max_iter;        /* Lanczos steps per solve (plain) / inner steps (mixed)       */
+  int krylov_dim;      /* Lanczos basis before restart                                */
+  uint64_t seed;       /* start vectors                                               */
+} dmrg2d_sweep_opts;
+
+typedef struct dmrg2d_sweep_report {
+  int cap;             /* entries the arrays below hold                               */
+  int n_steps;         /* steps done                                                  */
+  double* energy;
+  double* trunc;
+  int* l;
+  int* sweep;
+  double seconds;      /* wall time of the call                                       */
+  double solve_seconds;/* of which ground-state solves                                */
+} dmrg2d_sweep_report;
+
+int dmrg2d_sweep(const dmrg2d_model* model, const dmrg2d_sweep_opts* opts,
+                 dmrg2d_sweep_report* report, void* stream);
+
 /* Thread-local text of the last error of this thread ("" if none). */
 const char* dmrg2d_last_error(void);
 

@@ -193,6 +193,14 @@ int check_block(const dmrg2d_block* b, int n_legs, int kind, const char* name) {
 
 }  // namespace
 
+void spin_column_ops(int n, double J_rung, bool pbc, SpinColumnOps* out) {
+  const Column c = spin_column(n, J_rung, pbc);
+  out->d = c.d;
+  out->H = c.H;
+  out->sz = c.sz;
+  out->sp = c.sp;
+}
+
 // Assemble the packed operators on the host.
 static int assemble(const dmrg2d_model* M, const dmrg2d_block* L, const dmrg2d_block* R,
                     dmrg2d_ops* ops, std::vector<double>& HL, std::vector<double>& HR) {

@@ -13,6 +13,14 @@
 
 namespace dmrg2d {
 
+// ---- exact spin-column operators (row-major d x d), shared with the DMRG sweep --------
+struct SpinColumnOps {
+  int d = 0;
+  std::vector<double> H;                     // rung bonds of one column
+  std::vector<std::vector<double>> sz, sp;   // per leg: S^z_y, S^+_y
+};
+void spin_column_ops(int n, double J_rung, bool pbc, SpinColumnOps* out);
+
 // ---- error reporting (thread-local message, negative status codes) --------------------
 int set_error(int code, const char* fmt, ...);
 void clear_error();

@@ -39,6 +39,19 @@ class Block(C.Structure):
                 ("qn", C.POINTER(C.c_int32))]
 
 
+class SweepOpts(C.Structure):
+    _fields_ = [("n_columns", C.c_int), ("m_warmup", C.c_int), ("n_sweeps", C.c_int),
+                ("m_sweep", C.POINTER(C.c_int)), ("precision", C.c_int), ("tol", C.c_double),
+                ("max_iter", C.c_int), ("krylov_dim", C.c_int), ("seed", C.c_uint64)]
+
+
+class SweepReport(C.Structure):
+    _fields_ = [("cap", C.c_int), ("n_steps", C.c_int), ("energy", C.POINTER(C.c_double)),
+                ("trunc", C.POINTER(C.c_double)), ("l", C.POINTER(C.c_int)),
+                ("sweep", C.POINTER(C.c_int)), ("seconds", C.c_double),
+                ("solve_seconds", C.c_double)]
+
+
 class OpsInfo(C.Structure):
     _fields_ = [("n_vec", C.c_int64), ("m1", C.c_int), ("m4", C.c_int), ("d", C.c_int),
                 ("n_legs", C.c_int), ("n_blk_left", C.c_int), ("n_blk_right", C.c_int),
@@ -81,6 +94,8 @@ SIGNATURES = {
                                                 C.c_void_p]),
     "dmrg2d_default_solver_opts": (None, [C.POINTER(SolverOpts)]),
     "dmrg2d_wait_selftest": (C.c_int, [C.c_double, C.c_void_p]),
+    "dmrg2d_sweep": (C.c_int, [C.POINTER(Model), C.POINTER(SweepOpts), C.POINTER(SweepReport),
+                               C.c_void_p]),
     "dmrg2d_diagonal": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "dmrg2d_default_davidson_opts": (None, [C.POINTER(DavidsonOpts)]),
     "dmrg2d_davidson_ground": (C.c_int, [C.c_void_p, C.POINTER(DavidsonOpts), C.c_void_p,
@@ -196,12 +211,16 @@ class Ops:
             pass
 
 
-def build_ops(model: dict, left: dict, right: dict, target=None, stream=None) -> Ops:
+def _model(model: dict) -> Model:
     kind = HEISENBERG if model["kind"] == "heisenberg" else HUBBARD
-    nq = 1 if kind == HEISENBERG else 2
-    mdl = Model(kind, int(model["n_legs"]), float(model.get("J_leg", 1.0)),
-                float(model.get("J_rung", 1.0)), float(model.get("t", 1.0)),
-                float(model.get("U", 0.0)), int(bool(model.get("rung_pbc", False))))
+    return Model(kind, int(model["n_legs"]), float(model.get("J_leg", 1.0)),
+                 float(model.get("J_rung", 1.0)), float(model.get("t", 1.0)),
+                 float(model.get("U", 0.0)), int(bool(model.get("rung_pbc", False))))
+
+
+def build_ops(model: dict, left: dict, right: dict, target=None, stream=None) -> Ops:
+    mdl = _model(model)
+    nq = 1 if mdl.kind == HEISENBERG else 2
     la, ra = _BlockArgs(left, nq), _BlockArgs(right, nq)
     tgt = None
     if target is not None:
@@ -443,3 +462,22 @@ def mlp_make_batch(ops: Ops, x_k, r_k, theta, x_final, D, idx, X, w, T, stream=N
         C.c_void_p(x_final.data_ptr()), C.c_void_p(D.data_ptr()), C.c_void_p(idx.data_ptr()),
         int(idx.numel()), C.c_void_p(X.data_ptr()), C.c_void_p(w.data_ptr()),
         C.c_void_p(T.data_ptr()), _stream(stream)))
+
+
+def sweep(model: dict, n_columns: int, m_warmup: int, m_sweeps, precision=FP64, tol=1e-10,
+          max_iter=300, krylov_dim=100, seed=1, cap=4096, stream=None) -> dict:
+    """dmrg2d_sweep: warm-up plus one finite sweep per entry of m_sweeps on an n-leg
+    Heisenberg ladder of n_columns columns.  Returns the per-step energy, truncation
+    error, block-1 length and sweep index (-1 = warm-up), and the timings."""
+    precision = PRECISION.get(precision, precision)
+    ms = (C.c_int * max(1, len(m_sweeps)))(*[int(m) for m in m_sweeps])
+    opts = SweepOpts(int(n_columns), int(m_warmup), len(m_sweeps), ms, int(precision), float(tol),
+                     int(max_iter), int(krylov_dim), int(seed))
+    e, t = (C.c_double * cap)(), (C.c_double * cap)()
+    ll, sw = (C.c_int * cap)(), (C.c_int * cap)()
+    rep = SweepReport(cap, 0, e, t, ll, sw, 0.0, 0.0)
+    mdl = _model(model)
+    _check(lib().dmrg2d_sweep(C.byref(mdl), C.byref(opts), C.byref(rep), _stream(stream)))
+    n = min(rep.n_steps, cap)
+    return {"energy": list(e[:n]), "trunc": list(t[:n]), "l": list(ll[:n]), "sweep": list(sw[:n]),
+            "n_steps": rep.n_steps, "seconds": rep.seconds, "solve_seconds": rep.solve_seconds}

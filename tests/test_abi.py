@@ -74,3 +74,19 @@ def test_wait_selftest_rejects_bad_limits(lib):
     from paper_0707_0159_gb300 import dmrg2d
     assert dmrg2d.wait_selftest(0.0) == -1      # EINVAL before any device work
     assert dmrg2d.wait_selftest(5.0) == -1
+
+
+def test_sweep_rejects_bad_options(lib):
+    from paper_0707_0159_gb300 import dmrg2d, synth
+    mdl = synth.model("heisenberg", 2, J_leg=1.0, J_rung=1.0)
+    for kw in (dict(n_columns=5), dict(n_columns=2), dict(m_warmup=0), dict(tol=0.0)):
+        args = dict(n_columns=6, m_warmup=8, m_sweeps=[8], tol=1e-10)
+        args.update(kw)
+        n_columns, m_warmup = args.pop("n_columns"), args.pop("m_warmup")
+        with pytest.raises(dmrg2d.Dmrg2dError) as e:
+            dmrg2d.sweep(mdl, n_columns, m_warmup, **args)
+        assert e.value.code == -1
+    hub = synth.model("hubbard", 2, t=1.0, U=8.0)
+    with pytest.raises(dmrg2d.Dmrg2dError) as e:
+        dmrg2d.sweep(hub, 6, 8, [8])
+    assert e.value.code == -8
