@@ -332,6 +332,8 @@ def run_ours(args):
 
     if args.tte and rank == 0:
         out["time_to_energy"] = time_to_energy(ops, n, prec, args, dev)
+    if args.sweep and rank == 0:
+        out["dmrg_sweep"] = dmrg_sweep_run(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(seconds=float(args.ref_seconds))
     if rank == 0:
@@ -339,6 +341,25 @@ def run_ours(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def dmrg_sweep_run(args):
+    """The DMRG sweep around the path: 4 x 12 open Heisenberg ladder (J = 1), warm-up
+    with m = 64, then finite sweeps with the --sweep-m schedule, superblock ground states
+    in --precision with FP64 refinement; energies per sweep and the time split."""
+    from paper_0707_0159_gb300 import dmrg2d, synth
+    mdl = synth.model("heisenberg", 4, J_leg=1.0, J_rung=1.0)
+    ms = [int(m) for m in args.sweep_m.split(",")]
+    out = dmrg2d.sweep(mdl, 12, m_warmup=64, m_sweeps=ms, precision=args.precision, tol=1e-9,
+                       max_iter=600, krylov_dim=80)
+    e, sw = out["energy"], out["sweep"]
+    per = {str(s): min(e[i] for i in range(len(e)) if sw[i] == s) for s in sorted(set(sw))}
+    return {"lattice": "4x12 open Heisenberg ladder, J=1", "m_warmup": 64, "m_sweeps": ms,
+            "precision": args.precision, "steps": out["n_steps"],
+            "energy_min_per_sweep": per, "energy_last": e[-1], "max_trunc": max(out["trunc"]),
+            "solver_steps": sum(out["iters"]), "seconds": out["seconds"],
+            "solve_seconds": out["solve_seconds"], "build_seconds": out["build_seconds"],
+            "density_matrix_seconds": out["dm_seconds"], "renorm_seconds": out["renorm_seconds"]}
 
 
 def time_to_energy(ops, n, prec, args, dev):
@@ -382,6 +403,8 @@ def main():
     ap.add_argument("--tte-tol", type=float, default=1e-7)
     ap.add_argument("--tte-fp64-max-iter", type=int, default=900)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep", action="store_true", help="also run the DMRG sweep (4 x 12 ladder)")
+    ap.add_argument("--sweep-m", default="128,256", help="states kept per finite sweep")
     ap.add_argument("--tile-config", type=int, default=None,
                     help="tensor-core tile configuration index instead of the autotuner")
     ap.add_argument("--ref-seconds", type=float, default=15.0)

@@ -352,10 +352,14 @@ void dmrg2d_free_ops(dmrg2d_ops* ops);
  * dsyevd); ties in the density-matrix spectrum keep the eigenvectors dsyevd returns last.
  * Ground states: `precision` FP64 runs the plain Lanczos; TF32/BF16 the mixed solver
  * with FP64 refinement where the tensor-core path supports the superblock's shapes
- * (plain FP64 otherwise).  Each step starts from a seeded random vector.
+ * (plain FP64 otherwise).  Warm-up steps start from a seeded random vector; every
+ * finite-sweep step starts from the previous ground state carried into its basis (the
+ * wavefunction transformation: the new block's U and the stored U of the block that
+ * splits into a smaller block and a column).
  * report: caller-owned arrays of `cap` entries receive, per step in order, the
  * superblock ground energy, the truncation error 1 - (kept weight), the number of
- * columns in block 1 and the sweep index (-1 for the warm-up); n_steps counts all
+ * columns in block 1, the sweep index (-1 for the warm-up) and the solver's steps
+ * (Lanczos steps, or low-precision inner steps of the mixed solver); n_steps counts all
  * steps (entries beyond cap are not stored).  Synchronises `stream`.
  * Errors: EINVAL (bad options), EUNSUPPORTED (model), solver and CUDA errors. */
 typedef struct dmrg2d_sweep_opts {
@@ -377,8 +381,12 @@ typedef struct dmrg2d_sweep_report {
   double* trunc;
   int* l;
   int* sweep;
-  double seconds;      /* wall time of the call                                       */
-  double solve_seconds;/* of which ground-state solves                                */
+  int* iters;          /* ground-state solver steps (Lanczos or inner low-precision)  */
+  double seconds;      /* wall time of the call, of which:                            */
+  double solve_seconds;/*   ground-state solves (dmrg2d_lanczos_ground)              */
+  double build_seconds;/*   superblock operator assembly (dmrg2d_build_ops)          */
+  double dm_seconds;   /*   density matrix and its eigenvectors                      */
+  double renorm_seconds;/*  new block operators U^T O U and their copy to the host   */
 } dmrg2d_sweep_report;
 
 int dmrg2d_sweep(const dmrg2d_model* model, const dmrg2d_sweep_opts* opts,

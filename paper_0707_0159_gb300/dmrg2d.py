@@ -48,8 +48,10 @@ class SweepOpts(C.Structure):
 class SweepReport(C.Structure):
     _fields_ = [("cap", C.c_int), ("n_steps", C.c_int), ("energy", C.POINTER(C.c_double)),
                 ("trunc", C.POINTER(C.c_double)), ("l", C.POINTER(C.c_int)),
-                ("sweep", C.POINTER(C.c_int)), ("seconds", C.c_double),
-                ("solve_seconds", C.c_double)]
+                ("sweep", C.POINTER(C.c_int)), ("iters", C.POINTER(C.c_int)),
+                ("seconds", C.c_double),
+                ("solve_seconds", C.c_double), ("build_seconds", C.c_double),
+                ("dm_seconds", C.c_double), ("renorm_seconds", C.c_double)]
 
 
 class OpsInfo(C.Structure):
@@ -474,10 +476,13 @@ def sweep(model: dict, n_columns: int, m_warmup: int, m_sweeps, precision=FP64, 
     opts = SweepOpts(int(n_columns), int(m_warmup), len(m_sweeps), ms, int(precision), float(tol),
                      int(max_iter), int(krylov_dim), int(seed))
     e, t = (C.c_double * cap)(), (C.c_double * cap)()
-    ll, sw = (C.c_int * cap)(), (C.c_int * cap)()
-    rep = SweepReport(cap, 0, e, t, ll, sw, 0.0, 0.0)
+    ll, sw, it = (C.c_int * cap)(), (C.c_int * cap)(), (C.c_int * cap)()
+    rep = SweepReport(cap, 0, e, t, ll, sw, it, 0.0, 0.0, 0.0, 0.0, 0.0)
     mdl = _model(model)
     _check(lib().dmrg2d_sweep(C.byref(mdl), C.byref(opts), C.byref(rep), _stream(stream)))
     n = min(rep.n_steps, cap)
     return {"energy": list(e[:n]), "trunc": list(t[:n]), "l": list(ll[:n]), "sweep": list(sw[:n]),
-            "n_steps": rep.n_steps, "seconds": rep.seconds, "solve_seconds": rep.solve_seconds}
+            "iters": list(it[:n]),
+            "n_steps": rep.n_steps, "seconds": rep.seconds, "solve_seconds": rep.solve_seconds,
+            "build_seconds": rep.build_seconds, "dm_seconds": rep.dm_seconds,
+            "renorm_seconds": rep.renorm_seconds}

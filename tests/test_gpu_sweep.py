@@ -6,7 +6,9 @@
   spectrum has a gap at the cut (SU(2) multiplets are not split, so the kept subspace is
   unique): the per-step energies and truncation errors equal the oracle's;
 * mixed precision (TF32 superblock H·v + FP64 refinement) on a 4-leg ladder gives the
-  plain FP64 sweep's energies.
+  plain FP64 sweep's energies;
+* the wavefunction transformation: untruncated, each carried-over ground state is the
+  next superblock's ground state.
 """
 import numpy as np
 import pytest
@@ -33,6 +35,19 @@ def test_untruncated_sweep_equals_ed():
     sw = np.array(out["sweep"])
     assert np.allclose(e[sw >= 0], e_ed, rtol=0, atol=1e-9), (e, e_ed)
     assert max(out["trunc"]) <= 1e-12
+
+
+def test_wavefunction_transformation_gives_the_next_ground_state():
+    """Without truncation the previous ground state, carried into the next superblock's
+    basis, is that superblock's ground state: every finite step after the first (which
+    starts from a random vector) converges at the first convergence check."""
+    mdl = model(2)
+    out = dmrg2d.sweep(mdl, 6, m_warmup=64, m_sweeps=[64, 64], precision="fp64", tol=1e-10,
+                       max_iter=600)
+    sw = np.array(out["sweep"])
+    it = np.array(out["iters"])[sw >= 0]
+    assert it[0] > 10                      # seeded random start
+    assert np.all(it[1:] <= 5), it         # one convergence check (every 5 steps)
 
 
 @pytest.mark.parametrize("n,m", [(2, 8), (3, 16)])
