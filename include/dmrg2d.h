@@ -276,8 +276,9 @@ int dmrg2d_diagonal(const dmrg2d_ops* ops, double* out, void* stream);
  * Lowest eigenpair by Davidson: expand an orthonormal basis V by the preconditioned
  * residual t = M(theta) r, Rayleigh-Ritz on V^T H V, restart from the Ritz vector when
  * V holds max_subspace vectors.  Preconditioners: NONE (t = r), JACOBI
- * (t_i = r_i / (theta - D_i), D = diag H), MLP (t_i = (r_i / s_D) g(x_i), g a trained
- * dmrg2d_mlp, see below).  With precision TF32/BF16 the basis images H V use the
+ * (t_i = r_i / (theta - D_i), D = diag H), MLP (t_i = (r_i / s_D) j(d_i) (1 + y(x_i)):
+ * the Jacobi factor j(d) = -clamp(1/d, +-16) in units of s_D, corrected by the output y
+ * of a trained dmrg2d_mlp, see below; y = 0 is plain Jacobi).  With precision TF32/BF16 the basis images H V use the
  * low-precision H~·v; refine = 1 then finishes with the FP64 outer loop of
  * dmrg2d_lanczos_ground (tolerance refine_tol, inner_iter CG steps, outer_max steps).
  * Stops when ||H x - theta x|| <= tol * |theta|.  log_cap > 0 records the first
@@ -310,14 +311,16 @@ int dmrg2d_davidson_ground(const dmrg2d_ops* ops, const dmrg2d_davidson_opts* op
  * one device array: W1[hidden][4], b1[hidden], W2[hidden][hidden], b2[hidden],
  * w3[hidden], b3.  Inputs of component i (d_i = (D_i - theta)/s_D, s_D the RMS of
  * D - theta): clamp(d_i, +-8), clamp(1/d_i, +-16)/16, clamp of the sector's mean
- * (D - theta)/s_D, log(sector size)/16.  Trained on weighted least squares
- *   L = 1/(2B) sum_b (w_b g(X_b) - T_b)^2
+ * (D - theta)/s_D, log(sector size)/16.  Output layer initialised to zero (y = 0:
+ * Jacobi).  Trained on weighted least squares
+ *   L = 1/(2B) sum_b (w_b y(X_b) - T_b)^2
  * with batches built by dmrg2d_mlp_make_batch from a logged Davidson step (x_k, r_k,
- * theta_k) and the converged vector x_f: w = r_i/(s_D s_t), T = alpha delta_i / s_t,
- * delta = x_f - (x_k . x_f) x_k, alpha = (delta . t_J)/(delta . delta), t_J the Jacobi
- * correction and s_t its RMS.  All arrays are device arrays unless noted; X is B x 4.
- * The Davidson solver evaluates g exactly on 1024 values of d per sector each step and
- * interpolates linearly in between. */
+ * theta_k) and the converged vector x_f: w = (r_i/s_D) j(d_i)/s_t,
+ * T = alpha delta_i / s_t - w, delta = x_f - (x_k . x_f) x_k,
+ * alpha = (delta . t_J)/(delta . delta), t_J the Jacobi correction and s_t its RMS (so
+ * w y - T = ((r/s_D) j (1 + y) - alpha delta)/s_t).  All arrays are device arrays unless
+ * noted; X is B x 4.  The Davidson solver evaluates y exactly on 1024 values of d per
+ * sector each step and interpolates linearly in between. */
 int dmrg2d_mlp_create(int hidden, uint64_t seed, dmrg2d_mlp** out);
 void dmrg2d_mlp_free(dmrg2d_mlp* mlp);
 int dmrg2d_mlp_num_params(const dmrg2d_mlp* mlp);

@@ -183,7 +183,14 @@ __device__ __forceinline__ int sector_of(const long long* __restrict__ qstart, i
   return lo;
 }
 
-// t_i = (r_i / s_D) * interpolated g(d_i) from the sector's table
+// The Jacobi factor in units of s_D: t_i = r_i / (theta - D_i) = (r_i / s_D) j(d_i),
+// j(d) = -1/d, clamped like the network's input |1/d| <= 16.
+__device__ __forceinline__ double jacobi_factor(double d) {
+  const double inv = d != 0.0 ? 1.0 / d : 16.0;
+  return -fmin(fmax(inv, -16.0), 16.0);
+}
+
+// t_i = (r_i / s_D) j(d_i) (1 + y(d_i)), y interpolated from the sector's table
 __global__ void k_apply_table(double* __restrict__ t, const double* __restrict__ r,
                               const double* __restrict__ D, const float* __restrict__ table,
                               const double* __restrict__ qp, const long long* __restrict__ qstart,
@@ -198,8 +205,8 @@ __global__ void k_apply_table(double* __restrict__ t, const double* __restrict__
     const int k = min((int)u, GRID - 2);
     const double f = u - k;
     const float* tq = table + (size_t)q * GRID;
-    const double g = (1.0 - f) * tq[k] + f * tq[k + 1];
-    t[i] = r[i] / sD * g;
+    const double y = (1.0 - f) * tq[k] + f * tq[k + 1];
+    t[i] = r[i] / sD * jacobi_factor(d) * (1.0 + y);
   }
 }
 
@@ -214,8 +221,11 @@ __global__ void k_make_batch(const double* __restrict__ xk, const double* __rest
     const long long i = idx[b];
     const int q = sector_of(qstart, nq, i);
     features(D[i], theta, sD, (float)qp[4 * q + 2], (float)qp[4 * q + 3], X + (size_t)b * MF);
-    w[b] = (float)(rk[i] / (sD * st));
-    T[b] = (float)(alpha * (xf[i] - proj * xk[i]) / st);
+    // the preconditioner is (r/s_D) j (1 + y): w y - T with w = (r/s_D) j / s_t and
+    // T = (target - (r/s_D) j) / s_t fits the correction y to plain Jacobi
+    const double wj = rk[i] / sD * jacobi_factor((D[i] - theta) / sD) / st;
+    w[b] = (float)wj;
+    T[b] = (float)(alpha * (xf[i] - proj * xk[i]) / st - wj);
   }
 }
 
@@ -519,7 +529,8 @@ extern "C" int dmrg2d_mlp_create(int hidden, uint64_t seed, dmrg2d_mlp** out) {
   const int H = hidden;
   for (int i = 0; i < H * MF; ++i) h[i] = nd(rng) / std::sqrt((float)MF);
   for (int i = 0; i < H * H; ++i) h[off_W2(H) + i] = nd(rng) / std::sqrt((float)H);
-  for (int i = 0; i < H; ++i) h[off_w3(H) + i] = nd(rng) / std::sqrt((float)H);
+  // output layer starts at zero: y = 0 is plain Jacobi (the factor is j(d) (1 + y))
+  for (int i = 0; i < H; ++i) h[off_w3(H) + i] = 0.f;
   int st = DMRG2D_OK;
   for (float** b : {&M->p, &M->g, &M->m1, &M->m2})
     if (st == DMRG2D_OK && cudaMalloc((void**)b, (size_t)M->np * 4) != cudaSuccess)

@@ -64,8 +64,10 @@ def test_davidson_jacobi_matches_lanczos():
 def test_mlp_kernels_match_oracle():
     H, B = 32, 1000
     net = dmrg2d.MLP(hidden=H, seed=3)
-    p = net.get_params().astype(np.float64)
     rng = np.random.default_rng(0)
+    # random parameters everywhere (a new network's output layer starts at zero)
+    net.set_params((0.3 * rng.standard_normal(net.n_params)).astype(np.float32))
+    p = net.get_params().astype(np.float64)
     X = rng.normal(size=(B, 4)).astype(np.float32)
     w = rng.normal(size=B).astype(np.float32)
     T = rng.normal(size=B).astype(np.float32)
