@@ -366,54 +366,120 @@ __global__ void k_tridiag_ground(const double* __restrict__ alpha, const double*
 }
 
 // lowest eigenpair of a small symmetric matrix G (n x n, leading dim ldg) by cyclic Jacobi
-__global__ void k_small_eigh(const double* __restrict__ G, int n, int ldg, double* __restrict__ out,
-                             double* __restrict__ c, double* __restrict__ scr) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double* A = scr;          // n*n
-  double* Vv = scr + n * n; // n*n
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) {
-      A[i * n + j] = 0.5 * (G[i * ldg + j] + G[j * ldg + i]);
-      Vv[i * n + j] = i == j ? 1.0 : 0.0;
-    }
+// Lowest eigenpair of the symmetrised n x n matrix G (n <= 48): cyclic Jacobi with the
+// round-robin ordering, one block: in each round the N/2 disjoint pairs (p, q) of a
+// tournament schedule (N = n rounded up to even, a padded index never rotates) get their
+// rotations from the same A, then all column and all row updates run in parallel.  A and
+// the rotation product V live in shared memory.  out[0] = eigenvalue, c = eigenvector
+// (sign: first component >= 0).  scr is unused (kept for the call signature).
+constexpr int SE_MAX = 48;
+constexpr int SE_THREADS = 256;
+__global__ void __launch_bounds__(SE_THREADS)
+k_small_eigh(const double* __restrict__ G, int n, int ldg, double* __restrict__ out,
+             double* __restrict__ c, double* __restrict__ scr) {
+  __shared__ double A[SE_MAX][SE_MAX + 1];
+  __shared__ double V[SE_MAX][SE_MAX + 1];
+  __shared__ double rc[SE_MAX / 2], rs[SE_MAX / 2];
+  __shared__ int rp[SE_MAX / 2], rq[SE_MAX / 2];
+  __shared__ double red[SE_THREADS];
+  __shared__ int stop;
+  const int tid = threadIdx.x;
+  const int N = n + (n & 1), half = N / 2;
+  for (int e = tid; e < n * n; e += SE_THREADS) {
+    const int i = e / n, j = e % n;
+    A[i][j] = 0.5 * (G[i * ldg + j] + G[j * ldg + i]);
+    V[i][j] = i == j ? 1.0 : 0.0;
+  }
+  __syncthreads();
   for (int sweep = 0; sweep < 60; ++sweep) {
     double off = 0.0, tot = 0.0;
-    for (int i = 0; i < n; ++i)
-      for (int j = 0; j < n; ++j) {
-        tot += A[i * n + j] * A[i * n + j];
-        if (i != j) off += A[i * n + j] * A[i * n + j];
+    for (int e = tid; e < n * n; e += SE_THREADS) {
+      const int i = e / n, j = e % n;
+      const double v = A[i][j] * A[i][j];
+      tot += v;
+      if (i != j) off += v;
+    }
+    red[tid] = off;
+    __syncthreads();
+    for (int w = SE_THREADS / 2; w > 0; w >>= 1) {
+      if (tid < w) red[tid] += red[tid + w];
+      __syncthreads();
+    }
+    const double off_sum = red[0];
+    __syncthreads();
+    red[tid] = tot;
+    __syncthreads();
+    for (int w = SE_THREADS / 2; w > 0; w >>= 1) {
+      if (tid < w) red[tid] += red[tid + w];
+      __syncthreads();
+    }
+    if (tid == 0) stop = off_sum <= 1e-32 * red[0] + 1e-300;
+    __syncthreads();
+    if (stop) break;
+    for (int round = 0; round < N - 1; ++round) {
+      if (tid < half) {  // pair tid of this round: (N-1, round) and a circle around it
+        int p, q;
+        if (tid == 0) {
+          p = round;
+          q = N - 1;
+        } else {
+          p = (round + tid) % (N - 1);
+          q = (round + N - 1 - tid) % (N - 1);
+        }
+        if (p > q) {
+          const int t = p;
+          p = q;
+          q = t;
+        }
+        double cs = 1.0, sn = 0.0;
+        if (q < n) {
+          const double apq = A[p][q];
+          if (apq != 0.0) {
+            const double th = (A[q][q] - A[p][p]) / (2.0 * apq);
+            const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+            cs = 1.0 / sqrt(t * t + 1.0);
+            sn = t * cs;
+          }
+        }
+        rp[tid] = p;
+        rq[tid] = q;
+        rc[tid] = cs;
+        rs[tid] = sn;
       }
-    if (off <= 1e-32 * tot + 1e-300) break;
-    for (int p = 0; p < n; ++p)
-      for (int q = p + 1; q < n; ++q) {
-        const double apq = A[p * n + q];
-        if (apq == 0.0) continue;
-        const double th = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
-        const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-        const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
-        for (int r = 0; r < n; ++r) {  // A <- J^T A J
-          const double arp = A[r * n + p], arq = A[r * n + q];
-          A[r * n + p] = cs * arp - sn * arq;
-          A[r * n + q] = sn * arp + cs * arq;
-        }
-        for (int r = 0; r < n; ++r) {
-          const double apr = A[p * n + r], aqr = A[q * n + r];
-          A[p * n + r] = cs * apr - sn * aqr;
-          A[q * n + r] = sn * apr + cs * aqr;
-        }
-        for (int r = 0; r < n; ++r) {
-          const double vrp = Vv[r * n + p], vrq = Vv[r * n + q];
-          Vv[r * n + p] = cs * vrp - sn * vrq;
-          Vv[r * n + q] = sn * vrp + cs * vrq;
-        }
+      __syncthreads();
+      for (int e = tid; e < half * n; e += SE_THREADS) {  // A <- A J, V <- V J (columns)
+        const int k = e / n, r = e % n;
+        const int p = rp[k], q = rq[k];
+        if (q >= n || rs[k] == 0.0) continue;
+        const double cs = rc[k], sn = rs[k];
+        const double arp = A[r][p], arq = A[r][q];
+        A[r][p] = cs * arp - sn * arq;
+        A[r][q] = sn * arp + cs * arq;
+        const double vrp = V[r][p], vrq = V[r][q];
+        V[r][p] = cs * vrp - sn * vrq;
+        V[r][q] = sn * vrp + cs * vrq;
       }
+      __syncthreads();
+      for (int e = tid; e < half * n; e += SE_THREADS) {  // A <- J^T A (rows)
+        const int k = e / n, r = e % n;
+        const int p = rp[k], q = rq[k];
+        if (q >= n || rs[k] == 0.0) continue;
+        const double cs = rc[k], sn = rs[k];
+        const double apr = A[p][r], aqr = A[q][r];
+        A[p][r] = cs * apr - sn * aqr;
+        A[q][r] = sn * apr + cs * aqr;
+      }
+      __syncthreads();
+    }
   }
-  int best = 0;
-  for (int i = 1; i < n; ++i)
-    if (A[i * n + i] < A[best * n + best]) best = i;
-  double sg = Vv[best] >= 0 ? 1.0 : -1.0;
-  for (int i = 0; i < n; ++i) c[i] = sg * Vv[i * n + best];
-  out[0] = A[best * n + best];
+  if (tid == 0) {
+    int best = 0;
+    for (int i = 1; i < n; ++i)
+      if (A[i][i] < A[best][best]) best = i;
+    const double sg = V[0][best] >= 0 ? 1.0 : -1.0;
+    for (int i = 0; i < n; ++i) c[i] = sg * V[i][best];
+    out[0] = A[best][best];
+  }
 }
 
 // ---- host-side helpers ---------------------------------------------------------------------
@@ -748,7 +814,7 @@ static int mixed_outer(Ctx& C, const dmrg2d_solver_opts* o, double* x, double* e
   int status = DMRG2D_ENOCONV;
   for (int outer = 0; outer <= o->outer_max; ++outer) {
     D2_CUDA(cudaMemcpyAsync(G, Gh.data(), sizeof(double) * smax * smax, cudaMemcpyHostToDevice, C.s));
-    k_small_eigh<<<1, 1, 0, C.s>>>(G, s, smax, sc + 5, cc, scr);
+    k_small_eigh<<<1, SE_THREADS, 0, C.s>>>(G, s, smax, sc + 5, cc, scr);
     D2_CUDA(cudaGetLastError());
     D2_TRY(C.combo(x, U, n, s, cc, 0));
     D2_TRY(C.combo(hx, W, n, s, cc, 0));
@@ -1131,7 +1197,7 @@ int davidson_solve(Ctx& C, const dmrg2d_davidson_opts* o, double* x, double* ene
   double theta = 0.0, rn = INFINITY;
   for (it = 1; it <= o->max_iter; ++it) {
     D2_CUDA(cudaMemcpyAsync(G, Gh.data(), sizeof(double) * smax * smax, cudaMemcpyHostToDevice, C.s));
-    k_small_eigh<<<1, 1, 0, C.s>>>(G, s, smax, sc + 5, cc, scr);
+    k_small_eigh<<<1, SE_THREADS, 0, C.s>>>(G, s, smax, sc + 5, cc, scr);
     D2_CUDA(cudaGetLastError());
     D2_TRY(C.combo(x, V, n, s, cc, 0));
     D2_TRY(C.combo(hx, W, n, s, cc, 0));
