@@ -344,17 +344,20 @@ def run_ours(args):
 
 
 def dmrg_sweep_run(args):
-    """The DMRG sweep around the path: 4 x 12 open Heisenberg ladder (J = 1), warm-up
-    with m = 64, then finite sweeps with the --sweep-m schedule, superblock ground states
-    in --precision with FP64 refinement; energies per sweep and the time split."""
+    """The DMRG sweep around the path: 4 x 12 open Heisenberg ladder (J = 1) in the
+    S^z_tot = 0 sector, warm-up with --sweep-m-warmup states, then finite sweeps with the
+    --sweep-m schedule, superblock ground states in --precision with FP64 refinement;
+    energies per sweep and the time split."""
     from paper_0707_0159_gb300 import dmrg2d, synth
     mdl = synth.model("heisenberg", 4, J_leg=1.0, J_rung=1.0)
     ms = [int(m) for m in args.sweep_m.split(",")]
-    out = dmrg2d.sweep(mdl, 12, m_warmup=64, m_sweeps=ms, precision=args.precision, tol=1e-9,
-                       max_iter=600, krylov_dim=80)
+    out = dmrg2d.sweep(mdl, 12, m_warmup=args.sweep_m_warmup, m_sweeps=ms,
+                       precision=args.precision, tol=1e-9, max_iter=600, krylov_dim=80,
+                       sectors=True)
     e, sw = out["energy"], out["sweep"]
     per = {str(s): min(e[i] for i in range(len(e)) if sw[i] == s) for s in sorted(set(sw))}
-    return {"lattice": "4x12 open Heisenberg ladder, J=1", "m_warmup": 64, "m_sweeps": ms,
+    return {"lattice": "4x12 open Heisenberg ladder, J=1, S^z_tot = 0 sector",
+            "m_warmup": args.sweep_m_warmup, "m_sweeps": ms,
             "precision": args.precision, "steps": out["n_steps"],
             "energy_min_per_sweep": per, "energy_last": e[-1], "max_trunc": max(out["trunc"]),
             "solver_steps": sum(out["iters"]), "seconds": out["seconds"],
@@ -404,7 +407,9 @@ def main():
     ap.add_argument("--tte-fp64-max-iter", type=int, default=900)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep", action="store_true", help="also run the DMRG sweep (4 x 12 ladder)")
-    ap.add_argument("--sweep-m", default="128,256", help="states kept per finite sweep")
+    ap.add_argument("--sweep-m", default="128,512,512,1024,1024",
+                    help="states kept per finite sweep")
+    ap.add_argument("--sweep-m-warmup", type=int, default=128)
     ap.add_argument("--tile-config", type=int, default=None,
                     help="tensor-core tile configuration index instead of the autotuner")
     ap.add_argument("--ref-seconds", type=float, default=15.0)

@@ -350,7 +350,11 @@ void dmrg2d_free_ops(dmrg2d_ops* ops);
  * lattice; each finite sweep then moves to the right end, to the left end and back to
  * the middle.
  * Supported: Heisenberg ladders (model->kind == DMRG2D_HEISENBERG), open along the
- * legs, n_columns even and >= 4, superblocks without quantum-number sectors.
+ * legs, n_columns even and >= 4; dense superblocks, or (use_sectors) the S^z_tot = 0
+ * sector: blocks carry their states' N_up (grouped by label), the superblock H·v runs
+ * on the sector-restricted layout, and the density matrix, block diagonal in the
+ * growing half's label, is diagonalised sector by sector (dsyevd), keeping the m
+ * largest eigenvalues over all sectors.
  * Density matrices and their eigenvectors are FP64 on the GPU (cuBLAS DSYRK, cuSOLVER
  * dsyevd); ties in the density-matrix spectrum keep the eigenvectors dsyevd returns last.
  * Ground states: `precision` FP64 runs the plain Lanczos; TF32/BF16 the mixed solver
@@ -375,6 +379,8 @@ typedef struct dmrg2d_sweep_opts {
   int max_iter;        /* Lanczos steps per solve (plain) / inner steps (mixed)       */
   int krylov_dim;      /* Lanczos basis before restart                                */
   uint64_t seed;       /* start vectors                                               */
+  int use_sectors;     /* 1: S^z_tot = 0 sector-restricted superblocks (blocks carry  */
+                       /*    N_up labels, density matrices per sector)               */
 } dmrg2d_sweep_opts;
 
 typedef struct dmrg2d_sweep_report {

@@ -126,6 +126,11 @@ int sec_apply(const dmrg2d_ops* ops, const void* v, void* y, int precision, cuda
 int sec_zero_padding(const dmrg2d_ops* ops, double* x, cudaStream_t s);
 int sec_dense_index(const dmrg2d_ops* ops, int64_t* out);
 int sec_count(const dmrg2d_ops* ops);
+// per matrix V_q of a sector-restricted vector: row r -> enlarged-left index i1 + m1 i2
+// (-1 for padding rows), column c -> enlarged-right index i4 + m4 i3 (concatenated over q)
+int sec_layout(const dmrg2d_ops* ops, std::vector<long long>& qbase, std::vector<int>& qld,
+               std::vector<int>& qcols, std::vector<int64_t>& row_left,
+               std::vector<int64_t>& col_right);
 int sec_diag_tables(const dmrg2d_ops* ops, std::vector<long long>& qbase, std::vector<int>& qld,
                     std::vector<int>& qcols, std::vector<double>& rowD, std::vector<int>& rowI2,
                     std::vector<double>& colD, std::vector<int>& colI3);

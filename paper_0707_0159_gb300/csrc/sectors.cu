@@ -646,6 +646,37 @@ int sec_diag_tables(const dmrg2d_ops* ops, std::vector<long long>& qbase, std::v
   return DMRG2D_OK;
 }
 
+int sec_layout(const dmrg2d_ops* ops, std::vector<long long>& qbase, std::vector<int>& qld,
+               std::vector<int>& qcols, std::vector<int64_t>& row_left,
+               std::vector<int64_t>& col_right) {
+  const SecState* S = (const SecState*)ops->sec;
+  if (!S) return set_error(DMRG2D_EINVAL, "not a sector-restricted ops object");
+  const int64_t m1 = ops->m1, m4 = ops->m4;
+  qbase = S->qbase;
+  qld = S->qld;
+  qcols = S->qcols;
+  row_left.clear();
+  col_right.clear();
+  for (int q = 0; q < S->nQ; ++q) {
+    const size_t r0 = row_left.size(), c0 = col_right.size();
+    row_left.resize(r0 + S->qld[q], -1);  // padding rows stay -1
+    col_right.resize(c0 + S->qcols[q], -1);
+    for (size_t r = 0; r < S->rseg.size(); ++r) {
+      const RowSegD& rs = S->rseg[r];
+      if (rs.q != q) continue;
+      const int64_t a0 = S->a_first[S->rs_a[r]], i2 = S->rs_i2[r];
+      for (int i = 0; i < rs.dim; ++i) row_left[r0 + rs.off + i] = a0 + i + m1 * i2;
+    }
+    for (size_t c = 0; c < S->cseg.size(); ++c) {
+      const ColSegD& cs = S->cseg[c];
+      if (cs.q != q) continue;
+      const int64_t b0 = S->b_first[S->cs_b[c]], i3 = S->cs_i3[c];
+      for (int j = 0; j < cs.dim; ++j) col_right[c0 + cs.off + j] = b0 + j + m4 * i3;
+    }
+  }
+  return DMRG2D_OK;
+}
+
 int sec_read_error(const dmrg2d_ops* ops, int* code) {
   *code = 0;
   const SecState* S = (const SecState*)ops->sec;

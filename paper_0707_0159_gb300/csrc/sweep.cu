@@ -54,6 +54,27 @@ struct Block {
   std::vector<Mat> edge;
   int m_prev = 0;
   std::shared_ptr<DBuf> U;
+  int cols = 1;                 // lattice columns in the block
+  std::vector<int32_t> qn;      // sectors: N_up of each state, equal labels contiguous
+};
+
+struct IBuf {  // device int64 / int32 arrays for the sector maps
+  void* p = nullptr;
+  ~IBuf() {
+    if (p) cudaFree(p);
+  }
+  template <typename T>
+  int upload(const std::vector<T>& h, cudaStream_t s) {
+    if (p) cudaFree(p);
+    p = nullptr;
+    if (h.empty()) return DMRG2D_OK;
+    if (cudaMalloc(&p, h.size() * sizeof(T)) != cudaSuccess) {
+      p = nullptr;
+      return set_error(DMRG2D_ENOMEM, "sweep: cudaMalloc failed (maps)");
+    }
+    D2_CUDA(cudaMemcpyAsync(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    return DMRG2D_OK;
+  }
 };
 
 struct DBuf {
@@ -99,6 +120,42 @@ __global__ void k_take_leading(const double* __restrict__ Q, int64_t n, int k,
     const int64_t j = i / n, r = i - j * n;
     U[i] = Q[r + (k - 1 - j) * n];
   }
+}
+
+// One matrix V_q of a sector-restricted vector against the dense V (ldd rows):
+// to_packed: xq[r + qld c] = Vd[rowL[r] + ldd colR[c]] (0 on padding rows); else the reverse.
+__global__ void k_pack(double* __restrict__ Vd, int64_t ldd, double* __restrict__ xq, int qld,
+                       int qcols, const int64_t* __restrict__ rowL,
+                       const int64_t* __restrict__ colR, int to_packed) {
+  const int64_t total = (int64_t)qld * qcols;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(i % qld), c = (int)(i / qld);
+    const int64_t row = rowL[r];
+    if (to_packed)
+      xq[i] = row >= 0 ? Vd[row + ldd * colR[c]] : 0.0;
+    else if (row >= 0)
+      Vd[row + ldd * colR[c]] = xq[i];
+  }
+}
+
+// G (nr x cols) = the rows rows[0..nr) of X (ldx rows)
+__global__ void k_gather_rows(const double* __restrict__ X, int ldx, int cols,
+                              const int* __restrict__ rows, int nr, double* __restrict__ G) {
+  const int64_t total = (int64_t)nr * cols;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(i % nr), c = (int)(i / nr);
+    G[i] = X[rows[r] + (int64_t)ldx * c];
+  }
+}
+
+// U[idx[i], col] = Q[i + ldq * qcol] for i < len
+__global__ void k_scatter_col(const double* __restrict__ Q, int ldq, int qcol, int len,
+                              const int64_t* __restrict__ idx, double* __restrict__ U, int64_t ldu,
+                              int col) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < len; i += gridDim.x * blockDim.x)
+    U[idx[i] + ldu * col] = Q[i + (int64_t)ldq * qcol];
 }
 
 // xorshift64* stream for the start vectors (values in (-1, 1))
@@ -181,12 +238,28 @@ class Sweeper {
   }
   Block column_block() const {
     Block b;
-    b.m = col_.d;
-    b.H = col_.H;
+    const int d = col_.d;
+    b.m = d;
+    // with sectors the block's states must be grouped by label: order by N_up (stable)
+    std::vector<int> perm(d);
+    for (int i = 0; i < d; ++i) perm[i] = i;
+    if (o_.use_sectors)
+      std::stable_sort(perm.begin(), perm.end(), [](int a, int c) {
+        return __builtin_popcount((unsigned)a) < __builtin_popcount((unsigned)c);
+      });
+    auto permuted = [&](const Mat& A) {
+      Mat P((size_t)d * d);
+      for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) P[(size_t)i * d + j] = A[(size_t)perm[i] * d + perm[j]];
+      return P;
+    };
+    b.H = permuted(col_.H);
     for (size_t y = 0; y < col_.sz.size(); ++y) {
-      b.edge.push_back(col_.sz[y]);
-      b.edge.push_back(col_.sp[y]);
+      b.edge.push_back(permuted(col_.sz[y]));
+      b.edge.push_back(permuted(col_.sp[y]));
     }
+    if (o_.use_sectors)
+      for (int i = 0; i < d; ++i) b.qn.push_back(__builtin_popcount((unsigned)perm[i]));
     return b;
   }
 
@@ -208,6 +281,152 @@ class Sweeper {
     return DMRG2D_OK;
   }
 
+  // Full eigendecomposition (ascending) of the symmetric n x n matrix A (lower) in place;
+  // eigenvalues to the host.
+  int eigh_all(double* A, int n, Mat* w_host) {
+    DBuf w, work;
+    D2_TRY(w.alloc((size_t)n));
+    int lwork = 0;
+    D2_SOLV(cusolverDnDsyevd_bufferSize(libs_.sv, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
+                                        n, A, n, w.p, &lwork));
+    D2_TRY(work.alloc((size_t)std::max(lwork, 1)));
+    IBuf info;
+    D2_TRY(info.upload(std::vector<int>{0}, strm_));
+    D2_SOLV(cusolverDnDsyevd(libs_.sv, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, A, n,
+                             w.p, work.p, lwork, (int*)info.p));
+    int hinfo = 0;
+    w_host->resize((size_t)n);
+    D2_CUDA(cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, strm_));
+    D2_CUDA(cudaMemcpyAsync(w_host->data(), w.p, n * sizeof(double), cudaMemcpyDeviceToHost, strm_));
+    D2_CUDA(cudaStreamSynchronize(strm_));
+    if (hinfo != 0) return set_error(DMRG2D_ECUDA, "sweep: dsyevd info %d", hinfo);
+    return DMRG2D_OK;
+  }
+
+  // Dense superblock: rho = V V^T (grow_left) or V^T V of the dense V = x ((n x other) or
+  // (other x n)), its k leading eigenvectors (dsyevdx, selected by index) into U, largest
+  // first; *kept = their eigenvalue sum.
+  int dmd_dense(const double* x, bool grow_left, int64_t n, int64_t other, int k, DBuf& U,
+                double* kept) {
+    DBuf rho;
+    D2_TRY(rho.alloc((size_t)(n * n)));
+    const double one = 1.0, zero = 0.0;
+    D2_BLAS(cublasDsyrk(libs_.bl, CUBLAS_FILL_MODE_LOWER, grow_left ? CUBLAS_OP_N : CUBLAS_OP_T,
+                        (int)n, (int)other, &one, x, grow_left ? (int)n : (int)other, &zero,
+                        rho.p, (int)n));
+    DBuf w, work;
+    D2_TRY(w.alloc((size_t)n));
+    int lwork = 0, meig = 0;
+    const int il = (int)n - k + 1, iu = (int)n;  // 1-based eigenvalue indices
+    D2_SOLV(cusolverDnDsyevdx_bufferSize(libs_.sv, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I,
+                                         CUBLAS_FILL_MODE_LOWER, (int)n, rho.p, (int)n, 0.0, 0.0,
+                                         il, iu, &meig, w.p, &lwork));
+    D2_TRY(work.alloc((size_t)std::max(lwork, 1)));
+    IBuf info;
+    D2_TRY(info.upload(std::vector<int>{0}, strm_));
+    D2_SOLV(cusolverDnDsyevdx(libs_.sv, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I,
+                              CUBLAS_FILL_MODE_LOWER, (int)n, rho.p, (int)n, 0.0, 0.0, il, iu,
+                              &meig, w.p, work.p, lwork, (int*)info.p));
+    int hinfo = 0;
+    Mat hw((size_t)k);
+    D2_CUDA(cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, strm_));
+    D2_CUDA(cudaMemcpyAsync(hw.data(), w.p, k * sizeof(double), cudaMemcpyDeviceToHost, strm_));
+    D2_CUDA(cudaStreamSynchronize(strm_));
+    if (hinfo != 0 || meig != k)
+      return set_error(DMRG2D_ECUDA, "sweep: dsyevdx info %d, %d of %d eigenpairs", hinfo, meig, k);
+    *kept = 0.0;
+    for (int j = 0; j < k; ++j) *kept += hw[(size_t)j];
+    k_take_leading<<<1024, 256, 0, strm_>>>(rho.p, n, k, U.p);
+    D2_CUDA(cudaGetLastError());
+    return DMRG2D_OK;
+  }
+
+  // Sector-restricted superblock: the density matrix is block diagonal in the growing
+  // half's label.  Left: for each V_q, rho_q = G G^T with G its rows without padding;
+  // right: rho_q = V_q^T V_q.  All eigenpairs of every rho_q, the k largest eigenvalues
+  // over all sectors are kept; the new block's states are grouped by label (ascending)
+  // and, within a label, by decreasing weight.  U (n x k, zero outside each state's
+  // sector) gets the eigenvectors at their dense indices i1 + m1 i2 (or i4 + m4 i3).
+  int dmd_sectors(const double* xpk, bool grow_left, const Block& Lb, const Block& Rb,
+                  const std::vector<long long>& qbase, const std::vector<int>& qld,
+                  const std::vector<int>& qcols, const std::vector<int64_t>& rowL,
+                  const std::vector<int64_t>& colR, int* kio, DBuf& U, double* kept,
+                  std::vector<int32_t>* labels) {
+    const int nQ = (int)qld.size();
+    const double one = 1.0, zero = 0.0;
+    std::vector<std::shared_ptr<DBuf>> vecs(nQ);
+    std::vector<std::shared_ptr<IBuf>> idx(nQ);
+    std::vector<int> dim(nQ), lab(nQ);
+    struct Cand {
+      double w;
+      int q, j;
+    };
+    std::vector<Cand> cand;
+    int64_t r0 = 0, c0 = 0;
+    for (int q = 0; q < nQ; ++q) {
+      std::vector<int64_t> dense;
+      const double* xq = xpk + qbase[q];
+      vecs[q] = std::make_shared<DBuf>();
+      if (grow_left) {
+        std::vector<int> rows;
+        for (int r = 0; r < qld[q]; ++r)
+          if (rowL[r0 + r] >= 0) {
+            rows.push_back(r);
+            dense.push_back(rowL[r0 + r]);
+          }
+        const int nr = (int)rows.size();
+        IBuf d_rows;
+        D2_TRY(d_rows.upload(rows, strm_));
+        DBuf G;
+        D2_TRY(G.alloc((size_t)nr * qcols[q]));
+        k_gather_rows<<<512, 256, 0, strm_>>>(xq, qld[q], qcols[q], (const int*)d_rows.p, nr, G.p);
+        D2_CUDA(cudaGetLastError());
+        D2_TRY(vecs[q]->alloc((size_t)nr * nr));
+        D2_BLAS(cublasDsyrk(libs_.bl, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, nr, qcols[q], &one, G.p,
+                            nr, &zero, vecs[q]->p, nr));
+        dim[q] = nr;
+        const int64_t e = dense[0];  // label of the enlarged-left state i1 + m1 i2
+        lab[q] = Lb.qn[(size_t)(e % Lb.m)] + __builtin_popcount((unsigned)(e / Lb.m));
+      } else {
+        for (int c = 0; c < qcols[q]; ++c) dense.push_back(colR[c0 + c]);
+        D2_TRY(vecs[q]->alloc((size_t)qcols[q] * qcols[q]));
+        D2_BLAS(cublasDsyrk(libs_.bl, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, qcols[q], qld[q], &one,
+                            xq, qld[q], &zero, vecs[q]->p, qcols[q]));
+        dim[q] = qcols[q];
+        const int64_t e = dense[0];  // label of the enlarged-right state i4 + m4 i3
+        lab[q] = Rb.qn[(size_t)(e % Rb.m)] + __builtin_popcount((unsigned)(e / Rb.m));
+      }
+      idx[q] = std::make_shared<IBuf>();
+      D2_TRY(idx[q]->upload(dense, strm_));
+      Mat w;
+      D2_TRY(eigh_all(vecs[q]->p, dim[q], &w));
+      for (int j = 0; j < dim[q]; ++j) cand.push_back({w[(size_t)j], q, j});
+      r0 += qld[q];
+      c0 += qcols[q];
+    }
+    std::stable_sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& b) { return a.w > b.w; });
+    const int k = std::min(*kio, (int)cand.size());  // states of the target-compatible sectors
+    *kio = k;
+    std::vector<Cand> keep(cand.begin(), cand.begin() + k);
+    std::stable_sort(keep.begin(), keep.end(), [&](const Cand& a, const Cand& b) {
+      return lab[a.q] < lab[b.q];  // group by label; stable keeps decreasing weight
+    });
+    const int64_t n = (int64_t)(grow_left ? Lb.m : Rb.m) * col_.d;
+    D2_TRY(U.alloc((size_t)(n * k)));
+    D2_CUDA(cudaMemsetAsync(U.p, 0, (size_t)n * k * sizeof(double), strm_));
+    *kept = 0.0;
+    labels->clear();
+    for (int c = 0; c < k; ++c) {
+      const Cand& cd = keep[(size_t)c];
+      k_scatter_col<<<64, 256, 0, strm_>>>(vecs[cd.q]->p, dim[cd.q], cd.j, dim[cd.q],
+                                           (const int64_t*)idx[cd.q]->p, U.p, n, c);
+      *kept += cd.w;
+      labels->push_back(lab[cd.q]);
+    }
+    D2_CUDA(cudaGetLastError());
+    return DMRG2D_OK;
+  }
+
   // One DMRG step on block 1 = L, block 4 = R; grows L (grow_left) or R into *out.
   int step(const Block& Lb, const Block& Rb, bool grow_left, int m_keep, int l, int sweep,
            Block* out, const DBuf* guess) {
@@ -215,11 +434,16 @@ class Sweeper {
     std::vector<const double*> le, re;
     for (auto& e : Lb.edge) le.push_back(e.data());
     for (auto& e : Rb.edge) re.push_back(e.data());
-    dmrg2d_block bl{Lb.m, Lb.H.data(), (int)le.size(), le.data(), nullptr, nullptr};
-    dmrg2d_block br{Rb.m, Rb.H.data(), (int)re.size(), re.data(), nullptr, nullptr};
+    const bool sec = o_.use_sectors != 0;
+    dmrg2d_block bl{Lb.m, Lb.H.data(), (int)le.size(), le.data(), nullptr,
+                    sec ? Lb.qn.data() : nullptr};
+    dmrg2d_block br{Rb.m, Rb.H.data(), (int)re.size(), re.data(), nullptr,
+                    sec ? Rb.qn.data() : nullptr};
+    // S^z_tot = 0: half the superblock's sites up
+    const int32_t target = M_.n_legs * (Lb.cols + Rb.cols + 2) / 2;
     dmrg2d_ops* ops = nullptr;
     auto tb = std::chrono::steady_clock::now();
-    D2_TRY(dmrg2d_build_ops(&M_, &bl, &br, nullptr, &ops, strm_));
+    D2_TRY(dmrg2d_build_ops(&M_, &bl, &br, sec ? &target : nullptr, &ops, strm_));
     build_seconds += since(tb);
     struct FreeOps {
       dmrg2d_ops* p;
@@ -228,19 +452,52 @@ class Sweeper {
     dmrg2d_ops_info info;
     D2_TRY(dmrg2d_ops_get_info(ops, &info));
     const int64_t nv = info.n_vec;
-    auto xp = std::make_shared<DBuf>();
-    DBuf& x = *xp;
-    if (guess && guess->n == (size_t)nv) {  // the previous ground state, in this basis
+    const int d = col_.d;
+    const int64_t nL = (int64_t)Lb.m * d, nR = (int64_t)d * Rb.m, nd = nL * nR;  // dense V
+    // sector layout of the packed vector (rows/columns of each V_q in the dense V)
+    std::vector<long long> qbase;
+    std::vector<int> qld, qcols;
+    std::vector<int64_t> rowL, colR;
+    IBuf d_rowL, d_colR;
+    if (sec) {
+      D2_TRY(sec_layout(ops, qbase, qld, qcols, rowL, colR));
+      D2_TRY(d_rowL.upload(rowL, strm_));
+      D2_TRY(d_colR.upload(colR, strm_));
+    }
+    auto pack = [&](double* Vd, double* xpk, int to_packed) -> int {
+      int64_t r0 = 0, c0 = 0;
+      for (size_t q = 0; q < qld.size(); ++q) {
+        k_pack<<<512, 256, 0, strm_>>>(Vd, nL, xpk + qbase[q], qld[q], qcols[q],
+                                       (const int64_t*)d_rowL.p + r0, (const int64_t*)d_colR.p + c0,
+                                       to_packed);
+        r0 += qld[q];
+        c0 += qcols[q];
+      }
+      D2_CUDA(cudaGetLastError());
+      return DMRG2D_OK;
+    };
+    DBuf x;
+    if (guess && guess->n == (size_t)nd) {  // the previous ground state, in this basis
       D2_TRY(x.alloc((size_t)nv));
-      D2_CUDA(cudaMemcpyAsync(x.p, guess->p, nv * sizeof(double), cudaMemcpyDeviceToDevice,
-                              strm_));
+      if (sec)
+        D2_TRY(pack(guess->p, x.p, 1));
+      else
+        D2_CUDA(cudaMemcpyAsync(x.p, guess->p, nv * sizeof(double), cudaMemcpyDeviceToDevice,
+                                strm_));
     } else {
       Mat x0((size_t)nv);
       for (auto& v : x0) v = rng_.next();
+      if (sec) {  // zero on the padding rows
+        int64_t r0 = 0;
+        for (size_t q = 0; q < qld.size(); ++q) {
+          for (int c = 0; c < qcols[q]; ++c)
+            for (int r = 0; r < qld[q]; ++r)
+              if (rowL[r0 + r] < 0) x0[(size_t)(qbase[q] + r + (int64_t)qld[q] * c)] = 0.0;
+          r0 += qld[q];
+        }
+      }
       D2_TRY(x.upload(x0, strm_));
     }
-    last_x_ = xp;
-    last_nv_ = nv;
     dmrg2d_solver_opts so;
     dmrg2d_default_solver_opts(&so);
     so.tol = o_.tol;
@@ -262,61 +519,44 @@ class Sweeper {
     solve_seconds += since(t0);
     if (st != DMRG2D_OK && st != DMRG2D_ENOCONV) return st;
     const auto td = std::chrono::steady_clock::now();
-    // ---- DMF: reduced density matrix of the growing half --------------------------------
-    const int mb = grow_left ? Lb.m : Rb.m;  // block that grows
-    const int d = col_.d;
-    const int64_t n = (int64_t)mb * d;
-    const int64_t other = nv / n;
-    DBuf rho;
-    D2_TRY(rho.alloc((size_t)(n * n)));
-    const double one = 1.0, zero = 0.0;
-    // V: (m1 d) x (d m4) column-major view of x; rho_L = V V^T, rho_R = V^T V (lower)
-    D2_BLAS(cublasDsyrk(libs_.bl, CUBLAS_FILL_MODE_LOWER, grow_left ? CUBLAS_OP_N : CUBLAS_OP_T,
-                        (int)n, (int)other, &one, x.p, grow_left ? (int)n : (int)other, &zero,
-                        rho.p, (int)n));
-    // ---- DMD: the k leading eigenpairs (selected by index, ascending order) ---------------
-    const int k = (int)std::min<int64_t>(m_keep, n);
+    // the ground state as the dense V ((m1 d) x (d m4)) for the next step's start vector
+    auto xd = std::make_shared<DBuf>();
+    D2_TRY(xd->alloc((size_t)nd));
+    if (sec) {
+      D2_CUDA(cudaMemsetAsync(xd->p, 0, nd * sizeof(double), strm_));
+      D2_TRY(pack(xd->p, x.p, 0));
+    } else {
+      D2_CUDA(cudaMemcpyAsync(xd->p, x.p, nd * sizeof(double), cudaMemcpyDeviceToDevice, strm_));
+    }
+    last_x_ = xd;
+    last_nv_ = nd;
     double norm2 = 0.0;  // trace of rho = |x|^2
     D2_BLAS(cublasDdot(libs_.bl, (int)nv, x.p, 1, x.p, 1, &norm2));
-    DBuf w, work;
-    D2_TRY(w.alloc((size_t)n));
-    int lwork = 0, meig = 0;
-    const int il = (int)n - k + 1, iu = (int)n;  // 1-based eigenvalue indices
-    D2_SOLV(cusolverDnDsyevdx_bufferSize(libs_.sv, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I,
-                                         CUBLAS_FILL_MODE_LOWER, (int)n, rho.p, (int)n, 0.0, 0.0,
-                                         il, iu, &meig, w.p, &lwork));
-    D2_TRY(work.alloc((size_t)std::max(lwork, 1)));
-    int* dinfo = nullptr;
-    D2_CUDA(cudaMalloc((void**)&dinfo, sizeof(int)));
-    struct FreeInt {
-      int* p;
-      ~FreeInt() { cudaFree(p); }
-    } fi{dinfo};
-    D2_SOLV(cusolverDnDsyevdx(libs_.sv, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I,
-                              CUBLAS_FILL_MODE_LOWER, (int)n, rho.p, (int)n, 0.0, 0.0, il, iu,
-                              &meig, w.p, work.p, lwork, dinfo));
-    int hinfo = 0;
-    Mat hw((size_t)k);
-    D2_CUDA(cudaMemcpyAsync(&hinfo, dinfo, sizeof(int), cudaMemcpyDeviceToHost, strm_));
-    D2_CUDA(cudaMemcpyAsync(hw.data(), w.p, k * sizeof(double), cudaMemcpyDeviceToHost, strm_));
-    D2_CUDA(cudaStreamSynchronize(strm_));
-    dm_seconds += since(td);
-    if (hinfo != 0 || meig != k)
-      return set_error(DMRG2D_ECUDA, "sweep: dsyevdx info %d, %d of %d eigenpairs", hinfo, meig, k);
+    // ---- DMF + DMD: k leading eigenvectors of the growing half's density matrix ----------
+    const int mb = grow_left ? Lb.m : Rb.m;  // block that grows
+    const int64_t n = (int64_t)mb * d;
+    int k = (int)std::min<int64_t>(m_keep, n);
+    auto Up = std::make_shared<DBuf>();
+    DBuf& U = *Up;
+    std::vector<int32_t> labels;
     double kept = 0.0;
-    for (int j = 0; j < k; ++j) kept += hw[(size_t)j];
+    if (sec) {  // k may shrink to the states the target sector leaves
+      D2_TRY(dmd_sectors(x.p, grow_left, Lb, Rb, qbase, qld, qcols, rowL, colR, &k, U, &kept,
+                         &labels));
+    } else {
+      D2_TRY(U.alloc((size_t)(n * k)));
+      D2_TRY(dmd_dense(x.p, grow_left, n, nd / n, k, U, &kept));
+    }
     kept /= norm2;
+    dm_seconds += since(td);
     record(energy, 1.0 - kept, l, sweep, stats.iters);
     if (!out) return DMRG2D_OK;
     // ---- renormalisation: U^T O U for H_enl and the new boundary operators ----------------
     const auto tr = std::chrono::steady_clock::now();
-    auto Up = std::make_shared<DBuf>();
-    DBuf &U = *Up, HU, T;
-    D2_TRY(U.alloc((size_t)(n * k)));
+    const double one = 1.0, zero = 0.0;
+    DBuf HU, T;
     D2_TRY(HU.alloc((size_t)(n * k)));
     D2_TRY(T.alloc((size_t)(n * k)));
-    k_take_leading<<<1024, 256, 0, strm_>>>(rho.p, n, k, U.p);
-    D2_CUDA(cudaGetLastError());
     const Block& B = grow_left ? Lb : Rb;
     DBuf dHB;
     D2_TRY(dHB.upload(B.H, strm_));
@@ -358,6 +598,8 @@ class Sweeper {
     out->m = k;
     out->m_prev = mb;
     out->U = Up;
+    out->cols = (grow_left ? Lb.cols : Rb.cols) + 1;
+    out->qn = labels;
     D2_TRY(project(HU.p, &out->H, true));
     out->edge.assign(2 * col_.sz.size(), Mat());
     for (size_t y = 0; y < col_.sz.size(); ++y) {

@@ -42,7 +42,8 @@ class Block(C.Structure):
 class SweepOpts(C.Structure):
     _fields_ = [("n_columns", C.c_int), ("m_warmup", C.c_int), ("n_sweeps", C.c_int),
                 ("m_sweep", C.POINTER(C.c_int)), ("precision", C.c_int), ("tol", C.c_double),
-                ("max_iter", C.c_int), ("krylov_dim", C.c_int), ("seed", C.c_uint64)]
+                ("max_iter", C.c_int), ("krylov_dim", C.c_int), ("seed", C.c_uint64),
+                ("use_sectors", C.c_int)]
 
 
 class SweepReport(C.Structure):
@@ -467,14 +468,14 @@ def mlp_make_batch(ops: Ops, x_k, r_k, theta, x_final, D, idx, X, w, T, stream=N
 
 
 def sweep(model: dict, n_columns: int, m_warmup: int, m_sweeps, precision=FP64, tol=1e-10,
-          max_iter=300, krylov_dim=100, seed=1, cap=4096, stream=None) -> dict:
+          max_iter=300, krylov_dim=100, seed=1, cap=4096, sectors=False, stream=None) -> dict:
     """dmrg2d_sweep: warm-up plus one finite sweep per entry of m_sweeps on an n-leg
     Heisenberg ladder of n_columns columns.  Returns the per-step energy, truncation
     error, block-1 length and sweep index (-1 = warm-up), and the timings."""
     precision = PRECISION.get(precision, precision)
     ms = (C.c_int * max(1, len(m_sweeps)))(*[int(m) for m in m_sweeps])
     opts = SweepOpts(int(n_columns), int(m_warmup), len(m_sweeps), ms, int(precision), float(tol),
-                     int(max_iter), int(krylov_dim), int(seed))
+                     int(max_iter), int(krylov_dim), int(seed), int(bool(sectors)))
     e, t = (C.c_double * cap)(), (C.c_double * cap)()
     ll, sw, it = (C.c_int * cap)(), (C.c_int * cap)(), (C.c_int * cap)()
     rep = SweepReport(cap, 0, e, t, ll, sw, it, 0.0, 0.0, 0.0, 0.0, 0.0)

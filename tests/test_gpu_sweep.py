@@ -71,3 +71,19 @@ def test_mixed_precision_sweep_matches_fp64():
     assert mix["l"] == ref["l"]
     # same kept subspaces as long as the density-matrix cuts are clean; energies agree
     assert np.allclose(mix["energy"], ref["energy"], rtol=1e-8, atol=0)
+
+
+@pytest.mark.parametrize("n,m,L", [(2, 8, 6), (3, 16, 6), (2, 64, 6)])
+def test_sector_sweep_matches_dense_sweep(n, m, L):
+    """S^z_tot = 0 sector-restricted sweep (blocks labelled by N_up, density matrices per
+    sector) against the dense sweep: same energies and truncation errors wherever the
+    density-matrix cut has a gap (checked on the oracle), and exact when untruncated."""
+    mdl = model(n)
+    if m < 64:
+        assert min(odmrg.dmrg(mdl, L, m_warmup=m, m_sweeps=[m, m])["gap"]) > 1e-7
+    kw = dict(m_warmup=m, m_sweeps=[m, m], precision="fp64", tol=1e-12, max_iter=800)
+    dense = dmrg2d.sweep(mdl, L, **kw)
+    sec = dmrg2d.sweep(mdl, L, sectors=True, **kw)
+    assert sec["l"] == dense["l"] and sec["sweep"] == dense["sweep"]
+    assert np.allclose(sec["energy"], dense["energy"], rtol=1e-10, atol=0)
+    assert np.allclose(sec["trunc"], dense["trunc"], rtol=1e-5, atol=1e-12)
