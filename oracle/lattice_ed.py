@@ -57,6 +57,33 @@ def heisenberg_spectrum(n_legs: int, L: int, **kw) -> np.ndarray:
     return np.linalg.eigvalsh(heisenberg_matrix(n_legs, L, **kw))
 
 
+def spin_dot(N: int, a: int, b: int) -> np.ndarray:
+    """S_a . S_b on N spin-1/2 sites (bit s of a state = spin up at site s)."""
+    dim = 1 << N
+    O = np.zeros((dim, dim))
+    for st in range(dim):
+        ba, bb = (st >> a) & 1, (st >> b) & 1
+        if a == b:
+            O[st, st] = 0.75
+            continue
+        O[st, st] += 0.25 if ba == bb else -0.25
+        if ba != bb:
+            O[st ^ ((1 << a) | (1 << b)), st] += 0.5
+    return O
+
+
+def heisenberg_ground_correlations(n_legs: int, L: int, J_leg=1.0, J_rung=1.0):
+    """Ground energy, state and a function (a, b) -> <S_a . S_b> of the open ladder
+    (site index x * n_legs + y), and <S_tot^2> = sum_ab <S_a . S_b>."""
+    H = heisenberg_matrix(n_legs, L, J_leg=J_leg, J_rung=J_rung)
+    w, v = np.linalg.eigh(H)
+    psi = v[:, 0]
+    N = n_legs * L
+    corr = lambda a, b: float(psi @ spin_dot(N, a, b) @ psi)   # noqa: E731
+    s2 = sum(corr(a, b) for a in range(N) for b in range(N))
+    return float(w[0]), psi, corr, s2
+
+
 def _sign_below(state: int, mode: int) -> int:
     return -1 if bin(state & ((1 << mode) - 1)).count("1") % 2 else 1
 

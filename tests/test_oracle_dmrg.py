@@ -66,3 +66,35 @@ def test_keep_states_weights():
     assert trunc == pytest.approx(1.0 - full[:4].sum())
     assert np.allclose(U.T @ U, np.eye(4), atol=1e-12)
     assert gap == pytest.approx(full[3] - full[4])
+
+
+def test_ed_bond_energies_and_lieb_mattis():
+    # the bond expectations reproduce the energy; the ground state is a singlet
+    n, L = 2, 4
+    mdl = ladder_model()
+    e, psi, corr, s2 = lattice_ed.heisenberg_ground_correlations(n, L, J_leg=1.0, J_rung=0.8)
+    total = 0.0
+    for a, b, kind in lattice_ed.ladder_bonds(n, L):
+        total += (mdl["J_leg"] if kind == "leg" else mdl["J_rung"]) * corr(a, b)
+    assert total == pytest.approx(e, abs=1e-12)
+    assert abs(s2) <= 1e-10
+    assert corr(0, 0) == pytest.approx(0.75)
+
+
+def test_untruncated_observables_equal_ed():
+    """Leg bonds between the central columns, rung bonds of column 2 and <S^2> of every
+    finite-sweep step of an untruncated 2 x 6 sweep equal the ED values of those bonds."""
+    n, L = 2, 6
+    mdl = ladder_model()
+    out = dmrg.dmrg(mdl, L, m_warmup=64, m_sweeps=[64])
+    _, _, corr, s2 = lattice_ed.heisenberg_ground_correlations(n, L, J_leg=1.0, J_rung=0.8)
+    assert abs(s2) <= 1e-10
+    for k, sw in enumerate(out["sweep"]):
+        if sw < 0:
+            continue
+        x2 = out["l"][k]                        # lattice column of column 2 (0-based)
+        for y in range(n):
+            assert out["leg"][k][y] == pytest.approx(corr(x2 * n + y, (x2 + 1) * n + y), abs=1e-9)
+        for y in range(n - 1):
+            assert out["rung"][k][y] == pytest.approx(corr(x2 * n + y, x2 * n + y + 1), abs=1e-9)
+        assert abs(out["s2"][k]) <= 1e-8
