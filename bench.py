@@ -381,13 +381,23 @@ def dmrg_sweep_run(args):
                        sectors=True)
     e, sw = out["energy"], out["sweep"]
     per = {str(s): min(e[i] for i in range(len(e)) if sw[i] == s) for s in sorted(set(sw))}
+    last = max(sw)
+    # leg-bond energies between lattice columns x and x + 1 along the last sweep (the
+    # paper's h(x, y) profile), and <S_tot^2> at the end of each sweep (Lieb-Mattis)
+    profile = {}
+    for i in range(len(e)):
+        if sw[i] == last:
+            profile[str(out["l"][i])] = out["leg_bond"][i]
+    s2 = {str(sw[i]): out["s2"][i] for i in range(len(e)) if out["s2"][i] == out["s2"][i]}
     return {"lattice": "4x12 open Heisenberg ladder, J=1, S^z_tot = 0 sector",
             "m_warmup": args.sweep_m_warmup, "m_sweeps": ms,
             "precision": args.precision, "steps": out["n_steps"],
             "energy_min_per_sweep": per, "energy_last": e[-1], "max_trunc": max(out["trunc"]),
             "solver_steps": sum(out["iters"]), "seconds": out["seconds"],
             "solve_seconds": out["solve_seconds"], "build_seconds": out["build_seconds"],
-            "density_matrix_seconds": out["dm_seconds"], "renorm_seconds": out["renorm_seconds"]}
+            "density_matrix_seconds": out["dm_seconds"], "renorm_seconds": out["renorm_seconds"],
+            "observables_seconds": out["obs_seconds"], "s2_per_sweep": s2,
+            "leg_bond_profile_last_sweep": profile}
 
 
 def time_to_energy(ops, n, prec, args, dev):

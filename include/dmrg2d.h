@@ -391,11 +391,22 @@ typedef struct dmrg2d_sweep_report {
   int* l;
   int* sweep;
   int* iters;          /* ground-state solver steps (Lanczos or inner low-precision)  */
+  /* observables of each step's superblock ground state (the paper's bond energies):
+   * leg_bond[step * n_legs + y] = <S_(2,y) . S_(3,y)> between the two central columns,
+   * rung_bond[step * max(n_legs - 1, 1) + y] = <S_(2,y) . S_(2,y+1)> in column 2,
+   * s2[step] = <S_tot^2> at the last step of each sweep (back in the middle; also the
+   * single warm-up step of a 4-column lattice) — the Lieb-Mattis check: 0 for the
+   * ladder's ground state — NaN elsewhere.  Column 2 is
+   * lattice column l (0-based).  Any of the three may be NULL. */
+  double* leg_bond;
+  double* rung_bond;
+  double* s2;
   double seconds;      /* wall time of the call, of which:                            */
   double solve_seconds;/*   ground-state solves (dmrg2d_lanczos_ground)              */
   double build_seconds;/*   superblock operator assembly (dmrg2d_build_ops)          */
   double dm_seconds;   /*   density matrix and its eigenvectors                      */
   double renorm_seconds;/*  new block operators U^T O U and their copy to the host   */
+  double obs_seconds;  /*   observables                                              */
 } dmrg2d_sweep_report;
 
 int dmrg2d_sweep(const dmrg2d_model* model, const dmrg2d_sweep_opts* opts,

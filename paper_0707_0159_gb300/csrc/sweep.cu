@@ -56,6 +56,7 @@ struct Block {
   std::shared_ptr<DBuf> U;
   int cols = 1;                 // lattice columns in the block
   std::vector<int32_t> qn;      // sectors: N_up of each state, equal labels contiguous
+  Mat Sz_tot, Sp_tot;           // the block's total S^z and S^+ (for <S_tot^2>)
 };
 
 struct IBuf {  // device int64 / int32 arrays for the sector maps
@@ -185,6 +186,40 @@ class Sweeper {
     D2_SOLV(cusolverDnSetStream(libs_.sv, strm_));
     // column operators on the device (row-major buffers)
     D2_TRY(dH_col_.upload(col_.H, strm_));
+    const int dd = col_.d, nl = (int)col_.sz.size();
+    col_Sz_tot_.assign((size_t)dd * dd, 0.0);
+    col_Sp_tot_.assign((size_t)dd * dd, 0.0);
+    for (int y = 0; y < nl; ++y)
+      for (size_t e = 0; e < col_Sz_tot_.size(); ++e) {
+        col_Sz_tot_[e] += col_.sz[y][e];
+        col_Sp_tot_[e] += col_.sp[y][e];
+      }
+    D2_TRY(dSz_tot_.upload(col_Sz_tot_, strm_));
+    D2_TRY(dSp_tot_.upload(col_Sp_tot_, strm_));
+    // rung bond S_y . S_{y+1} of one column (row-major d x d)
+    auto mm = [dd](const Mat& a, const Mat& b) {
+      Mat c((size_t)dd * dd, 0.0);
+      for (int i = 0; i < dd; ++i)
+        for (int k = 0; k < dd; ++k) {
+          const double x = a[(size_t)i * dd + k];
+          if (x != 0.0)
+            for (int j = 0; j < dd; ++j) c[(size_t)i * dd + j] += x * b[(size_t)k * dd + j];
+        }
+      return c;
+    };
+    auto tr = [dd](const Mat& a) {
+      Mat t((size_t)dd * dd);
+      for (int i = 0; i < dd; ++i)
+        for (int j = 0; j < dd; ++j) t[(size_t)j * dd + i] = a[(size_t)i * dd + j];
+      return t;
+    };
+    drung_.resize(std::max(nl - 1, 0));
+    for (int y = 0; y + 1 < nl; ++y) {
+      Mat b = mm(col_.sz[y], col_.sz[y + 1]);
+      const Mat pm = mm(col_.sp[y], tr(col_.sp[y + 1])), mp = mm(tr(col_.sp[y]), col_.sp[y + 1]);
+      for (size_t e = 0; e < b.size(); ++e) b[e] += 0.5 * (pm[e] + mp[e]);
+      D2_TRY(drung_[y].upload(b, strm_));
+    }
     dsz_.resize(col_.sz.size());
     dsp_.resize(col_.sp.size());
     for (size_t y = 0; y < col_.sz.size(); ++y) {
@@ -230,7 +265,8 @@ class Sweeper {
     return DMRG2D_OK;
   }
 
-  double solve_seconds = 0.0, build_seconds = 0.0, dm_seconds = 0.0, renorm_seconds = 0.0;
+  double solve_seconds = 0.0, build_seconds = 0.0, dm_seconds = 0.0, renorm_seconds = 0.0,
+         obs_seconds = 0.0;
 
  private:
   static double since(std::chrono::steady_clock::time_point t0) {
@@ -260,6 +296,8 @@ class Sweeper {
     }
     if (o_.use_sectors)
       for (int i = 0; i < d; ++i) b.qn.push_back(__builtin_popcount((unsigned)perm[i]));
+    b.Sz_tot = permuted(col_Sz_tot_);
+    b.Sp_tot = permuted(col_Sp_tot_);
     return b;
   }
 
@@ -427,6 +465,86 @@ class Sweeper {
     return DMRG2D_OK;
   }
 
+  // ---- observables of the dense V (nL = m1 d rows i1 + m1 i2, nR = d m4 columns
+  // i4 + m4 i3) -------------------------------------------------------------------------
+  // out = alpha V (op(X) (x) 1_m4)^T + beta out: X acts on i3 (column 3); op(X) = X^T if tX
+  int col3(const double* X, bool tX, const double* V, double* out, int64_t nL, int m4,
+           double alpha, double beta) {
+    const int d = col_.d;
+    D2_BLAS(cublasDgemm(libs_.bl, CUBLAS_OP_N, tX ? CUBLAS_OP_T : CUBLAS_OP_N, (int)(nL * m4), d, d,
+                        &alpha, V, (int)(nL * m4), X, d, &beta, out, (int)(nL * m4)));
+    return DMRG2D_OK;
+  }
+  // out = alpha V (1_d (x) Y)^T + beta out: Y (row-major m4 x m4) acts on i4 (block 4)
+  int blk4(const double* Y, const double* V, double* out, int64_t nL, int m4, double alpha,
+           double beta) {
+    D2_BLAS(cublasDgemmStridedBatched(libs_.bl, CUBLAS_OP_N, CUBLAS_OP_N, (int)nL, m4, m4, &alpha,
+                                      V, (int)nL, (long long)nL * m4, Y, m4, 0, &beta, out, (int)nL,
+                                      (long long)nL * m4, col_.d));
+    return DMRG2D_OK;
+  }
+  int dotv(const double* a, const double* b, int64_t n, double* r) {
+    D2_BLAS(cublasDdot(libs_.bl, (int)n, a, 1, b, 1, r));
+    return DMRG2D_OK;
+  }
+  // <S_(2,y) . S_(3,y)> (leg bonds between the central columns), <S_(2,y) . S_(2,y+1)>
+  // (rung bonds of column 2) and, when with_s2, <S_tot^2> = |S+ x|^2 + |Sz x|^2 + <Sz>.
+  int observables(const double* V, const Block& Lb, const Block& Rb, bool with_s2,
+                  std::vector<double>* leg, std::vector<double>* rung, double* s2) {
+    const int m1 = Lb.m, m4 = Rb.m, d = col_.d, nl = (int)col_.sz.size();
+    const int64_t nL = (int64_t)m1 * d, nR = (int64_t)d * m4, nd = nL * nR;
+    DBuf T, T2;
+    D2_TRY(T.alloc((size_t)nd));
+    D2_TRY(T2.alloc((size_t)nd));
+    leg->assign(nl, 0.0);
+    rung->assign(std::max(nl - 1, 0), 0.0);
+    for (int y = 0; y < nl; ++y) {
+      // (A (x) 1) V (B (x) 1)^T for (A, B) = (Sz, Sz), (S+, S-), (S-, S+) with weights 1, 1/2, 1/2
+      const double* sz = dsz_[y].p;
+      const double* sp = dsp_[y].p;
+      struct P { const double* a; bool ta; const double* b; bool tb; double c; };
+      const P terms[3] = {{sz, false, sz, false, 1.0}, {sp, false, sp, true, 0.5},
+                          {sp, true, sp, false, 0.5}};
+      for (const P& t : terms) {
+        D2_TRY(kron_col(t.a, t.ta, V, T.p, m1, (int)nR, 1.0, 0.0));
+        D2_TRY(col3(t.b, t.tb, T.p, T2.p, nL, m4, 1.0, 0.0));
+        double r = 0.0;
+        D2_TRY(dotv(V, T2.p, nd, &r));
+        (*leg)[y] += t.c * r;
+      }
+    }
+    for (int y = 0; y + 1 < nl; ++y) {
+      D2_TRY(kron_col(drung_[y].p, false, V, T.p, m1, (int)nR, 1.0, 0.0));
+      D2_TRY(dotv(V, T.p, nd, &(*rung)[y]));
+    }
+    *s2 = std::nan("");
+    if (with_s2) {
+      DBuf b1z, b1p, b4z, b4p;
+      D2_TRY(b1z.upload(Lb.Sz_tot, strm_));
+      D2_TRY(b1p.upload(Lb.Sp_tot, strm_));
+      D2_TRY(b4z.upload(Rb.Sz_tot, strm_));
+      D2_TRY(b4p.upload(Rb.Sp_tot, strm_));
+      double a = 0.0, b = 0.0, c = 0.0;
+      for (int pass = 0; pass < 2; ++pass) {  // 0: S^+_tot x, 1: S^z_tot x
+        const double* cb = pass ? dSz_tot_.p : dSp_tot_.p;
+        D2_TRY(kron_blk(pass ? b1z.p : b1p.p, false, V, T.p, m1, (int)nR));
+        D2_TRY(kron_col(cb, false, V, T.p, m1, (int)nR, 1.0, 1.0));
+        D2_TRY(col3(cb, false, V, T.p, nL, m4, 1.0, 1.0));
+        D2_TRY(blk4(pass ? b4z.p : b4p.p, V, T.p, nL, m4, 1.0, 1.0));  // V (1 (x) Y4)^T
+        double r = 0.0;
+        D2_TRY(dotv(T.p, T.p, nd, &r));
+        if (pass == 0) {
+          a = r;
+        } else {
+          b = r;
+          D2_TRY(dotv(V, T.p, nd, &c));
+        }
+      }
+      *s2 = a + b + c;
+    }
+    return DMRG2D_OK;
+  }
+
   // One DMRG step on block 1 = L, block 4 = R; grows L (grow_left) or R into *out.
   int step(const Block& Lb, const Block& Rb, bool grow_left, int m_keep, int l, int sweep,
            Block* out, const DBuf* guess) {
@@ -549,7 +667,17 @@ class Sweeper {
     }
     kept /= norm2;
     dm_seconds += since(td);
-    record(energy, 1.0 - kept, l, sweep, stats.iters);
+    // observables of this step's ground state (<S_tot^2> only where no block is grown:
+    // the last step of each sweep)
+    const auto to = std::chrono::steady_clock::now();
+    std::vector<double> leg, rung;
+    double s2 = 0.0;
+    D2_TRY(observables(xd->p, Lb, Rb, out == nullptr, &leg, &rung, &s2));
+    for (double& v : leg) v /= norm2;
+    for (double& v : rung) v /= norm2;
+    s2 /= norm2;
+    obs_seconds += since(to);
+    record(energy, 1.0 - kept, l, sweep, stats.iters, leg, rung, s2);
     if (!out) return DMRG2D_OK;
     // ---- renormalisation: U^T O U for H_enl and the new boundary operators ----------------
     const auto tr = std::chrono::steady_clock::now();
@@ -608,13 +736,29 @@ class Sweeper {
       D2_TRY(kron_col(dsp_[y].p, false, U.p, T.p, mb, k, 1.0, 0.0));
       D2_TRY(project(T.p, &out->edge[2 * y + 1], false));
     }
+    // total S^z, S^+ of the new block: U^T (1 (x) S_B + S_col (x) 1) U
+    for (int pass = 0; pass < 2; ++pass) {
+      DBuf dB;
+      D2_TRY(dB.upload(pass ? B.Sp_tot : B.Sz_tot, strm_));
+      D2_TRY(kron_blk(dB.p, false, U.p, T.p, mb, k));
+      D2_TRY(kron_col(pass ? dSp_tot_.p : dSz_tot_.p, false, U.p, T.p, mb, k, 1.0, 1.0));
+      D2_TRY(project(T.p, pass ? &out->Sp_tot : &out->Sz_tot, pass == 0));
+    }
     renorm_seconds += since(tr);
     return DMRG2D_OK;
   }
 
-  void record(double e, double trunc, int l, int sweep, int iters) {
+  void record(double e, double trunc, int l, int sweep, int iters, const std::vector<double>& leg,
+              const std::vector<double>& rung, double s2) {
     const int i = rep_->n_steps++;
     if (i < rep_->cap) {
+      const int nl = (int)col_.sz.size(), nr = std::max(nl - 1, 1);
+      if (rep_->leg_bond)
+        for (int y = 0; y < nl; ++y) rep_->leg_bond[(size_t)i * nl + y] = leg[(size_t)y];
+      if (rep_->rung_bond)
+        for (int y = 0; y < nr; ++y)
+          rep_->rung_bond[(size_t)i * nr + y] = y < (int)rung.size() ? rung[(size_t)y] : 0.0;
+      if (rep_->s2) rep_->s2[i] = s2;
       if (rep_->iters) rep_->iters[i] = iters;
       if (rep_->energy) rep_->energy[i] = e;
       if (rep_->trunc) rep_->trunc[i] = trunc;
@@ -623,6 +767,9 @@ class Sweeper {
     }
   }
 
+  Mat col_Sz_tot_, col_Sp_tot_;
+  DBuf dSz_tot_, dSp_tot_;
+  std::vector<DBuf> drung_;
   std::shared_ptr<DBuf> last_x_;  // ground state of the last step's superblock
   int64_t last_nv_ = 0;
 
@@ -704,7 +851,7 @@ extern "C" int dmrg2d_sweep(const dmrg2d_model* model, const dmrg2d_sweep_opts* 
   if (report->cap < 0) return set_error(DMRG2D_EINVAL, "sweep: report cap < 0");
   report->n_steps = 0;
   report->seconds = report->solve_seconds = report->build_seconds = 0.0;
-  report->dm_seconds = report->renorm_seconds = 0.0;
+  report->dm_seconds = report->renorm_seconds = report->obs_seconds = 0.0;
   const auto t0 = std::chrono::steady_clock::now();
   Sweeper sw(model, opts, report, (cudaStream_t)stream);
   const int st = sw.run();
@@ -713,5 +860,6 @@ extern "C" int dmrg2d_sweep(const dmrg2d_model* model, const dmrg2d_sweep_opts* 
   report->build_seconds = sw.build_seconds;
   report->dm_seconds = sw.dm_seconds;
   report->renorm_seconds = sw.renorm_seconds;
+  report->obs_seconds = sw.obs_seconds;
   return st;
 }

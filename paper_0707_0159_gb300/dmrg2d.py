@@ -50,9 +50,12 @@ class SweepReport(C.Structure):
     _fields_ = [("cap", C.c_int), ("n_steps", C.c_int), ("energy", C.POINTER(C.c_double)),
                 ("trunc", C.POINTER(C.c_double)), ("l", C.POINTER(C.c_int)),
                 ("sweep", C.POINTER(C.c_int)), ("iters", C.POINTER(C.c_int)),
+                ("leg_bond", C.POINTER(C.c_double)), ("rung_bond", C.POINTER(C.c_double)),
+                ("s2", C.POINTER(C.c_double)),
                 ("seconds", C.c_double),
                 ("solve_seconds", C.c_double), ("build_seconds", C.c_double),
-                ("dm_seconds", C.c_double), ("renorm_seconds", C.c_double)]
+                ("dm_seconds", C.c_double), ("renorm_seconds", C.c_double),
+                ("obs_seconds", C.c_double)]
 
 
 class OpsInfo(C.Structure):
@@ -478,12 +481,18 @@ def sweep(model: dict, n_columns: int, m_warmup: int, m_sweeps, precision=FP64, 
                      int(max_iter), int(krylov_dim), int(seed), int(bool(sectors)))
     e, t = (C.c_double * cap)(), (C.c_double * cap)()
     ll, sw, it = (C.c_int * cap)(), (C.c_int * cap)(), (C.c_int * cap)()
-    rep = SweepReport(cap, 0, e, t, ll, sw, it, 0.0, 0.0, 0.0, 0.0, 0.0)
+    nl = int(model["n_legs"])
+    nr = max(nl - 1, 1)
+    leg, rung, s2 = (C.c_double * (cap * nl))(), (C.c_double * (cap * nr))(), (C.c_double * cap)()
+    rep = SweepReport(cap, 0, e, t, ll, sw, it, leg, rung, s2, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0)
     mdl = _model(model)
     _check(lib().dmrg2d_sweep(C.byref(mdl), C.byref(opts), C.byref(rep), _stream(stream)))
     n = min(rep.n_steps, cap)
     return {"energy": list(e[:n]), "trunc": list(t[:n]), "l": list(ll[:n]), "sweep": list(sw[:n]),
             "iters": list(it[:n]),
+            "leg_bond": [list(leg[i * nl:(i + 1) * nl]) for i in range(n)],
+            "rung_bond": [list(rung[i * nr:(i + 1) * nr])[:nl - 1] for i in range(n)],
+            "s2": list(s2[:n]), "obs_seconds": rep.obs_seconds,
             "n_steps": rep.n_steps, "seconds": rep.seconds, "solve_seconds": rep.solve_seconds,
             "build_seconds": rep.build_seconds, "dm_seconds": rep.dm_seconds,
             "renorm_seconds": rep.renorm_seconds}

@@ -87,3 +87,23 @@ def test_sector_sweep_matches_dense_sweep(n, m, L):
     assert sec["l"] == dense["l"] and sec["sweep"] == dense["sweep"]
     assert np.allclose(sec["energy"], dense["energy"], rtol=1e-10, atol=0)
     assert np.allclose(sec["trunc"], dense["trunc"], rtol=1e-5, atol=1e-12)
+
+
+@pytest.mark.parametrize("n,m,sectors", [(2, 8, False), (3, 16, True), (2, 64, True)])
+def test_sweep_observables_match_oracle(n, m, sectors):
+    """Per-step bond energies (leg bonds between the central columns, rung bonds of column
+    2) and <S_tot^2> at the end of each sweep, against the oracle's
+    measurements on its own DMRG run (same kept subspaces where the cuts have gaps)."""
+    mdl = model(n)
+    ref = odmrg.dmrg(mdl, 6, m_warmup=m, m_sweeps=[m, m])
+    out = dmrg2d.sweep(mdl, 6, m_warmup=m, m_sweeps=[m, m], precision="fp64", tol=1e-12,
+                       max_iter=800, sectors=sectors)
+    assert out["l"] == ref["l"]
+    assert np.allclose(np.array(out["leg_bond"]), np.array(ref["leg"]), rtol=0, atol=1e-8)
+    if n > 1:
+        assert np.allclose(np.array(out["rung_bond"]), np.array(ref["rung"]), rtol=0, atol=1e-8)
+    s2 = np.array(out["s2"])
+    measured = ~np.isnan(s2)
+    assert measured.sum() == 2                   # the last step of each sweep
+    assert np.allclose(s2[measured], np.array(ref["s2"])[measured], rtol=0, atol=1e-7)
+    assert np.all(np.abs(s2[measured]) <= 1e-3)  # Lieb-Mattis: singlet ground state
