@@ -10,10 +10,11 @@ so no flush is needed between steps.
 
 Also reported: the roofline of the dominant kernel (CUDA events around every
 launch of it, from the library's own timing hook), the end-to-end rate through
-the same call with the vector staged from/to pinned host memory, SM clocks
-sampled during the timed region, the CPU oracle timed on a bounded sample, and
-(with --tte) the time to the ground energy of the mixed-precision solver next
-to the plain FP64 Lanczos.
+the same call with the vector staged from/to pinned host memory (pipelined over
+three streams), SM clocks sampled during the timed region, the CPU oracle timed
+on a bounded sample, the time to the ground energy (residual 1e-7 |E|) of the
+mixed-precision solver (--no-tte to skip; --tte-fp64 adds the plain FP64 Lanczos,
+which takes over 25 minutes), and with --sweep the DMRG sweep on a 4 x 12 ladder.
 
   python bench.py [--gpus N --steps K --warmup W] [--precision tf32|bf16|fp32|fp64]
   python bench.py --impl reference     # the CPU oracle on the same workload
@@ -436,7 +437,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default=os.environ.get("DMRG2D_BENCH_PREC", "tf32"),
                     choices=["tf32", "bf16", "fp32", "fp64"])
-    ap.add_argument("--tte", action="store_true", help="also time the ground-state solve")
+    ap.add_argument("--tte", action="store_true", default=True,
+                    help="time the mixed-precision ground-state solve (default on)")
+    ap.add_argument("--no-tte", dest="tte", action="store_false")
     ap.add_argument("--tte-fp64", action="store_true", help="with --tte: also the plain FP64 solve")
     ap.add_argument("--tte-tol", type=float, default=1e-7)
     ap.add_argument("--tte-fp64-max-iter", type=int, default=900)
