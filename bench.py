@@ -403,19 +403,25 @@ def dmrg_sweep_run(args):
 
 def time_to_energy(ops, n, prec, args, dev):
     """Ground energy to a residual of tol*|E| from the same start vector: the mixed
-    solver (low-precision H·v + FP64 outer loop) and, with --tte-fp64, plain FP64 Lanczos."""
+    solver (low-precision H·v + an outer Rayleigh-Ritz loop whose H·v is FP64 emulated
+    with float pairs, and again with true FP64 H·v there) and, with --tte-fp64, plain
+    FP64 Lanczos."""
     import torch
     from paper_0707_0159_gb300 import dmrg2d, synth
     v0 = torch.from_numpy(synth.start_vector(n, 3)).to(dev)
     res = {"tol_rel_residual": args.tte_tol}
-    x = v0.clone()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    e_mp, st_mp, c_mp = dmrg2d.lanczos_ground(ops, x, precision=prec, refine=1, tol=args.tte_tol,
-                                              inner_iter=300, krylov_dim=40, outer_max=40)
-    torch.cuda.synchronize()
-    res["mixed"] = {"precision": args.precision, "seconds": time.perf_counter() - t0,
-                    "energy": e_mp, "status": c_mp, **st_mp}
+    for key, rprec in (("mixed", "fp64x"), ("mixed_fp64_refine", "fp64")):
+        x = v0.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e_mp, st_mp, c_mp = dmrg2d.lanczos_ground(ops, x, precision=prec, refine=1,
+                                                  tol=args.tte_tol, inner_iter=300,
+                                                  krylov_dim=40, outer_max=40,
+                                                  refine_precision=rprec)
+        torch.cuda.synchronize()
+        res[key] = {"precision": args.precision, "refine_precision": rprec,
+                    "seconds": time.perf_counter() - t0, "energy": e_mp, "status": c_mp, **st_mp}
+    e_mp = res["mixed"]["energy"]
     if args.tte_fp64:
         x = v0.clone()
         t0 = time.perf_counter()

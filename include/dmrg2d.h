@@ -61,7 +61,10 @@ enum {
   DMRG2D_FP64 = 0,   /* v, y double; DFMA                                            */
   DMRG2D_TF32 = 1,   /* v float, y float; tcgen05 kind::tf32, FP32 accumulate in TMEM */
   DMRG2D_BF16 = 2,   /* v bf16 (uint16 bits), y float; tcgen05 kind::f16, FP32 acc  */
-  DMRG2D_FP32 = 3    /* v float, y float; FP32 FMA on CUDA cores                      */
+  DMRG2D_FP32 = 3,   /* v float, y float; FP32 FMA on CUDA cores                      */
+  DMRG2D_FP64X = 4   /* v, y double; float-pair arithmetic (~48-bit significands) on
+                        the FP32 CUDA cores: FP64 emulated for the mixed solver's
+                        residuals; dense superblocks only                             */
 };
 
 typedef struct dmrg2d_model {
@@ -166,6 +169,8 @@ typedef struct dmrg2d_solver_opts {
   int start_reorth;    /* mixed: Gram-Schmidt passes per step of the low-precision
                           start (2 = full reorthogonalisation as in the plain solve,
                           1 = one pass, 0 = the three-term recurrence only)          */
+  int refine_precision;/* mixed: H·v of the outer loop's residuals, DMRG2D_FP64 or
+                          DMRG2D_FP64X (float pairs, dense superblocks)              */
 } dmrg2d_solver_opts;
 
 typedef struct dmrg2d_solver_stats {

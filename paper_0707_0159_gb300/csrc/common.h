@@ -106,6 +106,7 @@ inline std::pair<cudaEvent_t, cudaEvent_t> prof_slot(const dmrg2d_ops* ops) {
 
 // hv_simt.cu
 int launch_hv_simt_f64(const dmrg2d_ops* ops, const double* v, double* y, cudaStream_t s);
+int launch_hv_simt_ff64(const dmrg2d_ops* ops, const double* v, double* y, cudaStream_t s);
 int launch_hv_simt_f32(const dmrg2d_ops* ops, const float* v, float* y, cudaStream_t s);
 
 // hv_tc.cu

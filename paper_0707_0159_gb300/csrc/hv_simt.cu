@@ -125,6 +125,150 @@ hv_simt_kernel(const T* __restrict__ v, T* __restrict__ y, const T* __restrict__
     }
 }
 
+// ---- FP64 emulated with float pairs (FP64X) ------------------------------------------------
+// A double x is carried as (hi, lo) = (fl(x), fl(x - hi)): about 48 significant bits.
+// Products are exact in two floats (hi*hi by FMA error-free transformation, cross terms
+// added to the error word; lo*lo dropped, 2^-48 relative); sums use the two-sum of Knuth
+// on the high words with all errors collected in the low word, renormalised at the end.
+// Relative error per H·v ~ 2^-48 sqrt(K) (K = terms per output), far below what the
+// mixed solver's residual needs.  Same tiling as hv_simt_kernel; float-pair arithmetic
+// runs on the FP32 pipes (64x the FP64 rate on this part).
+struct ff {
+  float hi, lo;
+};
+__device__ __forceinline__ ff ff_of(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+// acc (sum in hi, collected errors in lo) += a * b
+__device__ __forceinline__ void ff_fma(ff& acc, const ff a, const ff b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);        // exact: a.hi b.hi = p + e
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  const float s = acc.hi + p;            // two-sum of the high words
+  const float bb = s - acc.hi;
+  const float err = (acc.hi - (s - bb)) + (p - bb);
+  acc.hi = s;
+  acc.lo += err + e;
+}
+__device__ __forceinline__ double ff_to_double(const ff a) { return (double)a.hi + (double)a.lo; }
+
+__global__ void __launch_bounds__(TX * TY)
+hv_simt_ff_kernel(const double* __restrict__ v, double* __restrict__ y,
+                  const double* __restrict__ HL, const double* __restrict__ HR,
+                  const double* __restrict__ Cval, SimtParams p) {
+  __shared__ ff As[BK][BM];
+  __shared__ ff Bs[BK][BN];
+  const int nbm = (p.m1 + BM - 1) / BM;
+  const int nbn = (p.m4 + BN - 1) / BN;
+  const int bm = blockIdx.x % nbm, i2 = blockIdx.x / nbm;
+  const int bn = blockIdx.y % nbn, i3 = blockIdx.y / nbn;
+  const int i0 = bm * BM, j0 = bn * BN;
+  const int tid = threadIdx.x;
+  const int tx = tid % TX, ty = tid / TX;
+  const int m1 = p.m1, m4 = p.m4;
+  const int64_t ld = p.ld;
+  const ff zero = {0.f, 0.f};
+
+  ff acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = zero;
+
+  auto mma_tile = [&]() {
+#pragma unroll
+    for (int k = 0; k < BK; ++k) {
+      ff av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[k][tx + TX * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = Bs[k][ty + TY * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) ff_fma(acc[a][b], av[a], bv[b]);
+    }
+  };
+
+  // ---- phase 1: H_l V ----
+  for (int e = p.Lptr[i2]; e < p.Lptr[i2 + 1]; ++e) {
+    const double* A = HL + (size_t)e * m1 * m1;
+    const double* B = v + (int64_t)p.Lcol[e] * m1 + ld * ((int64_t)i3 * m4);
+    for (int k0 = 0; k0 < m1; k0 += BK) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int k = tid % BK, i = tid / BK + 16 * r;
+        const int gi = i0 + i, gk = k0 + k;
+        As[k][i] = (gi < m1 && gk < m1) ? ff_of(A[(size_t)gi * m1 + gk]) : zero;
+        const int gj = j0 + i;
+        Bs[k][i] = (gk < m1 && gj < m4) ? ff_of(B[gk + ld * gj]) : zero;
+      }
+      __syncthreads();
+      mma_tile();
+      __syncthreads();
+    }
+  }
+  // ---- phase 2: V H_r^T ----
+  for (int e = p.Rptr[i3]; e < p.Rptr[i3 + 1]; ++e) {
+    const double* A = v + (int64_t)i2 * m1 + ld * ((int64_t)p.Rcol[e] * m4);
+    const double* B = HR + (size_t)e * m4 * m4;
+    for (int k0 = 0; k0 < m4; k0 += BK) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int i = tid % BM, k = tid / BM + 4 * r;
+        const int gi = i0 + i, gk = k0 + k;
+        As[k][i] = (gi < m1 && gk < m4) ? ff_of(A[gi + ld * gk]) : zero;
+        const int kb = tid % BK, j = tid / BK + 16 * r;
+        const int gj = j0 + j, gkb = k0 + kb;
+        Bs[kb][j] = (gj < m4 && gkb < m4) ? ff_of(B[(size_t)gj * m4 + gkb]) : zero;
+      }
+      __syncthreads();
+      mma_tile();
+      __syncthreads();
+    }
+  }
+  // ---- phase 3: scalar tile moves, then the single store of Y ----
+  const int t = i2 + p.d * i3;
+  for (int e = p.Cptr[t]; e < p.Cptr[t + 1]; ++e) {
+    const int src = p.Csrc[e];
+    const int s2 = src % p.d, s3 = src / p.d;
+    const ff c = ff_of(Cval[e]);
+    const double* S = v + (int64_t)s2 * m1 + ld * ((int64_t)s3 * m4);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int gi = i0 + tx + TX * a, gj = j0 + ty + TY * b;
+        if (gi < m1 && gj < m4) ff_fma(acc[a][b], c, ff_of(S[gi + ld * gj]));
+      }
+  }
+  double* Yt = y + (int64_t)i2 * m1 + ld * ((int64_t)i3 * m4);
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int gi = i0 + tx + TX * a, gj = j0 + ty + TY * b;
+      if (gi < m1 && gj < m4) Yt[gi + ld * gj] = ff_to_double(acc[a][b]);
+    }
+}
+
+SimtParams simt_params(const dmrg2d_ops* ops) {
+  SimtParams p;
+  p.m1 = ops->m1;
+  p.m4 = ops->m4;
+  p.d = ops->d;
+  p.ld = ops->ld;
+  p.Lptr = ops->dev.Lptr;
+  p.Lcol = ops->dev.Lcol;
+  p.Rptr = ops->dev.Rptr;
+  p.Rcol = ops->dev.Rcol;
+  p.Cptr = ops->dev.Cptr;
+  p.Csrc = ops->dev.Csrc;
+  return p;
+}
+
 template <typename T>
 int launch(const dmrg2d_ops* ops, const T* v, T* y, const T* HL, const T* HR, const T* C,
            cudaStream_t s) {
@@ -153,7 +297,29 @@ int launch(const dmrg2d_ops* ops, const T* v, T* y, const T* HL, const T* HR, co
   return DMRG2D_OK;
 }
 
+int launch_ff(const dmrg2d_ops* ops, const double* v, double* y, cudaStream_t s) {
+  const SimtParams p = simt_params(ops);
+  const int64_t gx = (int64_t)((ops->m1 + BM - 1) / BM) * ops->d;
+  const int64_t gy = (int64_t)((ops->m4 + BN - 1) / BN) * ops->d;
+  if (gx > 0x7fffffff || gy > 65535)
+    return set_error(DMRG2D_EUNSUPPORTED, "SIMT grid %lld x %lld too large", (long long)gx,
+                     (long long)gy);
+  auto ev = prof_slot(ops);
+  if (ev.first) D2_CUDA(cudaEventRecord(ev.first, s));
+  hv_simt_ff_kernel<<<dim3((unsigned)gx, (unsigned)gy), TX * TY, 0, s>>>(
+      v, y, ops->dev.HL64, ops->dev.HR64, ops->dev.Cval64, p);
+  D2_CUDA(cudaGetLastError());
+  if (ev.second) D2_CUDA(cudaEventRecord(ev.second, s));
+  return DMRG2D_OK;
+}
+
 }  // namespace
+
+int launch_hv_simt_ff64(const dmrg2d_ops* ops, const double* v, double* y, cudaStream_t s) {
+  if (ops->sec)
+    return set_error(DMRG2D_EUNSUPPORTED, "FP64X H·v: dense superblocks only");
+  return launch_ff(ops, v, y, s);
+}
 
 int launch_hv_simt_f64(const dmrg2d_ops* ops, const double* v, double* y, cudaStream_t s) {
   if (ops->sec) return sec_apply(ops, v, y, DMRG2D_FP64, s);
@@ -178,6 +344,8 @@ extern "C" int dmrg2d_apply_H(const dmrg2d_ops* ops, const void* v, void* y, int
       return launch_hv_simt_f64(ops, (const double*)v, (double*)y, s);
     case DMRG2D_FP32:
       return launch_hv_simt_f32(ops, (const float*)v, (float*)y, s);
+    case DMRG2D_FP64X:
+      return launch_hv_simt_ff64(ops, (const double*)v, (double*)y, s);
     case DMRG2D_TF32:
     case DMRG2D_BF16:
       if (!ops->tc_ok)

@@ -507,9 +507,12 @@ struct Ctx {
   int hv(int prec, const double* x, double* y) {
     cudaEvent_t a = nullptr, b = nullptr;
     D2_TRY(next_events(&a, &b));
-    if (prec == DMRG2D_FP64) {
+    if (prec == DMRG2D_FP64 || prec == DMRG2D_FP64X) {  // the refinement-precision H·v
       if (a) D2_CUDA(cudaEventRecord(a, s));
-      D2_TRY(launch_hv_simt_f64(ops, x, y, s));
+      if (prec == DMRG2D_FP64X)
+        D2_TRY(launch_hv_simt_ff64(ops, x, y, s));
+      else
+        D2_TRY(launch_hv_simt_f64(ops, x, y, s));
       if (b) D2_CUDA(cudaEventRecord(b, s));
       if (st) st->n_hv_fp64++;
       return DMRG2D_OK;
@@ -799,7 +802,8 @@ static int mixed_outer(Ctx& C, const dmrg2d_solver_opts* o, double* x, double* e
 
   D2_TRY(C.nrm(x, sc + 3));
   D2_TRY(C.scale_inv(U, x, sc + 3));
-  D2_TRY(C.hv(DMRG2D_FP64, U, W));
+  const int rprec = o->refine_precision == DMRG2D_FP64X ? DMRG2D_FP64X : DMRG2D_FP64;
+  D2_TRY(C.hv(rprec, U, W));
   int s = 1;
   std::vector<double> Gh(smax * smax, 0.0);
   auto update_G_col = [&](int jcol) -> int {
@@ -894,7 +898,7 @@ static int mixed_outer(Ctx& C, const dmrg2d_solver_opts* o, double* x, double* e
       break;
     }
     D2_TRY(C.scale_inv(U + (int64_t)s * n, t, sc + 4));
-    D2_TRY(C.hv(DMRG2D_FP64, U + (int64_t)s * n, W + (int64_t)s * n));
+    D2_TRY(C.hv(rprec, U + (int64_t)s * n, W + (int64_t)s * n));
     D2_TRY(update_G_col(s));
     ++s;
   }
@@ -922,6 +926,10 @@ extern "C" int dmrg2d_lanczos_ground(const dmrg2d_ops* ops, const dmrg2d_solver_
     return set_error(DMRG2D_EINVAL, "unknown precision %d", o.precision);
   if ((o.precision == DMRG2D_TF32 || o.precision == DMRG2D_BF16) && !ops->tc_ok)
     return set_error(DMRG2D_EUNSUPPORTED, "tensor-core path unsupported for these shapes");
+  if (o.refine_precision != DMRG2D_FP64 && o.refine_precision != DMRG2D_FP64X)
+    return set_error(DMRG2D_EINVAL, "refine_precision must be FP64 or FP64X");
+  if (o.refine_precision == DMRG2D_FP64X && ops->sec)
+    return set_error(DMRG2D_EUNSUPPORTED, "FP64X refinement: dense superblocks only");
   const auto t0 = std::chrono::steady_clock::now();
   dmrg2d_solver_stats local{};
   Ctx C;

@@ -13,8 +13,8 @@ import os
 import numpy as np
 
 HEISENBERG, HUBBARD = 0, 1
-FP64, TF32, BF16, FP32 = 0, 1, 2, 3
-PRECISION = {"fp64": FP64, "tf32": TF32, "bf16": BF16, "fp32": FP32}
+FP64, TF32, BF16, FP32, FP64X = 0, 1, 2, 3, 4
+PRECISION = {"fp64": FP64, "tf32": TF32, "bf16": BF16, "fp32": FP32, "fp64x": FP64X}
 STATUS = {0: "OK", -1: "EINVAL", -2: "ESHAPE", -3: "ENOMEM", -4: "ECUDA", -5: "ENOCONV",
           -6: "ETIMEOUT", -7: "ENAN", -8: "EUNSUPPORTED"}
 
@@ -69,7 +69,7 @@ class SolverOpts(C.Structure):
     _fields_ = [("max_iter", C.c_int), ("krylov_dim", C.c_int), ("tol", C.c_double),
                 ("fixed_steps", C.c_int), ("precision", C.c_int), ("refine", C.c_int),
                 ("inner_iter", C.c_int), ("outer_max", C.c_int), ("check_every", C.c_int),
-                ("start_reorth", C.c_int)]
+                ("start_reorth", C.c_int), ("refine_precision", C.c_int)]
 
 
 class DavidsonOpts(C.Structure):
@@ -246,7 +246,8 @@ def sector_dense_index(ops: Ops) -> np.ndarray:
 
 
 _DTYPES = {FP64: ("float64", "float64"), FP32: ("float32", "float32"),
-           TF32: ("float32", "float32"), BF16: ("bfloat16", "float32")}
+           TF32: ("float32", "float32"), BF16: ("bfloat16", "float32"),
+           FP64X: ("float64", "float64")}
 
 
 def apply_H(ops: Ops, v, y, precision=FP64, stream=None):
@@ -320,7 +321,7 @@ def lanczos_ground(ops: Ops, x, stream=None, **opts):
     for k, v in opts.items():
         if k not in o:
             raise KeyError(k)
-        o[k] = PRECISION.get(v, v) if k == "precision" else v
+        o[k] = PRECISION.get(v, v) if k in ("precision", "refine_precision") else v
     so = SolverOpts(**o)
     if not x.is_cuda or str(x.dtype) != "torch.float64" or x.numel() != ops.info["n_vec"]:
         raise ValueError("x must be a CUDA float64 tensor of n_vec elements")
@@ -346,7 +347,7 @@ def lanczos_ground_noalloc(ops: Ops, x, stream=None, **opts):
     for k, v in opts.items():
         if k not in o:
             raise KeyError(k)
-        o[k] = PRECISION.get(v, v) if k == "precision" else v
+        o[k] = PRECISION.get(v, v) if k in ("precision", "refine_precision") else v
     so = SolverOpts(**o)
     if not x.is_cuda or str(x.dtype) != "torch.float64" or x.numel() != ops.info["n_vec"]:
         raise ValueError("x must be a CUDA float64 tensor of n_vec elements")

@@ -29,8 +29,8 @@ def run(ops, v, prec):
         x = x.float()
     elif prec == dmrg2d.BF16:
         x = x.bfloat16()
-    y = torch.empty(x.numel(), dtype=torch.float64 if prec == dmrg2d.FP64 else torch.float32,
-                    device=DEV)
+    wide = prec in (dmrg2d.FP64, dmrg2d.FP64X)
+    y = torch.empty(x.numel(), dtype=torch.float64 if wide else torch.float32, device=DEV)
     dmrg2d.apply_H(ops, x, y, prec)
     torch.cuda.synchronize()
     return y.double().cpu().numpy(), x.double().cpu().numpy()
@@ -61,6 +61,17 @@ def test_fp64_small_shapes(case):
     assert ops.info["n_vec"] == sb.n_vec
     v = synth.start_vector(sb.n_vec, 7)
     y, _ = run(ops, v, dmrg2d.FP64)
+    assert rel(y, sb.apply(v)) <= 1e-12
+
+
+@pytest.mark.parametrize("case", SMALL)
+def test_fp64x_small_shapes(case):
+    """FP64 emulated with float pairs: FP64-class accuracy (<= 1e-12) against the oracle."""
+    mdl, left, right = make(*case)
+    sb = Superblock(mdl, left, right)
+    ops = dmrg2d.build_ops(mdl, left, right)
+    v = synth.start_vector(sb.n_vec, 7)
+    y, _ = run(ops, v, dmrg2d.FP64X)
     assert rel(y, sb.apply(v)) <= 1e-12
 
 
@@ -196,9 +207,10 @@ def ladder3_full():
     return ops, sb, v, idx
 
 
-def test_ladder3_full_fp64_sampled(ladder3_full):
+@pytest.mark.parametrize("prec", [dmrg2d.FP64, dmrg2d.FP64X])
+def test_ladder3_full_fp64_sampled(ladder3_full, prec):
     ops, sb, v, idx = ladder3_full
-    y, _ = run(ops, v, dmrg2d.FP64)
+    y, _ = run(ops, v, prec)
     ref = sb.apply_at(v, idx)
     assert rel(y[idx], ref) <= 1e-12
 

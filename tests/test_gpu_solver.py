@@ -107,12 +107,13 @@ def test_fp64_lanczos_converges(ladder2_m128):
     assert st64["resid"] <= 1e-10 * abs(e64)
 
 
-@pytest.mark.parametrize("prec", [dmrg2d.FP32, dmrg2d.TF32, dmrg2d.BF16])
-def test_mixed_precision_reaches_fp64_energy(ladder2_m128, prec):
+@pytest.mark.parametrize("prec,rprec", [(dmrg2d.FP32, dmrg2d.FP64), (dmrg2d.TF32, dmrg2d.FP64),
+                                        (dmrg2d.BF16, dmrg2d.FP64), (dmrg2d.TF32, dmrg2d.FP64X)])
+def test_mixed_precision_reaches_fp64_energy(ladder2_m128, prec, rprec):
     ops, v0, e64, st64, c64 = ladder2_m128
     assert ops.info["tc_ok"]
     e, x, st, code = gpu_ground(ops, v0, precision=prec, refine=1, tol=1e-8, inner_iter=60,
-                                outer_max=40)
+                                outer_max=40, refine_precision=rprec)
     assert code == 0, st
     assert abs(e - e64) <= 1e-8 * abs(e64), (e, e64, st)
     assert st["resid"] <= 1e-8 * abs(e)
