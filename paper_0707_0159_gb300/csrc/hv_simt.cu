@@ -142,15 +142,16 @@ __device__ __forceinline__ ff ff_of(double x) {
 }
 // acc (sum in hi, collected errors in lo) += a * b
 __device__ __forceinline__ void ff_fma(ff& acc, const ff a, const ff b) {
-  const float p = a.hi * b.hi;
+  // __fmul_rn / __fadd_rn: never contracted into an FMA, which would break the two-sum
+  const float p = __fmul_rn(a.hi, b.hi);
   float e = fmaf(a.hi, b.hi, -p);        // exact: a.hi b.hi = p + e
   e = fmaf(a.hi, b.lo, e);
   e = fmaf(a.lo, b.hi, e);
-  const float s = acc.hi + p;            // two-sum of the high words
-  const float bb = s - acc.hi;
-  const float err = (acc.hi - (s - bb)) + (p - bb);
+  const float s = __fadd_rn(acc.hi, p);  // two-sum of the high words
+  const float bb = __fsub_rn(s, acc.hi);
+  const float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
   acc.hi = s;
-  acc.lo += err + e;
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(err, e));
 }
 __device__ __forceinline__ double ff_to_double(const ff a) { return (double)a.hi + (double)a.lo; }
 

@@ -157,14 +157,34 @@ __global__ void k_f32_to_f64(const float* __restrict__ x, double* __restrict__ o
     o[e] = (double)x[e];
 }
 
-// ---- fused conjugate-gradient steps of the mixed solver's inner loop ----------------
-// The CG runs on (I - x x^T)(H~ - theta)(I - x x^T) t = -r.  With y = H~ p (FP32, straight
-// from the low-precision H·v) the projected operator applied to p is
-//   q = y - theta p - (x.q') x,   q' = y - theta p,
-// and one step needs x.q', p.q (= p.q' since p is orthogonal to x), then
-//   t += a p,  r -= a q,  rr' = r.r,  p = r + (rr'/rr) p.
-// Three passes over the vectors instead of eight; scalars stay on the device.
-enum { CG_XQ = 40, CG_PQ, CG_A, CG_RR, CG_RR1, CG_BETA, CG_THETA };
+// ---- FP32-vector kernels of the mixed solver's low-precision phases -----------------
+// Vectors that only ever meet the low-precision H~ (the Lanczos start basis, the vectors
+// of the inner CG on the correction equation) are stored in FP32: their own rounding
+// (6e-8) is far below H~'s, and it halves their HBM traffic.  Their arithmetic also stays
+// on the FP32 pipes: GB300 runs FP64 at 1/64 of the FP32 rate, so a single FP64 operation
+// per element already costs more time than the element's HBM traffic.  Dot products keep
+// ~48 bits per thread with a compensated FP32 sum (exact products by fmaf, Knuth's
+// two-sum), and the per-thread partials are reduced in FP64.
+
+struct acc2 {
+  float s = 0.f, c = 0.f;  // value s + c; c collects the rounding errors
+};
+// a += x, the rounding error of the sum kept in c (two-sum; __fadd_rn is never contracted)
+__device__ __forceinline__ void acc_add(acc2& a, float x) {
+  const float t = __fadd_rn(a.s, x);
+  const float bp = __fsub_rn(t, a.s);
+  const float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+  a.s = t;
+  a.c = __fadd_rn(a.c, err);
+}
+// a += x y with the product's rounding error fmaf(x, y, -xy) added to c
+__device__ __forceinline__ void acc_fma(acc2& a, float x, float y) {
+  const float p = __fmul_rn(x, y);
+  const float e = fmaf(x, y, -p);
+  acc_add(a, p);
+  a.c = __fadd_rn(a.c, e);
+}
+__device__ __forceinline__ double acc_val(const acc2& a) { return (double)a.s + (double)a.c; }
 
 __device__ __forceinline__ float to_tf32(float f) {
   uint32_t u;
@@ -172,23 +192,141 @@ __device__ __forceinline__ float to_tf32(float f) {
   return __uint_as_float(u);
 }
 
-// part[b] = partial x.q', part[g + b] = partial p.q'
-__global__ void k_cg_dots(const float* __restrict__ y, const double* __restrict__ p,
-                          const double* __restrict__ x, const double* __restrict__ scal,
-                          int64_t n, double* __restrict__ part) {
-  const double theta = scal[CG_THETA];
-  double sx = 0.0, sp = 0.0;
+// lo[e] = f in the H~ input format (BF16, TF32 rounded to nearest, or FP32)
+__device__ __forceinline__ void put_lo(void* lo, int precision, int64_t e, float f) {
+  if (precision == DMRG2D_BF16)
+    ((__nv_bfloat16*)lo)[e] = __float2bfloat16_rn(f);
+  else if (precision == DMRG2D_TF32)
+    ((float*)lo)[e] = to_tf32(f);
+  else
+    ((float*)lo)[e] = f;
+}
+
+__global__ void k_dot_partial32(const float* __restrict__ a, const float* __restrict__ b,
+                                int64_t n, double* __restrict__ part) {
+  acc2 s;
+#pragma unroll 4
+  for (int64_t i = (int64_t)blockIdx.x * VT + threadIdx.x; i < n; i += (int64_t)gridDim.x * VT)
+    acc_fma(s, a[i], b[i]);
+  const double v = block_sum(acc_val(s));
+  if (threadIdx.x == 0) part[blockIdx.x] = v;
+}
+
+// part[(i0+c)*gridDim.x + blk] = partial of Q_{i0+c} . w   (FP32 basis and vector)
+__global__ void k_multidot_partial32(const float* __restrict__ Q, int64_t stride, int k,
+                                     const float* __restrict__ w, int64_t n,
+                                     double* __restrict__ part) {
+  const int i0 = blockIdx.y * MD_CHUNK;
+  acc2 acc[MD_CHUNK];
   for (int64_t e = (int64_t)blockIdx.x * VT + threadIdx.x; e < n; e += (int64_t)gridDim.x * VT) {
-    const double pe = p[e];
-    const double q = (double)y[e] - theta * pe;
-    sx += x[e] * q;
-    sp += pe * q;
+    const float we = w[e];
+#pragma unroll
+    for (int c = 0; c < MD_CHUNK; ++c)
+      if (i0 + c < k) acc_fma(acc[c], Q[(int64_t)(i0 + c) * stride + e], we);
   }
-  sx = block_sum(sx);
-  sp = block_sum(sp);
+#pragma unroll
+  for (int c = 0; c < MD_CHUNK; ++c) {
+    double s = block_sum(acc_val(acc[c]));
+    if (threadIdx.x == 0 && i0 + c < k) part[(size_t)(i0 + c) * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// out -= sum_i h[i] Q_i (sign = -1) or out = sum_i h[i] Q_i (sign = 0), FP32 arithmetic
+template <typename TO>
+__global__ void k_combo32(TO* __restrict__ out, const float* __restrict__ Q, int64_t stride, int k,
+                          const double* __restrict__ h, int64_t n, int sign) {
+  extern __shared__ float hf[];
+  for (int i = threadIdx.x; i < k; i += VT) hf[i] = (float)h[i];
+  __syncthreads();
+  for (int64_t e = (int64_t)blockIdx.x * VT + threadIdx.x; e < n; e += (int64_t)gridDim.x * VT) {
+    float s = 0.f;
+    for (int i = 0; i < k; ++i) s = fmaf(hf[i], Q[(int64_t)i * stride + e], s);
+    out[e] = sign ? (TO)((float)out[e] - s) : (TO)s;
+  }
+}
+
+// w -= alpha[j] q_j + beta[j-1] q_{j-1}; part[b] = partial w.w of the result
+__global__ void k_lz_axpy2_nrm32(float* __restrict__ w, const float* __restrict__ qj,
+                                 const float* __restrict__ qjm1, const double* __restrict__ alpha_j,
+                                 const double* __restrict__ beta_jm1, int64_t n,
+                                 double* __restrict__ part) {
+  const float a = (float)*alpha_j;
+  const float b = beta_jm1 ? (float)*beta_jm1 : 0.f;
+  acc2 s;
+#pragma unroll 4
+  for (int64_t e = (int64_t)blockIdx.x * VT + threadIdx.x; e < n; e += (int64_t)gridDim.x * VT) {
+    float r = fmaf(-a, qj[e], w[e]);
+    if (qjm1) r = fmaf(-b, qjm1[e], r);
+    w[e] = r;
+    acc_fma(s, r, r);
+  }
+  const double v = block_sum(acc_val(s));
+  if (threadIdx.x == 0) part[blockIdx.x] = v;
+}
+
+// q = in / *nrm (zero when the norm is zero) in FP32, and its copy lo in the H~ format
+template <typename TI>
+__global__ void k_scale_to32(float* __restrict__ q, const TI* __restrict__ in,
+                             const double* __restrict__ nrm, void* __restrict__ lo, int precision,
+                             int64_t n) {
+  const double s = *nrm;
+  const float f = s > 0.0 ? (float)(1.0 / s) : 0.f;
+#pragma unroll 4
+  for (int64_t e = (int64_t)blockIdx.x * VT + threadIdx.x; e < n; e += (int64_t)gridDim.x * VT) {
+    const float v = (float)in[e] * f;
+    q[e] = v;
+    put_lo(lo, precision, e, v);
+  }
+}
+
+// ---- fused conjugate-gradient steps of the mixed solver's inner loop ----------------
+// The CG runs on (I - x x^T)(H~ - theta)(I - x x^T) t = -r.  With y = H~ p (FP32, straight
+// from the low-precision H·v) the projected operator applied to p is
+//   q = y - theta p - (x.q') x,   q' = y - theta p,
+// and one step needs x.q', p.q (= p.q' since p is orthogonal to x), then
+//   t += a p,  r -= a q,  rr' = r.r,  p = r + (rr'/rr) p.
+// Three passes over FP32 vectors (x32 is x rounded to FP32; the correction is
+// re-orthogonalised in FP64 afterwards); scalars stay on the device.
+enum { CG_XQ = 40, CG_PQ, CG_A, CG_RR, CG_RR1, CG_BETA, CG_THETA };
+
+// CG start: r32 = r, x32 = x, t32 = 0, p32 = r32 and its H~ copy; part[b] = partial r32.r32
+__global__ void k_cg_start32(const double* __restrict__ r, const double* __restrict__ x,
+                             float* __restrict__ r32, float* __restrict__ x32,
+                             float* __restrict__ t32, float* __restrict__ p32,
+                             void* __restrict__ lo, int precision, int64_t n,
+                             double* __restrict__ part) {
+  acc2 s;
+  for (int64_t e = (int64_t)blockIdx.x * VT + threadIdx.x; e < n; e += (int64_t)gridDim.x * VT) {
+    const float re = (float)r[e];
+    r32[e] = re;
+    p32[e] = re;
+    x32[e] = (float)x[e];
+    t32[e] = 0.f;
+    put_lo(lo, precision, e, re);
+    acc_fma(s, re, re);
+  }
+  const double v = block_sum(acc_val(s));
+  if (threadIdx.x == 0) part[blockIdx.x] = v;
+}
+
+// part[b] = partial x.q', part[g + b] = partial p.q'
+__global__ void k_cg_dots(const float* __restrict__ y, const float* __restrict__ p,
+                          const float* __restrict__ x, const double* __restrict__ scal,
+                          int64_t n, double* __restrict__ part) {
+  const float theta = (float)scal[CG_THETA];
+  acc2 sx, sp;
+#pragma unroll 4
+  for (int64_t e = (int64_t)blockIdx.x * VT + threadIdx.x; e < n; e += (int64_t)gridDim.x * VT) {
+    const float pe = p[e];
+    const float q = fmaf(-theta, pe, y[e]);
+    acc_fma(sx, x[e], q);
+    acc_fma(sp, pe, q);
+  }
+  const double vx = block_sum(acc_val(sx));
+  const double vp = block_sum(acc_val(sp));
   if (threadIdx.x == 0) {
-    part[blockIdx.x] = sx;
-    part[gridDim.x + blockIdx.x] = sp;
+    part[blockIdx.x] = vx;
+    part[gridDim.x + blockIdx.x] = vp;
   }
 }
 
@@ -209,25 +347,27 @@ __global__ void k_cg_alpha(const double* __restrict__ part, int np, double* __re
 }
 
 // t += a p, r -= a (y - theta p - xq x); part[b] = partial r.r (of the updated r)
-__global__ void k_cg_update(const float* __restrict__ y, const double* __restrict__ p,
-                            const double* __restrict__ x, double* __restrict__ t,
-                            double* __restrict__ r, const double* __restrict__ scal, int64_t n,
+__global__ void k_cg_update(const float* __restrict__ y, const float* __restrict__ p,
+                            const float* __restrict__ x, float* __restrict__ t,
+                            float* __restrict__ r, const double* __restrict__ scal, int64_t n,
                             double* __restrict__ part) {
-  const double a = scal[CG_A], xq = scal[CG_XQ], theta = scal[CG_THETA];
-  double s = 0.0;
+  const float a = (float)scal[CG_A], xq = (float)scal[CG_XQ], theta = (float)scal[CG_THETA];
+  const bool upd = scal[CG_A] != 0.0;
+  acc2 s;
+#pragma unroll 4
   for (int64_t e = (int64_t)blockIdx.x * VT + threadIdx.x; e < n; e += (int64_t)gridDim.x * VT) {
-    double re = r[e];
-    if (a != 0.0) {
-      const double pe = p[e];
-      const double q = ((double)y[e] - theta * pe) - xq * x[e];
-      t[e] += a * pe;
-      re -= a * q;
+    float re = r[e];
+    if (upd) {
+      const float pe = p[e];
+      const float q = fmaf(-xq, x[e], fmaf(-theta, pe, y[e]));
+      t[e] = fmaf(a, pe, t[e]);
+      re = fmaf(-a, q, re);
       r[e] = re;
     }
-    s += re * re;
+    acc_fma(s, re, re);
   }
-  s = block_sum(s);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  const double v = block_sum(acc_val(s));
+  if (threadIdx.x == 0) part[blockIdx.x] = v;
 }
 
 // scal[CG_RR1] = sum of partials; beta = rr1 / rr; rr <- rr1
@@ -243,22 +383,16 @@ __global__ void k_cg_beta(const double* __restrict__ part, int np, double* __res
   }
 }
 
-// p = r + beta p (beta from scal, or 0 for the first direction: p = r), and the
-// low-precision copy of p that the next H~ p reads
-__global__ void k_cg_direction(double* __restrict__ p, const double* __restrict__ r,
-                               const double* __restrict__ scal, int first, void* __restrict__ lo,
+// p = r + beta p, and the low-precision copy of p that the next H~ p reads
+__global__ void k_cg_direction(float* __restrict__ p, const float* __restrict__ r,
+                               const double* __restrict__ scal, void* __restrict__ lo,
                                int precision, int64_t n) {
-  const double beta = first ? 0.0 : scal[CG_BETA];
+  const float beta = (float)scal[CG_BETA];
+#pragma unroll 4
   for (int64_t e = (int64_t)blockIdx.x * VT + threadIdx.x; e < n; e += (int64_t)gridDim.x * VT) {
-    const double pe = first ? r[e] : r[e] + beta * p[e];
+    const float pe = fmaf(beta, p[e], r[e]);
     p[e] = pe;
-    const float f = (float)pe;
-    if (precision == DMRG2D_BF16)
-      ((__nv_bfloat16*)lo)[e] = __float2bfloat16_rn(f);
-    else if (precision == DMRG2D_TF32)
-      ((float*)lo)[e] = to_tf32(f);
-    else
-      ((float*)lo)[e] = f;
+    put_lo(lo, precision, e, pe);
   }
 }
 
@@ -713,6 +847,100 @@ int lanczos(Ctx& C, int prec, double* x, int max_iter, int kdim, double tol, int
   return status;
 }
 
+// Low-precision Lanczos for the mixed solver's start vector: H~ with an FP32 basis (the
+// three-term recurrence plus gs_passes classical Gram-Schmidt passes), explicit restarts
+// from the Ritz vector every kdim steps.  x (FP64): the start vector in, the normalised
+// Ritz vector out.  Per step: H~ q_j into y32, alpha = q_j.w, w -= alpha q_j + beta q_{j-1}
+// with |w| in the same pass, q_{j+1} = w / beta with its H~ copy in the same pass.
+int lanczos_lo(Ctx& C, int prec, double* x, int max_iter, int kdim, double tol, int check_every,
+               double* theta_out, double* resid_out, int* iters_out, int gs_passes) {
+  const int64_t n = C.n;
+  if (kdim < 2) kdim = 2;
+  if (kdim > max_iter + 1) kdim = max_iter + 1;
+  DevBuf Qb, ab, bb, hb, sb, tb;
+  D2_TRY(dmalloc(Qb, sizeof(float) * (size_t)(kdim + 1) * n));
+  D2_TRY(dmalloc(ab, sizeof(double) * (kdim + 1)));
+  D2_TRY(dmalloc(bb, sizeof(double) * (kdim + 1)));
+  D2_TRY(dmalloc(hb, sizeof(double) * (kdim + 1)));
+  D2_TRY(dmalloc(sb, sizeof(double) * (kdim + 1)));
+  D2_TRY(dmalloc(tb, sizeof(double) * 6 * (kdim + 1)));
+  float* Q = (float*)Qb.p;
+  float* w = C.y32;  // H~ q_j lands here and is orthogonalised in place
+  double* alpha = (double*)ab.p;
+  double* beta = (double*)bb.p;
+  double* h = (double*)hb.p;
+  double* sv = (double*)sb.p;
+  double* scr = (double*)tb.p;
+  double* out3 = C.scal;
+  const int g = vgrid(n);
+  auto start_from_x = [&]() -> int {
+    D2_TRY(C.nrm(x, C.scal + 3));
+    k_scale_to32<double><<<g, VT, 0, C.s>>>(Q, x, C.scal + 3, C.lo, prec, n);
+    D2_CUDA(cudaGetLastError());
+    return DMRG2D_OK;
+  };
+  D2_TRY(start_from_x());
+  int j = 0, total = 0;
+  double theta = 0.0, resid = INFINITY;
+  int status = DMRG2D_ENOCONV;
+  if (check_every < 1) check_every = 1;
+  while (true) {
+    float* qj = Q + (int64_t)j * n;
+    D2_TRY(C.hv_lo(prec));  // w = H~ q_j (its H~-format copy is in C.lo)
+    k_dot_partial32<<<g, VT, 0, C.s>>>(qj, w, n, C.part);
+    k_reduce<<<1, VT, 0, C.s>>>(C.part, g, alpha + j, 0);
+    k_lz_axpy2_nrm32<<<g, VT, 0, C.s>>>(w, qj, j > 0 ? qj - n : nullptr, alpha + j,
+                                        j > 0 ? beta + j - 1 : nullptr, n, C.part);
+    k_reduce<<<1, VT, 0, C.s>>>(C.part, g, beta + j, 1);
+    for (int pass = 0; pass < gs_passes; ++pass) {  // CGS against q_0..q_j
+      dim3 grid(g, (j + 1 + MD_CHUNK - 1) / MD_CHUNK);
+      k_multidot_partial32<<<grid, VT, 0, C.s>>>(Q, n, j + 1, w, n, C.part);
+      k_reduce<<<j + 1, VT, 0, C.s>>>(C.part, g, h, 0);
+      k_combo32<float><<<g, VT, (j + 1) * sizeof(float), C.s>>>(w, Q, n, j + 1, h, n, -1);
+      if (pass + 1 == gs_passes) {
+        k_dot_partial32<<<g, VT, 0, C.s>>>(w, w, n, C.part);
+        k_reduce<<<1, VT, 0, C.s>>>(C.part, g, beta + j, 1);
+      }
+    }
+    D2_CUDA(cudaGetLastError());
+    ++j;
+    ++total;
+    const bool last = total >= max_iter;
+    const bool full = j >= kdim;
+    if (last || full || total % check_every == 0) {
+      k_tridiag_ground<<<1, 1, 0, C.s>>>(alpha, beta, j, sv, out3, scr);
+      D2_CUDA(cudaGetLastError());
+      D2_TRY(C.fetch(out3, 3));
+      theta = C.hscal[0];
+      resid = C.hscal[1];
+      if (C.hscal[2] != 0.0 || !std::isfinite(theta)) {
+        status = set_error(DMRG2D_ENAN, "NaN/Inf in the low-precision Lanczos recurrence");
+        break;
+      }
+      const bool conv = resid <= tol * fabs(theta);
+      if (conv || last || full) {
+        k_combo32<double><<<g, VT, j * sizeof(float), C.s>>>(x, Q, n, j, sv, n, 0);  // Ritz
+        D2_CUDA(cudaGetLastError());
+        if (conv || last) {
+          status = conv ? DMRG2D_OK : DMRG2D_ENOCONV;
+          break;
+        }
+        D2_TRY(start_from_x());  // explicit restart from the Ritz vector
+        j = 0;
+        continue;
+      }
+    }
+    k_scale_to32<float><<<g, VT, 0, C.s>>>(Q + (int64_t)j * n, w, beta + j - 1, C.lo, prec, n);
+    D2_CUDA(cudaGetLastError());
+  }
+  D2_TRY(C.nrm(x, C.scal + 3));
+  D2_TRY(C.scale_inv(x, x, C.scal + 3));
+  *theta_out = theta;
+  *resid_out = resid;
+  *iters_out = total;
+  return status;
+}
+
 }  // namespace
 
 int convert_f64_to(const double* x, void* out, int precision, int64_t n, cudaStream_t s) {
@@ -769,7 +997,7 @@ static int mixed_solve(Ctx& C, const dmrg2d_solver_opts* o, double* x, double* e
   // inner_iter
   const int kdim1 = std::max(2, std::min(o->inner_iter, o->krylov_dim) + 1);
   const int passes = std::min(2, std::max(0, o->start_reorth));
-  int st = lanczos(C, o->precision, x, o->inner_iter, kdim1, 1e-6, 0, 5, &th0, &r0, &it0, passes);
+  int st = lanczos_lo(C, o->precision, x, o->inner_iter, kdim1, 1e-6, 5, &th0, &r0, &it0, passes);
   if (st != DMRG2D_OK && st != DMRG2D_ENOCONV) return st;
   C.st->iters += it0;
   // 2. FP64 outer loop
@@ -781,19 +1009,22 @@ static int mixed_outer(Ctx& C, const dmrg2d_solver_opts* o, double* x, double* e
   const int64_t n = C.n;
   const int prec = o->precision;
   const int smax = 6;
-  DevBuf Ub, Wb, xb, hxb, rb, tb, pb, qb, Gb, cb, scb;
+  DevBuf Ub, Wb, hxb, rb, tb, r32b, x32b, t32b, p32b, Gb, cb, scb;
   D2_TRY(dmalloc(Ub, sizeof(double) * (size_t)smax * n));
   D2_TRY(dmalloc(Wb, sizeof(double) * (size_t)smax * n));
   D2_TRY(dmalloc(hxb, sizeof(double) * n));
   D2_TRY(dmalloc(rb, sizeof(double) * n));
   D2_TRY(dmalloc(tb, sizeof(double) * n));
-  D2_TRY(dmalloc(pb, sizeof(double) * n));
-  D2_TRY(dmalloc(qb, sizeof(double) * n));
+  D2_TRY(dmalloc(r32b, sizeof(float) * n));  // the CG's vectors, FP32
+  D2_TRY(dmalloc(x32b, sizeof(float) * n));
+  D2_TRY(dmalloc(t32b, sizeof(float) * n));
+  D2_TRY(dmalloc(p32b, sizeof(float) * n));
   D2_TRY(dmalloc(Gb, sizeof(double) * smax * smax));
   D2_TRY(dmalloc(cb, sizeof(double) * smax));
   D2_TRY(dmalloc(scb, sizeof(double) * 2 * smax * smax));
   double *U = (double*)Ub.p, *W = (double*)Wb.p, *hx = (double*)hxb.p, *r = (double*)rb.p;
-  double *t = (double*)tb.p, *p = (double*)pb.p, *q = (double*)qb.p, *G = (double*)Gb.p;
+  double *t = (double*)tb.p, *G = (double*)Gb.p;
+  float *r32 = (float*)r32b.p, *x32 = (float*)x32b.p, *t32 = (float*)t32b.p, *p32 = (float*)p32b.p;
   double *cc = (double*)cb.p, *scr = (double*)scb.p;
   double* sc = C.scal;  // scalars: [4] tmp dot, [5..] host-fetched, [CG_XQ..] CG state
   const int g = vgrid(n);
@@ -842,29 +1073,28 @@ static int mixed_outer(Ctx& C, const dmrg2d_solver_opts* o, double* x, double* e
       set_error(DMRG2D_ENOCONV, "mixed: %d outer steps, residual %.3e", outer, rn);
       break;
     }
-    // ---- inner CG on (I - xx^T)(H~ - theta)(I - xx^T) t = -r, t0 = 0 ----
-    D2_CUDA(cudaMemsetAsync(t, 0, sizeof(double) * n, C.s));
-    // res (stored in r) = -r projected; p = res
+    // ---- inner CG on (I - xx^T)(H~ - theta)(I - xx^T) t = -r, t0 = 0, FP32 vectors ----
+    // res (stored in r) = -r projected; r32 = res, x32 = x, t32 = 0, p32 = res
     D2_TRY(C.axpby(r, r, 0.0, -1.0));
     D2_TRY(C.dot(x, r, sc + 4));
     D2_TRY(C.fetch(sc + 4, 1));
     D2_TRY(C.axpby(r, x, -C.hscal[0], 1.0));
-    D2_TRY(C.dot(r, r, sc + CG_RR));
     C.hscal[HS_THETA] = theta;
     D2_CUDA(cudaMemcpyAsync(sc + CG_THETA, C.hscal + HS_THETA, sizeof(double),
                             cudaMemcpyHostToDevice, C.s));
-    k_cg_direction<<<g, VT, 0, C.s>>>(p, r, sc, 1, C.lo, prec, n);
+    k_cg_start32<<<g, VT, 0, C.s>>>(r, x, r32, x32, t32, p32, C.lo, prec, n, C.part);
+    k_reduce<<<1, VT, 0, C.s>>>(C.part, g, sc + CG_RR, 0);
     D2_CUDA(cudaGetLastError());
     D2_TRY(C.fetch(sc + CG_RR, 1));
     const double rr0 = C.hscal[0];
     if (!step.exec) D2_TRY(step.capture(C, [&]() -> int {
       // one CG step: y32 = H~ p, the fused vector passes, scalars to the pinned mirror
       D2_TRY(C.hv_lo(prec, nullptr, nullptr, false));  // counted per replay
-      k_cg_dots<<<g, VT, 0, C.s>>>(C.y32, p, x, sc, n, C.part);
+      k_cg_dots<<<g, VT, 0, C.s>>>(C.y32, p32, x32, sc, n, C.part);
       k_cg_alpha<<<1, VT, 0, C.s>>>(C.part, g, sc);
-      k_cg_update<<<g, VT, 0, C.s>>>(C.y32, p, x, t, r, sc, n, C.part);
+      k_cg_update<<<g, VT, 0, C.s>>>(C.y32, p32, x32, t32, r32, sc, n, C.part);
       k_cg_beta<<<1, VT, 0, C.s>>>(C.part, g, sc);
-      k_cg_direction<<<g, VT, 0, C.s>>>(p, r, sc, 0, C.lo, prec, n);
+      k_cg_direction<<<g, VT, 0, C.s>>>(p32, r32, sc, C.lo, prec, n);
       D2_CUDA(cudaGetLastError());
       D2_CUDA(cudaMemcpyAsync(C.hscal, sc + CG_PQ, sizeof(double) * (CG_RR1 - CG_PQ + 1),
                               cudaMemcpyDeviceToHost, C.s));
@@ -879,6 +1109,8 @@ static int mixed_outer(Ctx& C, const dmrg2d_solver_opts* o, double* x, double* e
       if (!(pq > 0.0)) break;  // (no update was made)
       if (rr1 <= 1e-8 * rr0) break;
     }
+    k_f32_to_f64<<<g, VT, 0, C.s>>>(t32, t, n);
+    D2_CUDA(cudaGetLastError());
     // ---- orthonormalise t against U and extend the subspace ----
     if (s == smax) {  // restart with the current Ritz pair
       D2_CUDA(cudaMemcpyAsync(U, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, C.s));
