@@ -202,6 +202,37 @@ def max_over_ranks(x: float, device) -> float:
     return float(t.item())
 
 
+def parse_cpulist(text: str) -> set:
+    cpus = set()
+    for part in text.strip().split(","):
+        if not part:
+            continue
+        lo, _, hi = part.partition("-")
+        cpus.update(range(int(lo), int(hi or lo) + 1))
+    return cpus
+
+
+def bind_near_gpu(index: int):
+    """Restrict this process to the CPUs the GPU's PCI device reports as local (sysfs
+    local_cpulist), so pinned host buffers allocated afterwards land in the memory next
+    to the GPU's host link.  Returns (previous affinity, bound CPUs) or None when the
+    topology is not readable or shares no CPU with the current affinity."""
+    import torch
+    try:
+        p = torch.cuda.get_device_properties(index)
+        bdf = f"{p.pci_domain_id:04x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
+        with open(f"/sys/bus/pci/devices/{bdf}/local_cpulist") as f:
+            local = parse_cpulist(f.read())
+        prev = os.sched_getaffinity(0)
+        use = local & prev
+        if not use or use == prev:
+            return None
+        os.sched_setaffinity(0, use)
+        return prev, sorted(use)
+    except (AttributeError, OSError, ValueError):
+        return None
+
+
 def job_tflops(flops_per_rank_step: float, ms: float, world: int) -> float:
     """Whole-job throughput: every rank does one H·v of its own replica per step, the job
     step takes the slowest rank's time."""
@@ -278,8 +309,20 @@ def run_ours(args):
     # the result back.  Steps are pipelined the way a caller streams work through the
     # library: uploads on one stream, H·v on another, downloads on a third, two buffer
     # sets, so step i+1's upload and step i-1's download overlap step i's H·v.
+    near = bind_near_gpu(local)
     vh = v_host.pin_memory()
     yh = [torch.empty(n, dtype=out_dt).pin_memory() for _ in range(2)]
+    # host-link bandwidth alone, one buffer each way (context for the e2e figure)
+    link = {}
+    for name, (dst, src) in (("h2d_gbs", (v, vh)), ("d2h_gbs", (yh[0], y))):
+        dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        dst.copy_(src, non_blocking=True)
+        b.record()
+        torch.cuda.synchronize()
+        link[name] = src.numel() * src.element_size() / (a.elapsed_time(b) * 1e-3) / 1e9
     vd = [v, torch.empty_like(v)]
     yd = [y, torch.empty_like(y)]
     s_in, s_cmp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
@@ -319,7 +362,11 @@ def run_ours(args):
     e2e = {"value": job_tflops(flops, ms_e2e, world), "unit": "TFLOP/s",
            "h2d_bytes_per_step": vh.numel() * vh.element_size(),
            "d2h_bytes_per_step": yh[0].numel() * yh[0].element_size(),
-           "ms_per_step": ms_e2e, "pipelined": "upload / H·v / download on three streams"}
+           "ms_per_step": ms_e2e, "pipelined": "upload / H·v / download on three streams",
+           "host_link": link,
+           "cpus_bound": f"{len(near[1])} GPU-local CPUs" if near else "unchanged"}
+    if near:
+        os.sched_setaffinity(0, near[0])
 
     out_dtype = {dmrg2d.FP64: "f64", dmrg2d.FP32: "f32", dmrg2d.TF32: "tf32",
                  dmrg2d.BF16: "bf16"}[prec]

@@ -88,6 +88,7 @@ struct GDev {
   std::vector<void*> allocs;
 };
 
+template <int BF16>
 __global__ void __launch_bounds__(G_THREADS, 1)
 hv_tc_grouped_kernel(const __grid_constant__ GMaps maps, const GParams p) {
   extern __shared__ uint8_t smem_raw[];
@@ -200,6 +201,12 @@ hv_tc_grouped_kernel(const __grid_constant__ GMaps maps, const GParams p) {
       bool ok = true;
       for (int ph = 0; ph < 2 && ok; ++ph) {
         const int e0 = ph == 0 ? rs.k1b : cs.k2b, e1 = ph == 0 ? rs.k1e : cs.k2e;
+        // descriptor fields fixed for the phase (no branch between two MMAs: the tensor
+        // pipe's instruction queue is shallow)
+        const uint64_t a_hi = ph == 0 ? sdesc(0, 16, 1024)
+                                      : sdesc(0, p.a2_lbo, p.a2_sbo, p.a2_layout);
+        const uint32_t a_step = ph == 0 ? 32u : p.a2_kstep;
+        const uint64_t b_hi = sdesc(0, 16, 1024);
         for (int e = e0; e < e1 && ok; ++e) {
           const int kdim = ph == 0 ? p.k1[e].kdim : p.k2[e].kdim;
           const int neg = ph == 0 ? p.k1[e].neg : p.k2[e].neg;
@@ -207,28 +214,23 @@ hv_tc_grouped_kernel(const __grid_constant__ GMaps maps, const GParams p) {
                                       : (neg ? p.idesc2[1] : p.idesc2[0]);
           const int nk = (kdim + BK - 1) / BK;
           for (int kc = 0; kc < nk; ++kc) {
+            // the mbarrier's completion orders the TMA writes before these MMAs
             if (!mbar_wait(full(stage), phase, abort)) {
               raise_abort(abort, p.err, 13);
               ok = false;
               break;
             }
-            tc_fence_after();
             const uint32_t a_s = smem_u32(smem + stage * G_STAGE);
             const uint32_t b_s = a_s + G_STAGE_A;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-              const uint64_t ad = ph == 0 ? sdesc(a_s + k * 32, 16, 1024)
-                                          : sdesc(a_s + k * p.a2_kstep, p.a2_lbo, p.a2_sbo,
-                                                  p.a2_layout);
-              const uint64_t bd = sdesc(b_s + k * 32, 16, 1024);
-              umma(dt, ad, bd, id, accum, p.bf16);
+              umma_t<BF16>(dt, a_hi | sdesc_addr(a_s + k * a_step),
+                           b_hi | sdesc_addr(b_s + k * 32), id, accum);
               accum = 1;
             }
             umma_commit(empty(stage));
-            if (++stage == G_STAGES) {
-              stage = 0;
-              phase ^= 1u;
-            }
+            stage = stage + 1 == G_STAGES ? 0 : stage + 1;
+            phase ^= stage == 0 ? 1u : 0u;
           }
         }
       }
@@ -602,7 +604,9 @@ int gp_finalise(dmrg2d_ops* ops, GroupPlan* g, cudaStream_t s) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&D->sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaFuncSetAttribute(hv_tc_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(hv_tc_grouped_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)G_SMEM) != cudaSuccess ||
+        cudaFuncSetAttribute(hv_tc_grouped_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)G_SMEM) != cudaSuccess)
       st = set_error(DMRG2D_ECUDA, "cannot set %zu bytes of shared memory", G_SMEM);
   }
@@ -675,7 +679,10 @@ int gp_launch(const dmrg2d_ops* ops, const GroupPlan* g, const void* v, float* y
   const int grid = std::min(p.ntiles, D->sms);
   auto ev = prof_slot(ops);
   if (ev.first) D2_CUDA(cudaEventRecord(ev.first, s));
-  hv_tc_grouped_kernel<<<grid, G_THREADS, G_SMEM, s>>>(maps, p);
+  if (bf)
+    hv_tc_grouped_kernel<1><<<grid, G_THREADS, G_SMEM, s>>>(maps, p);
+  else
+    hv_tc_grouped_kernel<0><<<grid, G_THREADS, G_SMEM, s>>>(maps, p);
   D2_CUDA(cudaGetLastError());
   if (ev.second) D2_CUDA(cudaEventRecord(ev.second, s));
   return DMRG2D_OK;

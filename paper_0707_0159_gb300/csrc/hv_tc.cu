@@ -143,6 +143,7 @@ __device__ __forceinline__ void epilogue_piece(const TcParams& p, const TileCoor
   }
 }
 
+template <int BF16>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 hv_tc_kernel(const __grid_constant__ CUtensorMap mHL, const __grid_constant__ CUtensorMap mHR,
              const __grid_constant__ CUtensorMap mVk, const __grid_constant__ CUtensorMap mVm,
@@ -249,40 +250,35 @@ hv_tc_kernel(const __grid_constant__ CUtensorMap mHL, const __grid_constant__ CU
         const int e0 = ph == 0 ? p.Lptr[c.i2] : p.Rptr[c.i3];
         const int e1 = ph == 0 ? p.Lptr[c.i2 + 1] : p.Rptr[c.i3 + 1];
         const int kb = ph == 0 ? p.kblk1 : p.kblk2;
+        // descriptor fields fixed for the phase (the A operand of phase 2 is V, MN-major)
+        const uint64_t a_hi = ph == 0 ? sdesc(0, 16, 1024)
+                                      : sdesc(0, p.a2_lbo, p.a2_sbo, p.a2_layout);
+        const uint32_t a_step = ph == 0 ? 32u : p.a2_kstep;
+        const uint64_t b_hi = sdesc(0, 16, 1024);
         for (int e = e0; e < e1 && ok; ++e) {
-          // instruction descriptor of this operator block, chosen once per block from
-          // statically indexed parameters (the issuing thread is on the critical path)
+          // instruction descriptor of this operator block, chosen once per block
           const int neg = p.pooled ? (ph == 0 ? p.k1[e].neg : p.k2[e].neg) : 0;
           const uint32_t idb = ph == 0 ? (neg ? p.idesc1[1] : p.idesc1[0])
                                        : (neg ? p.idesc2[1] : p.idesc2[0]);
           for (int kc = 0; kc < kb; ++kc) {
+            // the mbarrier's completion orders the TMA writes before these MMAs; no
+            // tcgen05 fence is needed per stage
             if (!mbar_wait(full(stage), phase, abort)) {
               raise_abort(abort, p.err, 3);
               ok = false;
               break;
             }
-            tc_fence_after();
             const uint32_t a_s = smem_u32(smem + stage * STAGE_BYTES);
             const uint32_t b_s = a_s + STAGE_A;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-              uint64_t ad, bd;
-              uint32_t id;
-              if (ph == 0) {
-                ad = sdesc(a_s + k * 32, 16, 1024);
-              } else {
-                ad = sdesc(a_s + k * p.a2_kstep, p.a2_lbo, p.a2_sbo, p.a2_layout);
-              }
-              id = idb;
-              bd = sdesc(b_s + k * 32, 16, 1024);
-              umma(dt, ad, bd, id, accum, p.bf16);
+              umma_t<BF16>(dt, a_hi | sdesc_addr(a_s + k * a_step),
+                           b_hi | sdesc_addr(b_s + k * 32), idb, accum);
               accum = 1;
             }
             umma_commit(empty(stage));
-            if (++stage == STAGES) {
-              stage = 0;
-              phase ^= 1u;
-            }
+            stage = stage + 1 == STAGES ? 0 : stage + 1;
+            phase ^= stage == 0 ? 1u : 0u;
           }
         }
       }
@@ -347,6 +343,7 @@ constexpr uint32_t P_STAGE = 32768;  // A 128 rows + B 128 columns, BK of K
 constexpr size_t P_SMEM = P_STAGES * P_STAGE + 1024 + 256;
 constexpr int P_HALF = 128;          // B columns per CTA
 
+template <int BF16>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
 hv_tc_pair_kernel(const __grid_constant__ CUtensorMap mHL, const __grid_constant__ CUtensorMap mHR,
                   const __grid_constant__ CUtensorMap mVk, const __grid_constant__ CUtensorMap mVm,
@@ -457,39 +454,35 @@ hv_tc_pair_kernel(const __grid_constant__ CUtensorMap mHL, const __grid_constant
         const int e0 = ph == 0 ? p.Lptr[c.i2] : p.Rptr[c.i3];
         const int e1 = ph == 0 ? p.Lptr[c.i2 + 1] : p.Rptr[c.i3 + 1];
         const int kb = ph == 0 ? p.kblk1 : p.kblk2;
+        // descriptor fields fixed for the phase (the A operand of phase 2 is V, MN-major)
+        const uint64_t a_hi = ph == 0 ? sdesc(0, 16, 1024)
+                                      : sdesc(0, p.a2_lbo, p.a2_sbo, p.a2_layout);
+        const uint32_t a_step = ph == 0 ? 32u : p.a2_kstep;
+        const uint64_t b_hi = sdesc(0, 16, 1024);
         for (int e = e0; e < e1 && ok; ++e) {
-          // instruction descriptor of this operator block, chosen once per block from
-          // statically indexed parameters (the issuing thread is on the critical path)
+          // instruction descriptor of this operator block, chosen once per block
           const int neg = p.pooled ? (ph == 0 ? p.k1[e].neg : p.k2[e].neg) : 0;
           const uint32_t idb = ph == 0 ? (neg ? p.idesc1[1] : p.idesc1[0])
                                        : (neg ? p.idesc2[1] : p.idesc2[0]);
           for (int kc = 0; kc < kb; ++kc) {
+            // the mbarrier's completion orders the TMA writes before these MMAs; no
+            // tcgen05 fence is needed per stage
             if (!mbar_wait(full(stage), phase, abort)) {
               raise_abort(abort, p.err, 13);
               ok = false;
               break;
             }
-            tc_fence_after();
             const uint32_t a_s = smem_u32(smem + stage * P_STAGE);
             const uint32_t b_s = a_s + P_STAGE_A;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-              uint64_t ad;
-              uint32_t id;
-              if (ph == 0) {
-                ad = sdesc(a_s + k * 32, 16, 1024);
-              } else {
-                ad = sdesc(a_s + k * p.a2_kstep, p.a2_lbo, p.a2_sbo, p.a2_layout);
-              }
-              id = idb;
-              umma_pair(dt, ad, sdesc(b_s + k * 32, 16, 1024), id, accum, p.bf16);
+              umma_pair_t<BF16>(dt, a_hi | sdesc_addr(a_s + k * a_step),
+                                b_hi | sdesc_addr(b_s + k * 32), idb, accum);
               accum = 1;
             }
             umma_commit_pair(empty(stage));
-            if (++stage == P_STAGES) {
-              stage = 0;
-              phase ^= 1u;
-            }
+            stage = stage + 1 == P_STAGES ? 0 : stage + 1;
+            phase ^= stage == 0 ? 1u : 0u;
           }
         }
       }
@@ -710,11 +703,15 @@ int tc_prepare(dmrg2d_ops* ops, cudaStream_t s, const std::vector<double>& HL,
       int dev = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&T->sms, cudaDevAttrMultiProcessorCount, dev);
-      if (cudaFuncSetAttribute(hv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      if (cudaFuncSetAttribute(hv_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)SMEM_BYTES) != cudaSuccess ||
+          cudaFuncSetAttribute(hv_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)SMEM_BYTES) != cudaSuccess ||
           (T->pair_ok &&
-           cudaFuncSetAttribute(hv_tc_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)P_SMEM) != cudaSuccess))
+           (cudaFuncSetAttribute(hv_tc_pair_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)P_SMEM) != cudaSuccess ||
+            cudaFuncSetAttribute(hv_tc_pair_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)P_SMEM) != cudaSuccess)))
         st = set_error(DMRG2D_ECUDA, "cannot set %zu bytes of shared memory", SMEM_BYTES);
       if (st == DMRG2D_OK && T->pair_ok) {
         cudaLaunchConfig_t cfg = {};
@@ -722,7 +719,7 @@ int tc_prepare(dmrg2d_ops* ops, cudaStream_t s, const std::vector<double>& HL,
         cfg.blockDim = dim3(TC_THREADS);
         cfg.dynamicSmemBytes = P_SMEM;
         int ncl = 0;
-        if (cudaOccupancyMaxActiveClusters(&ncl, hv_tc_pair_kernel, &cfg) != cudaSuccess) {
+        if (cudaOccupancyMaxActiveClusters(&ncl, hv_tc_pair_kernel<0>, &cfg) != cudaSuccess) {
           cudaGetLastError();
           ncl = 0;
         }
@@ -872,9 +869,16 @@ static int launch_dense_kernel(const dmrg2d_ops* ops, const TcState* T, const vo
   if (ev.first) D2_CUDA(cudaEventRecord(ev.first, s));
   if (pair) {
     const int pairs = std::min(p.tiles, T->pairs);
-    hv_tc_pair_kernel<<<2 * pairs, TC_THREADS, P_SMEM, s>>>(*mA, *mB, mVk, mVm, p);
+    if (bf)
+      hv_tc_pair_kernel<1><<<2 * pairs, TC_THREADS, P_SMEM, s>>>(*mA, *mB, mVk, mVm, p);
+    else
+      hv_tc_pair_kernel<0><<<2 * pairs, TC_THREADS, P_SMEM, s>>>(*mA, *mB, mVk, mVm, p);
   } else {
-    hv_tc_kernel<<<std::min(p.tiles, T->sms), TC_THREADS, SMEM_BYTES, s>>>(*mA, *mB, mVk, mVm, p);
+    const int grid = std::min(p.tiles, T->sms);
+    if (bf)
+      hv_tc_kernel<1><<<grid, TC_THREADS, SMEM_BYTES, s>>>(*mA, *mB, mVk, mVm, p);
+    else
+      hv_tc_kernel<0><<<grid, TC_THREADS, SMEM_BYTES, s>>>(*mA, *mB, mVk, mVm, p);
   }
   D2_CUDA(cudaGetLastError());
   if (ev.second) D2_CUDA(cudaEventRecord(ev.second, s));

@@ -69,19 +69,6 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
   d |= (uint64_t)layout << 61;
   return d;
 }
-__device__ __forceinline__ void umma(uint32_t dt, uint64_t a, uint64_t b, uint32_t idesc,
-                                     uint32_t acc, int bf16) {
-  if (bf16)
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
-  else
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                    bar)
@@ -147,11 +134,29 @@ __device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap
       "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
       : "memory");
 }
-// MMA over the pair: A rows and B columns split between the two CTAs' shared memory,
-// D rows split between their tensor memories (issued by the even CTA only)
-__device__ __forceinline__ void umma_pair(uint32_t dt, uint64_t a, uint64_t b, uint32_t idesc,
-                                          uint32_t acc, int bf16) {
-  if (bf16)
+// tcgen05.mma on one CTA (umma_t) or over a CTA pair (umma_pair_t: A rows and B columns
+// split between the two CTAs' shared memory, D rows between their tensor memories; issued
+// by the even CTA only).  The operand kind is fixed at compile time so that the issuing
+// thread runs no branch between MMAs: the tensor pipe's instruction queue is shallow, and
+// every instruction between two MMAs can leave it idle.
+template <int BF16>
+__device__ __forceinline__ void umma_t(uint32_t dt, uint64_t a, uint64_t b, uint32_t idesc,
+                                       uint32_t acc) {
+  if constexpr (BF16)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  else
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+template <int BF16>
+__device__ __forceinline__ void umma_pair_t(uint32_t dt, uint64_t a, uint64_t b, uint32_t idesc,
+                                            uint32_t acc) {
+  if constexpr (BF16)
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
@@ -161,6 +166,10 @@ __device__ __forceinline__ void umma_pair(uint32_t dt, uint64_t a, uint64_t b, u
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
         "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+// shared-memory address field of a descriptor (OR-ed into the fixed high fields)
+__device__ __forceinline__ uint64_t sdesc_addr(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu);
 }
 // arrive on the mbarrier at this offset in both CTAs once the issued MMAs complete
 __device__ __forceinline__ void umma_commit_pair(uint32_t bar) {
