@@ -232,7 +232,10 @@ int dmrg2d_lanczos_ground_noalloc(const dmrg2d_ops* ops, const dmrg2d_solver_opt
  * tensor-core instructions) in column-slab / blocked order, and 12 and 13 the same
  * reading the deduplicated operator pool; 14 + c (c = 0..5, sector-restricted
  * superblocks) is grouped configuration c with the scalar moves in a separate kernel
- * instead of the grouped kernel's epilogue.
+ * instead of the grouped kernel's epilogue; 20 and 21 are the dense kernel / CTA-pair
+ * kernel in two passes over the output: H_l V with the moves inside a block column and
+ * H_c in column-slab order, then V H_r^T with the moves inside a block row in row-slab
+ * order, added to the stored Y (each pass finds the V tiles it reads in L2).
  * dmrg2d_autotune times a complete H·v (scalar moves included) with every
  * configuration that applies (one warm-up and three timed launches each, on scratch
  * buffers it allocates and frees), keeps the fastest for later apply_H and solver

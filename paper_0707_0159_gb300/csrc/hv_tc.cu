@@ -67,6 +67,9 @@ struct TcParams {
   const GK1* k1;
   const GK2* k2;
   int poolL_rows, poolR_rows, copies;  // rows of one pool replica; replicas
+  // phases run by this launch: [ph0, ph1) of {0: H_l V, 1: V H_r^T}; accum_y: the
+  // epilogue adds the Y already stored (second pass of the two-pass form)
+  int ph0, ph1, accum_y;
   // scalar tile moves fused into the epilogue (H_c and off-diagonal column terms)
   int fuse;
   const void* v;
@@ -103,41 +106,51 @@ __device__ __forceinline__ void epilogue_piece(const TcParams& p, const TileCoor
 #pragma unroll
     for (int j = 0; j < 32; ++j) o[j] = __uint_as_float(v[j]);
     // scalar tile moves of this piece: Y(i2,i3) += c V(i2',i3') on the same rows and
-    // columns of the source tile; a warp reads 32 consecutive rows per column, two
-    // moves at a time to keep more loads in flight
-    for (int e = e0; e < e1; e += 2) {
-      const bool two = e + 1 < e1;
-      const int sa = p.Csrc[e], sb = two ? p.Csrc[e + 1] : sa;
-      const float ca = p.Cval[e], cb = two ? p.Cval[e + 1] : 0.f;
-      const int64_t ra = (int64_t)(sa % p.d) * p.m1 + mt * BM + row;
-      const int64_t rb = (int64_t)(sb % p.d) * p.m1 + mt * BM + row;
-      const int64_t ka = (int64_t)(sa / p.d) * p.m4 + (int64_t)c.nt * p.BN + ch * 32;
-      const int64_t kb = (int64_t)(sb / p.d) * p.m4 + (int64_t)c.nt * p.BN + ch * 32;
+    // columns of the source tile; a warp reads 32 consecutive rows per column, MV moves
+    // at a time (MV x 32 loads in flight per thread: the moves are bound by the loads in
+    // flight; four spill registers)
+    constexpr int MV = 3;
+    for (int e = e0; e < e1; e += MV) {
+      float cm[MV];
+      int64_t off[MV];
+#pragma unroll
+      for (int m = 0; m < MV; ++m) {
+        const bool have = e + m < e1;
+        const int sm = p.Csrc[have ? e + m : e];
+        cm[m] = have ? p.Cval[e + m] : 0.f;
+        const int64_t rm = (int64_t)(sm % p.d) * p.m1 + mt * BM + row;
+        const int64_t km = (int64_t)(sm / p.d) * p.m4 + (int64_t)c.nt * p.BN + ch * 32;
+        off[m] = rm + p.ld * km;
+      }
+      float vm[MV][32];
       if (p.bf16) {
-        const __nv_bfloat16* A = (const __nv_bfloat16*)p.v + ra + p.ld * ka;
-        const __nv_bfloat16* B = (const __nv_bfloat16*)p.v + rb + p.ld * kb;
-        float va[32], vb[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          va[j] = __bfloat162float(A[p.ld * j]);
-          vb[j] = __bfloat162float(B[p.ld * j]);
+        for (int m = 0; m < MV; ++m) {
+          const __nv_bfloat16* A = (const __nv_bfloat16*)p.v + off[m];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) vm[m][j] = __bfloat162float(A[p.ld * j]);
         }
-#pragma unroll
-        for (int j = 0; j < 32; ++j) o[j] += ca * va[j] + cb * vb[j];
       } else {
-        const float* A = (const float*)p.v + ra + p.ld * ka;
-        const float* B = (const float*)p.v + rb + p.ld * kb;
-        float va[32], vb[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          va[j] = __ldg(A + p.ld * j);
-          vb[j] = __ldg(B + p.ld * j);
+        for (int m = 0; m < MV; ++m) {
+          const float* A = (const float*)p.v + off[m];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) vm[m][j] = __ldg(A + p.ld * j);
         }
+      }
 #pragma unroll
-        for (int j = 0; j < 32; ++j) o[j] += ca * va[j] + cb * vb[j];
+      for (int j = 0; j < 32; ++j) {
+        float s = o[j];
+#pragma unroll
+        for (int m = 0; m < MV; ++m) s = fmaf(cm[m], vm[m][j], s);
+        o[j] = s;
       }
     }
     float* yp = p.y + r + p.ld * (col0 + ch * 32);
+    if (p.accum_y) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) o[j] += yp[p.ld * j];
+    }
 #pragma unroll
     for (int j = 0; j < 32; ++j) yp[p.ld * j] = o[j];
   }
@@ -192,7 +205,7 @@ hv_tc_kernel(const __grid_constant__ CUtensorMap mHL, const __grid_constant__ CU
       const TileCoord c = decode(p, t);
       const int r0 = c.i2 * p.m1 + c.mt * BM;
       const int c0 = c.i3 * p.m4 + c.nt * p.BN;
-      for (int ph = 0; ph < 2; ++ph) {
+      for (int ph = p.ph0; ph < p.ph1; ++ph) {
         const int e0 = ph == 0 ? p.Lptr[c.i2] : p.Rptr[c.i3];
         const int e1 = ph == 0 ? p.Lptr[c.i2 + 1] : p.Rptr[c.i3 + 1];
         const int kb = ph == 0 ? p.kblk1 : p.kblk2;
@@ -246,7 +259,7 @@ hv_tc_kernel(const __grid_constant__ CUtensorMap mHL, const __grid_constant__ CU
       const uint32_t dt = tmem_base + acc * ACC_COLS;
       uint32_t accum = 0;
       bool ok = true;
-      for (int ph = 0; ph < 2 && ok; ++ph) {
+      for (int ph = p.ph0; ph < p.ph1 && ok; ++ph) {
         const int e0 = ph == 0 ? p.Lptr[c.i2] : p.Rptr[c.i3];
         const int e1 = ph == 0 ? p.Lptr[c.i2 + 1] : p.Rptr[c.i3 + 1];
         const int kb = ph == 0 ? p.kblk1 : p.kblk2;
@@ -397,7 +410,7 @@ hv_tc_pair_kernel(const __grid_constant__ CUtensorMap mHL, const __grid_constant
       const int mt = 2 * c.mt + (int)rank;
       const int r0 = c.i2 * p.m1 + mt * BM;
       const int cb = c.nt * p.BN + (int)rank * P_HALF;  // this CTA's B columns
-      for (int ph = 0; ph < 2; ++ph) {
+      for (int ph = p.ph0; ph < p.ph1; ++ph) {
         const int e0 = ph == 0 ? p.Lptr[c.i2] : p.Rptr[c.i3];
         const int e1 = ph == 0 ? p.Lptr[c.i2 + 1] : p.Rptr[c.i3 + 1];
         const int kb = ph == 0 ? p.kblk1 : p.kblk2;
@@ -450,7 +463,7 @@ hv_tc_pair_kernel(const __grid_constant__ CUtensorMap mHL, const __grid_constant
       const uint32_t dt = tmem_base + acc * ACC_COLS;
       uint32_t accum = 0;
       bool ok = true;
-      for (int ph = 0; ph < 2 && ok; ++ph) {
+      for (int ph = p.ph0; ph < p.ph1 && ok; ++ph) {
         const int e0 = ph == 0 ? p.Lptr[c.i2] : p.Rptr[c.i3];
         const int e1 = ph == 0 ? p.Lptr[c.i2 + 1] : p.Rptr[c.i3 + 1];
         const int kb = ph == 0 ? p.kblk1 : p.kblk2;
@@ -552,6 +565,13 @@ struct TcState {
   int* err = nullptr;
   int* order = nullptr;   // blocked piece order of the dense kernel
   int* order2 = nullptr;  // the same for the CTA-pair kernel (256-row pieces)
+  // two-pass form: pass A (H_l V, column-slab order) and pass B (V H_r^T, row-slab
+  // order), for 128-row pieces [0] and CTA-pair pieces [1]; the scalar moves split so
+  // that each pass reads the sources its order keeps in L2
+  int* orderA[2] = {nullptr, nullptr};
+  int* orderB[2] = {nullptr, nullptr};
+  int *CptrA = nullptr, *CsrcA = nullptr, *CptrB = nullptr, *CsrcB = nullptr;
+  float *CvalA = nullptr, *CvalB = nullptr;
   bool pair_ok = false;   // CTA-pair kernel applies (m1 % 256 == 0, 256-wide pieces)
   int pairs = 0;          // CTA pairs resident at once (persistent grid of the pair kernel)
   CUtensorMap mHR2[2];    // H_r blocks in 128-row boxes (half a piece's columns)
@@ -639,6 +659,27 @@ std::vector<int> blocked_order(int d, int n_mt, int n_nt, int B) {
   return out;
 }
 
+// Orders of the two-pass form (column-slab numbers, as blocked_order).  Pass A walks one
+// block column i3 at a time (all pieces of the column, so H_l V reads each V tile of the
+// column from L2 once it is there); pass B walks one block row i2 at a time.  Columns
+// (rows) follow a Gray code when d is a power of two, so consecutive slabs differ in one
+// bit of the state label and share the sources of the moves between slabs.
+std::vector<int> slab_order(int d, int n_mt, int n_nt, bool columns) {
+  const bool pow2 = (d & (d - 1)) == 0;
+  std::vector<int> out;
+  out.reserve((size_t)d * n_mt * d * n_nt);
+  for (int a = 0; a < d; ++a) {
+    const int s = pow2 ? (a ^ (a >> 1)) : a;
+    for (int b = 0; b < d; ++b) {
+      const int i2 = columns ? b : s, i3 = columns ? s : b;
+      for (int nt = 0; nt < n_nt; ++nt)
+        for (int mt = 0; mt < n_mt; ++mt)
+          out.push_back(i2 * n_mt + mt + d * n_mt * (i3 * n_nt + nt));
+    }
+  }
+  return out;
+}
+
 }  // namespace
 
 int tc_prepare(dmrg2d_ops* ops, cudaStream_t s, const std::vector<double>& HL,
@@ -699,6 +740,48 @@ int tc_prepare(dmrg2d_ops* ops, cudaStream_t s, const std::vector<double>& HL,
     };
     upload_order(&T->order, m1 / BM);
     if (T->pair_ok) upload_order(&T->order2, m1 / 256);
+    // two-pass form: slab orders and the moves split by pass (same column: pass A,
+    // same row: pass B, the rest (H_c between the two columns): pass A)
+    auto upload_ints = [&](int** dst, const std::vector<int>& h) {
+      alloc((void**)dst, sizeof(int) * std::max<size_t>(h.size(), 1));
+      if (st == DMRG2D_OK && !h.empty() &&
+          cudaMemcpy(*dst, h.data(), sizeof(int) * h.size(), cudaMemcpyHostToDevice) !=
+              cudaSuccess)
+        st = set_error(DMRG2D_ECUDA, "upload failed");
+    };
+    for (int k = 0; k < 2; ++k) {
+      if (k == 1 && !T->pair_ok) break;
+      const int pieces = k ? m1 / 256 : m1 / BM;
+      upload_ints(&T->orderA[k], slab_order(d, pieces, m4 / T->BN, true));
+      upload_ints(&T->orderB[k], slab_order(d, pieces, m4 / T->BN, false));
+    }
+    {
+      std::vector<int> pa(1, 0), pb(1, 0), sa, sb;
+      std::vector<float> va, vb;
+      for (int tt = 0; tt < d * d; ++tt) {
+        const int i2 = tt % d;
+        for (int e = ops->hCptr[tt]; e < ops->hCptr[tt + 1]; ++e) {
+          const int src = ops->hCsrc[e];
+          const bool row = src % d == i2 && src / d != tt / d;  // same block row: pass B
+          (row ? sb : sa).push_back(src);
+          (row ? vb : va).push_back((float)ops->hCval[e]);
+        }
+        pa.push_back((int)sa.size());
+        pb.push_back((int)sb.size());
+      }
+      upload_ints(&T->CptrA, pa);
+      upload_ints(&T->CptrB, pb);
+      upload_ints(&T->CsrcA, sa);
+      upload_ints(&T->CsrcB, sb);
+      alloc((void**)&T->CvalA, sizeof(float) * std::max<size_t>(va.size(), 1));
+      alloc((void**)&T->CvalB, sizeof(float) * std::max<size_t>(vb.size(), 1));
+      if (st == DMRG2D_OK &&
+          ((!va.empty() && cudaMemcpy(T->CvalA, va.data(), sizeof(float) * va.size(),
+                                      cudaMemcpyHostToDevice) != cudaSuccess) ||
+           (!vb.empty() && cudaMemcpy(T->CvalB, vb.data(), sizeof(float) * vb.size(),
+                                      cudaMemcpyHostToDevice) != cudaSuccess)))
+        st = set_error(DMRG2D_ECUDA, "upload failed");
+    }
     if (st == DMRG2D_OK) {
       int dev = 0;
       cudaGetDevice(&dev);
@@ -790,6 +873,13 @@ void tc_release(dmrg2d_ops* ops) {
   if (T->err) cudaFree(T->err);
   if (T->order) cudaFree(T->order);
   if (T->order2) cudaFree(T->order2);
+  for (int k = 0; k < 2; ++k) {
+    if (T->orderA[k]) cudaFree(T->orderA[k]);
+    if (T->orderB[k]) cudaFree(T->orderB[k]);
+  }
+  for (void* q : {(void*)T->CptrA, (void*)T->CsrcA, (void*)T->CvalA, (void*)T->CptrB,
+                  (void*)T->CsrcB, (void*)T->CvalB})
+    if (q) cudaFree(q);
   if (T->plan) {
     gp_release(T->plan);
     delete T->plan;
@@ -799,12 +889,15 @@ void tc_release(dmrg2d_ops* ops) {
 }
 
 // dense-kernel variants: tc_cfg = -1 - variant, variant bit 0 = operator pool, bit 1 =
-// blocked piece order, bit 2 = CTA-pair kernel; autotuner index 0 / 7 / 8 / 9 / 10 / 11 /
-// 12 / 13 = variant 0 / 1 / 2 / 3 / 4 / 6 / 5 / 7
+// blocked piece order, bit 2 = CTA-pair kernel, bit 3 = two passes (H_l V with the moves
+// of the same column and H_c in column-slab order, then V H_r^T with the moves of the
+// same row in row-slab order, adding to the stored Y); autotuner index 0 / 7 / 8 / 9 /
+// 10 / 11 / 12 / 13 / 20 / 21 = variant 0 / 1 / 2 / 3 / 4 / 6 / 5 / 7 / 8 / 12
 static int launch_dense_kernel(const dmrg2d_ops* ops, const TcState* T, const void* v, float* y,
                                bool bf, bool fuse_moves, int variant, cudaStream_t s) {
   const bool pair = (variant & 4) != 0;
   const bool use_pool = (variant & 1) != 0;
+  const bool two = (variant & 8) != 0;
   const int b = bf ? 1 : 0;
   const int m1 = ops->m1, m4 = ops->m4, d = ops->d;
   const uint32_t BK = bf ? 64 : 32;
@@ -817,6 +910,9 @@ static int launch_dense_kernel(const dmrg2d_ops* ops, const TcState* T, const vo
   p.n_nt = m4 / T->BN;
   p.tiles = d * p.n_mt * d * p.n_nt;
   p.order = (variant & 2) ? (pair ? T->order2 : T->order) : nullptr;
+  p.ph0 = 0;
+  p.ph1 = 2;
+  p.accum_y = 0;
   p.BK = (int)BK;
   p.kblk1 = m1 / (int)BK;
   p.kblk2 = m4 / (int)BK;
@@ -867,18 +963,38 @@ static int launch_dense_kernel(const dmrg2d_ops* ops, const TcState* T, const vo
                   bf ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B));
   auto ev = prof_slot(ops);
   if (ev.first) D2_CUDA(cudaEventRecord(ev.first, s));
-  if (pair) {
-    const int pairs = std::min(p.tiles, T->pairs);
-    if (bf)
-      hv_tc_pair_kernel<1><<<2 * pairs, TC_THREADS, P_SMEM, s>>>(*mA, *mB, mVk, mVm, p);
-    else
-      hv_tc_pair_kernel<0><<<2 * pairs, TC_THREADS, P_SMEM, s>>>(*mA, *mB, mVk, mVm, p);
+  auto launch = [&](const TcParams& q) {
+    if (pair) {
+      const int pairs = std::min(q.tiles, T->pairs);
+      if (bf)
+        hv_tc_pair_kernel<1><<<2 * pairs, TC_THREADS, P_SMEM, s>>>(*mA, *mB, mVk, mVm, q);
+      else
+        hv_tc_pair_kernel<0><<<2 * pairs, TC_THREADS, P_SMEM, s>>>(*mA, *mB, mVk, mVm, q);
+    } else {
+      const int grid = std::min(q.tiles, T->sms);
+      if (bf)
+        hv_tc_kernel<1><<<grid, TC_THREADS, SMEM_BYTES, s>>>(*mA, *mB, mVk, mVm, q);
+      else
+        hv_tc_kernel<0><<<grid, TC_THREADS, SMEM_BYTES, s>>>(*mA, *mB, mVk, mVm, q);
+    }
+  };
+  if (two) {
+    TcParams a = p, b2 = p;
+    a.order = T->orderA[pair ? 1 : 0];
+    a.ph1 = 1;
+    a.Cptr = T->CptrA;
+    a.Csrc = T->CsrcA;
+    a.Cval = T->CvalA;
+    b2.order = T->orderB[pair ? 1 : 0];
+    b2.ph0 = 1;
+    b2.accum_y = 1;
+    b2.Cptr = T->CptrB;
+    b2.Csrc = T->CsrcB;
+    b2.Cval = T->CvalB;
+    launch(a);
+    launch(b2);
   } else {
-    const int grid = std::min(p.tiles, T->sms);
-    if (bf)
-      hv_tc_kernel<1><<<grid, TC_THREADS, SMEM_BYTES, s>>>(*mA, *mB, mVk, mVm, p);
-    else
-      hv_tc_kernel<0><<<grid, TC_THREADS, SMEM_BYTES, s>>>(*mA, *mB, mVk, mVm, p);
+    launch(p);
   }
   D2_CUDA(cudaGetLastError());
   if (ev.second) D2_CUDA(cudaEventRecord(ev.second, s));
@@ -936,18 +1052,21 @@ namespace dmrg2d {
 // kernel reading the deduplicated (replicated) operator pool, 8 / 9 = dense kernel in the
 // blocked piece order (per-position blocks / pool)
 // 14 + c = grouped configuration c with the scalar moves in a separate kernel (sectors)
-constexpr int N_CANDIDATES = 20;
+// 20 / 21 = two-pass dense kernel (128-row pieces / CTA pairs)
+constexpr int N_CANDIDATES = 22;
 static int idx_to_cfg(int idx) {
   static const int dense_variant[14] = {0, -1, -1, -1, -1, -1, -1, 1, 2, 3, 4, 6, 5, 7};
   if (idx >= 1 && idx <= 6) return idx - 1;
+  if (idx == 20) return -1 - 8;
+  if (idx == 21) return -1 - 12;
   if (idx >= 14) return gp_num_configs() + idx - 14;
   return -1 - dense_variant[idx];
 }
 
 static bool tc_candidate_ok(const dmrg2d_ops* ops, int idx) {
   if (idx < 0 || idx >= N_CANDIDATES) return false;
-  if (idx >= 14) return ops->sec && ops->tc_ok;  // grouped, separate moves: sectors only
-  if (idx == 0 || idx >= 7) {                    // dense-kernel variants
+  if (idx >= 14 && idx < 20) return ops->sec && ops->tc_ok;  // grouped, separate moves
+  if (idx == 0 || idx >= 7) {                                // dense-kernel variants
     const TcState* T = (const TcState*)ops->tc;
     if (ops->sec || !T || !T->dense_ok) return false;
     const int variant = -1 - idx_to_cfg(idx);
@@ -983,6 +1102,8 @@ extern "C" const char* dmrg2d_tile_config_name(int index) {
   if (index == 11) return "CTA-pair kernel 256x256 (8x8-tile blocked raster)";
   if (index == 12) return "CTA-pair kernel 256x256 (column-slab raster), operator pool";
   if (index == 13) return "CTA-pair kernel 256x256 (8x8-tile blocked raster), operator pool";
+  if (index == 20) return "dense kernel 128x256, two passes (H_l V by column slabs, V H_r^T by row slabs)";
+  if (index == 21) return "CTA-pair kernel 256x256, two passes (H_l V by column slabs, V H_r^T by row slabs)";
   static const char* sep[6] = {
       "grouped 128x128 column-slab, separate moves kernel",
       "grouped 128x128 row-slab, separate moves kernel",

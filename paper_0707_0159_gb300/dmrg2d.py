@@ -284,7 +284,7 @@ def profile_stop(ops: Ops):
     return ms.value, n.value
 
 
-N_TILE_CONFIGS = 20
+N_TILE_CONFIGS = 22
 
 
 def autotune(ops: Ops, precision, stream=None):

@@ -65,21 +65,23 @@ def test_dense_and_grouped_kernels_agree(prec):
     v = synth.start_vector(sb.n_vec, 4)
     ref = sb.apply(v)
     out = {}
-    for cfg in (0, 1, 4, 7, 8, 9):
+    for cfg in (0, 1, 4, 7, 8, 9, 20):
         dmrg2d.set_tile_config(ops, prec, cfg)
         out[cfg] = run(ops, v, prec)
         assert rel(out[cfg], ref) <= TOL[prec]
     # same operands, same K order within a piece: the kernels agree far below the tolerance
-    for cfg in (1, 4, 7, 8, 9):
-        assert rel(out[cfg], out[0]) <= 1e-6, cfg
+    # (config 20, two passes, rounds the first pass's partial sum to FP32 once more)
+    for cfg in (1, 4, 7, 8, 9, 20):
+        assert rel(out[cfg], out[0]) <= (2e-5 if cfg == 20 else 1e-6), cfg
 
 
 @pytest.mark.parametrize("case", [("heisenberg", 3, 256, 256), ("hubbard", 1, 512, 512),
                                   ("heisenberg", 2, 256, 512)])
 @pytest.mark.parametrize("prec", [dmrg2d.TF32, dmrg2d.BF16])
 def test_cta_pair_kernel_matches_oracle_and_dense(case, prec):
-    """The CTA-pair kernel (configs 10 to 13) on shapes with one and two 256-row piece
-    pairs per block row and one and two 256-column pieces per block column."""
+    """The CTA-pair kernel (configs 10 to 13, and 21 in two passes; 20 is the two-pass
+    dense kernel) on shapes with one and two 256-row piece pairs per block row and one and
+    two 256-column pieces per block column."""
     mdl, left, right = make(*case)
     ops = dmrg2d.build_ops(mdl, left, right)
     sb = Superblock(mdl, left, right)
@@ -87,11 +89,11 @@ def test_cta_pair_kernel_matches_oracle_and_dense(case, prec):
     ref = sb.apply(v)
     dmrg2d.set_tile_config(ops, prec, 0)
     y0 = run(ops, v, prec)
-    for cfg in (10, 11, 12, 13):  # per-position operator blocks / deduplicated pool
+    for cfg in (10, 11, 12, 13, 20, 21):  # per-position blocks / pool / two passes
         dmrg2d.set_tile_config(ops, prec, cfg)
         y = run(ops, v, prec)
         assert rel(y, ref) <= TOL[prec], (cfg, rel(y, ref))
-        assert rel(y, y0) <= 1e-6, cfg
+        assert rel(y, y0) <= (2e-5 if cfg >= 20 else 1e-6), cfg
 
 
 CASES = {
@@ -129,7 +131,7 @@ def test_autotune_picks_a_working_config(prec):
     ops = dmrg2d.build_ops(mdl, left, right, target=target)
     best, ms = dmrg2d.autotune(ops, prec)
     assert 1 <= best < 7 or 14 <= best < 20
-    assert all(ms[i] == -1.0 for i in (0, 7, 8, 9, 10, 11, 12, 13))
+    assert all(ms[i] == -1.0 for i in (0, 7, 8, 9, 10, 11, 12, 13, 20, 21))
     assert all(t > 0 for t in ms[1:7] + ms[14:20])
     assert ms[best] == min(t for t in ms if t > 0)
     sb = Superblock(mdl, left, right)
