@@ -420,6 +420,25 @@ typedef struct dmrg2d_sweep_report {
 int dmrg2d_sweep(const dmrg2d_model* model, const dmrg2d_sweep_opts* opts,
                  dmrg2d_sweep_report* report, void* stream);
 
+/* Site densities of the two central columns of a superblock state: the observables of
+ * the paper's Hubbard study, hole density h(x,y) = 1 - <n_{x,y,up} + n_{x,y,dn}> (its
+ * Eq. (hole)) and staggered spin density s(x,y) = <n_{x,y,up} - n_{x,y,dn}> (which the
+ * Lieb-Mattis theorem makes vanish on every site of the finite ladder's ground state),
+ * with S(x) = max_y |s(x,y)|.  A DMRG step measures the sites of columns 2 and 3, which
+ * one superblock holds exactly.
+ *   x:   device, FP64, n_vec elements in the layout of ops (dense, or the packed sector
+ *        layout of a sector-restricted ops; padding rows are ignored); not modified and
+ *        need not be normalised (the densities are divided by <x|x>).
+ *   out: device, 8 n_legs + 2 doubles, written: out[4 (c n_legs + y) + k] for column
+ *        c = 0 (block 2) / 1 (block 3), leg y, k = 0 n_up, 1 n_dn, 2 h, 3 s; then
+ *        out[8 n_legs + c] = S(c).  For a spin model n_up / n_dn are the probabilities
+ *        of up / down on the site (h = 0, s = 2 <S^z>).
+ * One pass over x bins |x|^2 by each element's column states (i2, i3); the occupation
+ * numbers are diagonal in the column basis.  The call allocates small scratch
+ * (layout tables and 2 d bins) and synchronises the stream.  Errors: EINVAL on a NULL
+ * argument; ENOMEM / ECUDA from the allocation or launches. */
+int dmrg2d_site_densities(const dmrg2d_ops* ops, const double* x, double* out, void* stream);
+
 /* Thread-local text of the last error of this thread ("" if none). */
 const char* dmrg2d_last_error(void);
 

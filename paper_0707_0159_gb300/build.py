@@ -13,7 +13,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libdmrg2d.so")
 SOURCES = ["build_ops.cu", "hv_simt.cu", "hv_tc.cu", "grouped.cu", "sectors.cu", "diag.cu", "mlp.cu",
-           "solver.cu", "sweep.cu"]
+           "solver.cu", "sweep.cu", "densities.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
          "-I", os.path.join(ROOT, "include")]

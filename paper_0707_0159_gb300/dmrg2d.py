@@ -128,6 +128,7 @@ SIGNATURES = {
     "dmrg2d_check_device": (C.c_int, [C.c_void_p]),
     "dmrg2d_profile_start": (C.c_int, [C.c_void_p, C.c_int]),
     "dmrg2d_profile_stop": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
+    "dmrg2d_site_densities": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dmrg2d_last_error": (C.c_char_p, []),
     "dmrg2d_version": (C.c_char_p, []),
 }
@@ -361,6 +362,23 @@ def lanczos_ground_noalloc(ops: Ops, x, stream=None, **opts):
 
 
 PRECOND = {"none": 0, "jacobi": 1, "mlp": 2}
+
+
+def site_densities(ops: Ops, x, stream=None) -> dict:
+    """Densities of the two central columns' sites for the state x (CUDA float64, n_vec):
+    n[c, y, s] (c = 0 column 2, 1 column 3; s = 0 up, 1 down), hole density h[c, y],
+    staggered spin density sd[c, y] and S[c] = max_y |sd[c, y]| (dmrg2d_site_densities)."""
+    import torch
+    if not x.is_cuda or str(x.dtype) != "torch.float64" or x.numel() != ops.info["n_vec"]:
+        raise ValueError("x must be a CUDA float64 tensor of n_vec elements")
+    nl = ops.info["n_legs"]
+    out = torch.empty(8 * nl + 2, dtype=torch.float64, device=x.device)
+    _check(lib().dmrg2d_site_densities(ops.ptr, C.c_void_p(x.data_ptr()),
+                                       C.c_void_p(out.data_ptr()), _stream(stream)))
+    o = out.cpu().numpy()
+    per = o[:8 * nl].reshape(2, nl, 4)
+    return {"n": per[..., :2].copy(), "h": per[..., 2].copy(), "sd": per[..., 3].copy(),
+            "S": o[8 * nl:].copy()}
 
 
 def diagonal(ops: Ops, out, stream=None):
