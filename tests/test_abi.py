@@ -90,3 +90,11 @@ def test_sweep_rejects_bad_options(lib):
     with pytest.raises(dmrg2d.Dmrg2dError) as e:
         dmrg2d.sweep(hub, 6, 8, [8])
     assert e.value.code == -8
+
+
+def test_site_densities_rejects_null_arguments(lib):
+    import ctypes
+    assert lib.dmrg2d_site_densities(None, None, None, None) == -1      # EINVAL, no device work
+    assert "NULL" in lib.dmrg2d_last_error().decode()
+    buf = (ctypes.c_double * 4)()
+    assert lib.dmrg2d_site_densities(None, buf, buf, None) == -1
