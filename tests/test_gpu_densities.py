@@ -26,12 +26,15 @@ def close(got, ref, atol):
 
 
 @pytest.mark.parametrize("case", [("hubbard", 2, 33, 20), ("hubbard", 3, 8, 5),
-                                  ("heisenberg", 3, 40, 24), ("heisenberg", 4, 17, 9)])
+                                  ("heisenberg", 3, 40, 24), ("heisenberg", 4, 17, 9),
+                                  ("hubbard", 2, 1, 1), ("heisenberg", 2, 1, 6)])
 def test_dense_random_vector(case):
+    """Including the lattice ends: one-state blocks without boundary operators."""
     kind, nl, m1, m4 = case
     mdl = synth.model(kind, nl, J_leg=0.8, J_rung=1.1, t=1.0, U=6.0)
     mk = synth.heisenberg_block if kind == "heisenberg" else synth.hubbard_block
-    left, right = mk(m1, nl, 1), mk(m4, nl, 2)
+    left = mk(m1, nl, 1) if m1 > 1 else synth.empty_block(kind)
+    right = mk(m4, nl, 2) if m4 > 1 else synth.empty_block(kind)
     ops = dmrg2d.build_ops(mdl, left, right)
     sb = Superblock(mdl, left, right)
     x = synth.start_vector(sb.n_vec, 9)
