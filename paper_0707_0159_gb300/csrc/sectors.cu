@@ -1,6 +1,6 @@
 // Sector-restricted superblock H·v: quantum-number blocks of uneven size as one grouped
-// launch (the paper's blocks carry conserved quantum numbers but it
-// does not describe their use in H·v).
+// launch (the paper's blocks carry conserved quantum numbers, but it does not describe
+// their use in H·v).
 //
 // Packed vector layout (also in include/dmrg2d.h): for every combined left label qL
 // (block-1 label + column-2 label), in increasing lexicographic order, one column-major
