@@ -357,12 +357,18 @@ void dmrg2d_free_ops(dmrg2d_ops* ops);
  * grows block 1 and its mirror image block 4 together until the superblock spans the
  * lattice; each finite sweep then moves to the right end, to the left end and back to
  * the middle.
- * Supported: Heisenberg ladders (model->kind == DMRG2D_HEISENBERG), open along the
- * legs, n_columns even and >= 4; dense superblocks, or (use_sectors) the S^z_tot = 0
- * sector: blocks carry their states' N_up (grouped by label), the superblock H·v runs
- * on the sector-restricted layout, and the density matrix, block diagonal in the
- * growing half's label, is diagonalised sector by sector (dsyevd), keeping the m
- * largest eigenvalues over all sectors.
+ * Supported: Heisenberg ladders (model->kind == DMRG2D_HEISENBERG, n_legs <= 8), open
+ * along the legs, n_columns even and >= 4; dense superblocks, or (use_sectors) the
+ * S^z_tot = 0 sector: blocks carry their states' N_up (grouped by label), the superblock
+ * H·v runs on the sector-restricted layout, and the density matrix, block diagonal in
+ * the growing half's label, is diagonalised sector by sector (dsyevd), keeping the m
+ * largest eigenvalues over all sectors.  Hubbard ladders (DMRG2D_HUBBARD, n_legs <= 4,
+ * use_sectors = 1, else EUNSUPPORTED): the target sector is (n_up, n_dn) electrons on
+ * the whole ladder (on the warm-up's smaller superblocks the same filling per column,
+ * rounded half up); blocks carry the creation operators of their boundary column, their
+ * parity and (N_up, N_dn) labels; block 4 grows from its own density matrix during the
+ * warm-up (a mirrored fermion block would have the reversed mode order); every step
+ * records the site densities of its central columns (report->densities).
  * Density matrices and their eigenvectors are FP64 on the GPU (cuBLAS DSYRK, cuSOLVER
  * dsyevd); ties in the density-matrix spectrum keep the eigenvectors dsyevd returns last.
  * Ground states: `precision` FP64 runs the plain Lanczos; TF32/BF16 the mixed solver
@@ -389,6 +395,7 @@ typedef struct dmrg2d_sweep_opts {
   uint64_t seed;       /* start vectors                                               */
   int use_sectors;     /* 1: S^z_tot = 0 sector-restricted superblocks (blocks carry  */
                        /*    N_up labels, density matrices per sector)               */
+  int n_up, n_dn;      /* Hubbard ladders: electrons of each spin on the whole ladder */
 } dmrg2d_sweep_opts;
 
 typedef struct dmrg2d_sweep_report {
@@ -409,6 +416,11 @@ typedef struct dmrg2d_sweep_report {
   double* leg_bond;
   double* rung_bond;
   double* s2;
+  /* Hubbard ladders: the site densities of the two central columns of each step's
+   * ground state, densities[step * (8 n_legs + 2) + ...] in the layout of
+   * dmrg2d_site_densities (n_up, n_dn, hole density, staggered spin density per site;
+   * then S(x) of both columns).  May be NULL. */
+  double* densities;
   double seconds;      /* wall time of the call, of which:                            */
   double solve_seconds;/*   ground-state solves (dmrg2d_lanczos_ground)              */
   double build_seconds;/*   superblock operator assembly (dmrg2d_build_ops)          */

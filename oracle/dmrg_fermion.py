@@ -109,8 +109,8 @@ def sector_ground(sb: Superblock, target, seed: int = 0, tol: float = 1e-12):
 
 
 def dmrg(mdl: dict, L: int, n_up: int, n_dn: int, m_warmup: int, m_sweeps: list) -> dict:
-    """Warm-up growing both blocks (superblocks of 4, 6, ... columns at the nearest
-    proportional filling), then one finite sweep per entry of m_sweeps on the L-column
+    """Warm-up growing both blocks (superblocks of 4, 6, ... columns at the proportional
+    filling rounded half up), then one finite sweep per entry of m_sweeps on the L-column
     ladder at (n_up, n_dn).  L even, L >= 4.  Records per step the energy, truncation
     error, position l (columns in block 1), sweep (-1: warm-up) and the site densities of
     columns l and l + 1 (0-based)."""
@@ -128,7 +128,9 @@ def dmrg(mdl: dict, L: int, n_up: int, n_dn: int, m_warmup: int, m_sweeps: list)
             out[k].append(dens[k])
 
     def target_for(cols):
-        return (int(round(n_up * cols / L)), int(round(n_dn * cols / L)))
+        # the ladder's filling on a superblock of fewer columns, rounded half up (the
+        # paper does not say how the warm-up fills its smaller lattices)
+        return (int(np.floor(n_up * cols / L + 0.5)), int(np.floor(n_dn * cols / L + 0.5)))
 
     one = exact_column_block(mdl)
     left = {1: one}

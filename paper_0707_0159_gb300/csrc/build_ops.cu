@@ -201,6 +201,16 @@ void spin_column_ops(int n, double J_rung, bool pbc, SpinColumnOps* out) {
   out->sp = c.sp;
 }
 
+void hubbard_column_ops(int n, double t, double U, bool pbc, HubbardColumnOps* out) {
+  const Column c = hubbard_column(n, t, U, pbc);
+  out->d = c.d;
+  out->H = c.H;
+  out->cd = c.cd;
+  out->parity = c.parity;
+  out->nup = c.nup;
+  out->ndn = c.ndn;
+}
+
 // Assemble the packed operators on the host.
 static int assemble(const dmrg2d_model* M, const dmrg2d_block* L, const dmrg2d_block* R,
                     dmrg2d_ops* ops, std::vector<double>& HL, std::vector<double>& HR) {

@@ -20,6 +20,17 @@ struct SpinColumnOps {
   std::vector<std::vector<double>> sz, sp;   // per leg: S^z_y, S^+_y
 };
 void spin_column_ops(int n, double J_rung, bool pbc, SpinColumnOps* out);
+// exact Hubbard column: rung hopping + on-site U; c^dag of mode j = 2y + s (with the
+// in-column string), the parity (-1)^N and the (N_up, N_dn) of every state (bit j of a
+// state index is the occupation of mode j)
+struct HubbardColumnOps {
+  int d = 0;
+  std::vector<double> H;
+  std::vector<std::vector<double>> cd;
+  std::vector<double> parity;
+  std::vector<int> nup, ndn;
+};
+void hubbard_column_ops(int n, double t, double U, bool pbc, HubbardColumnOps* out);
 
 // ---- error reporting (thread-local message, negative status codes) --------------------
 int set_error(int code, const char* fmt, ...);

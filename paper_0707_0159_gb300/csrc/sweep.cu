@@ -1,5 +1,6 @@
 // Finite-system direct 2-D DMRG around the superblock H·v (paper: the algorithm around
-// Fig. 2) for Heisenberg ladders without quantum-number sectors.
+// Fig. 2) for Heisenberg ladders (dense, or in the S^z_tot = 0 sector) and Hubbard
+// ladders (in a target (N_up, N_dn) sector).
 //
 // One step: the superblock block 1 + column 2 + column 3 + block 4 is built from the
 // stored blocks (dmrg2d_build_ops), its ground state found on the GPU
@@ -8,7 +9,9 @@
 // or rho_R = V^T V over columns i4 + m4 i3; cuBLAS DSYRK, FP64) and diagonalised
 // (cuSOLVER dsyevd, FP64).  Its m leading eigenvectors U (n x k, n = m d) define the new
 // block: H' = U^T H_enl U and, per leg, the boundary operators U^T (X (x) 1) U of the
-// added column.  H_enl is never formed: with U viewed as k matrices W_j (m x d, block
+// added column (Hubbard: its creation operators, carrying the parity of the modes before
+// them in the block's mode order).  H_enl is never formed: with U viewed as k matrices
+// W_j (m x d, block
 // index fast), (X (x) 1) U is W_j X^T for every j (one strided-batched DGEMM) and
 // (1 (x) Y) U is Y [W_0 ... W_k-1] (one DGEMM).  New blocks are copied back to the host
 // (k x k), where the next dmrg2d_build_ops reads them.
@@ -55,8 +58,10 @@ struct Block {
   int m_prev = 0;
   std::shared_ptr<DBuf> U;
   int cols = 1;                 // lattice columns in the block
-  std::vector<int32_t> qn;      // sectors: N_up of each state, equal labels contiguous
+  std::vector<int32_t> qn;      // sectors: N_up (Hubbard: N_up, N_dn) of each state,
+                                // equal labels contiguous
   Mat Sz_tot, Sp_tot;           // the block's total S^z and S^+ (for <S_tot^2>)
+  Mat parity;                   // Hubbard: (-1)^N of each state
 };
 
 struct IBuf {  // device int64 / int32 arrays for the sector maps
@@ -179,7 +184,16 @@ class Sweeper {
       : M_(*M), o_(*o), rep_(rep), strm_(s), rng_(o->seed) {}
 
   int run() {
-    spin_column_ops(M_.n_legs, M_.J_rung, M_.rung_pbc != 0, &col_);
+    hub_ = M_.kind == DMRG2D_HUBBARD;
+    if (hub_) {  // the spin operators stay empty: every per-leg spin loop below is skipped
+      hubbard_column_ops(M_.n_legs, M_.t, M_.U, M_.rung_pbc != 0, &hc_);
+      col_.d = hc_.d;
+      col_.H = hc_.H;
+      col_.sz.clear();
+      col_.sp.clear();
+    } else {
+      spin_column_ops(M_.n_legs, M_.J_rung, M_.rung_pbc != 0, &col_);
+    }
     D2_BLAS(cublasCreate(&libs_.bl));
     D2_BLAS(cublasSetStream(libs_.bl, strm_));
     D2_SOLV(cusolverDnCreate(&libs_.sv));
@@ -226,11 +240,31 @@ class Sweeper {
       D2_TRY(dsz_[y].upload(col_.sz[y], strm_));
       D2_TRY(dsp_[y].upload(col_.sp[y], strm_));
     }
+    if (hub_) {  // c^dag_j and c^dag_j P of the column, row-major
+      dcd_.resize(hc_.cd.size());
+      dcdP_.resize(hc_.cd.size());
+      for (size_t j = 0; j < hc_.cd.size(); ++j) {
+        Mat cp = hc_.cd[j];
+        for (int r = 0; r < dd; ++r)
+          for (int c = 0; c < dd; ++c) cp[(size_t)r * dd + c] *= hc_.parity[(size_t)c];
+        D2_TRY(dcd_[j].upload(hc_.cd[j], strm_));
+        D2_TRY(dcdP_[j].upload(cp, strm_));
+      }
+    }
     const int L = o_.n_columns, half = (L - 2) / 2;
     std::map<int, Block> left, right;
     left[1] = column_block();
     right[1] = column_block();
     for (int l = 1; l < half; ++l) {  // warm-up: block 1 and its mirror image grow together
+      if (hub_) {  // electrons: block 4 grows from its own density matrix (a mirrored
+                   // block would have the reversed mode order)
+        Block nl, nr;
+        D2_TRY(step(left[l], right[l], true, o_.m_warmup, l, -1, &nl, nullptr));
+        D2_TRY(step(left[l], right[l], false, o_.m_warmup, l, -1, &nr, nullptr));
+        left[l + 1] = nl;
+        right[l + 1] = nr;
+        continue;
+      }
       Block nb;
       D2_TRY(step(left[l], right[l], true, o_.m_warmup, l, -1, &nb, nullptr));
       left[l + 1] = nb;
@@ -276,6 +310,27 @@ class Sweeper {
     Block b;
     const int d = col_.d;
     b.m = d;
+    if (hub_) {  // states grouped by (N_up, N_dn) (stable), as sector-restricted blocks need
+      std::vector<int> perm(d);
+      for (int i = 0; i < d; ++i) perm[i] = i;
+      std::stable_sort(perm.begin(), perm.end(), [&](int a, int c) {
+        return hc_.nup[a] != hc_.nup[c] ? hc_.nup[a] < hc_.nup[c] : hc_.ndn[a] < hc_.ndn[c];
+      });
+      auto permuted = [&](const Mat& A) {
+        Mat P((size_t)d * d);
+        for (int i = 0; i < d; ++i)
+          for (int j = 0; j < d; ++j) P[(size_t)i * d + j] = A[(size_t)perm[i] * d + perm[j]];
+        return P;
+      };
+      b.H = permuted(hc_.H);
+      for (const Mat& c : hc_.cd) b.edge.push_back(permuted(c));
+      for (int i = 0; i < d; ++i) {
+        b.parity.push_back(hc_.parity[(size_t)perm[i]]);
+        b.qn.push_back(hc_.nup[(size_t)perm[i]]);
+        b.qn.push_back(hc_.ndn[(size_t)perm[i]]);
+      }
+      return b;
+    }
     // with sectors the block's states must be grouped by label: order by N_up (stable)
     std::vector<int> perm(d);
     for (int i = 0; i < d; ++i) perm[i] = i;
@@ -379,6 +434,15 @@ class Sweeper {
     return DMRG2D_OK;
   }
 
+  // Label of state e = i_blk + m i_col of a block enlarged by a column, as one integer
+  // ordered like the label: N_up (spins), N_up * 4096 + N_dn (electrons)
+  int enlarged_label(const Block& B, int64_t e) const {
+    const int a = (int)(e % B.m), c = (int)(e / B.m);
+    if (!hub_) return B.qn[(size_t)a] + __builtin_popcount((unsigned)c);
+    return (B.qn[2 * (size_t)a] + hc_.nup[(size_t)c]) * 4096 + B.qn[2 * (size_t)a + 1] +
+           hc_.ndn[(size_t)c];
+  }
+
   // Sector-restricted superblock: the density matrix is block diagonal in the growing
   // half's label.  Left: for each V_q, rho_q = G G^T with G its rows without padding;
   // right: rho_q = V_q^T V_q.  All eigenpairs of every rho_q, the k largest eigenvalues
@@ -423,16 +487,14 @@ class Sweeper {
         D2_BLAS(cublasDsyrk(libs_.bl, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, nr, qcols[q], &one, G.p,
                             nr, &zero, vecs[q]->p, nr));
         dim[q] = nr;
-        const int64_t e = dense[0];  // label of the enlarged-left state i1 + m1 i2
-        lab[q] = Lb.qn[(size_t)(e % Lb.m)] + __builtin_popcount((unsigned)(e / Lb.m));
+        lab[q] = enlarged_label(Lb, dense[0]);  // of the enlarged-left state i1 + m1 i2
       } else {
         for (int c = 0; c < qcols[q]; ++c) dense.push_back(colR[c0 + c]);
         D2_TRY(vecs[q]->alloc((size_t)qcols[q] * qcols[q]));
         D2_BLAS(cublasDsyrk(libs_.bl, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, qcols[q], qld[q], &one,
                             xq, qld[q], &zero, vecs[q]->p, qcols[q]));
         dim[q] = qcols[q];
-        const int64_t e = dense[0];  // label of the enlarged-right state i4 + m4 i3
-        lab[q] = Rb.qn[(size_t)(e % Rb.m)] + __builtin_popcount((unsigned)(e / Rb.m));
+        lab[q] = enlarged_label(Rb, dense[0]);  // of the enlarged-right state i4 + m4 i3
       }
       idx[q] = std::make_shared<IBuf>();
       D2_TRY(idx[q]->upload(dense, strm_));
@@ -553,15 +615,22 @@ class Sweeper {
     for (auto& e : Lb.edge) le.push_back(e.data());
     for (auto& e : Rb.edge) re.push_back(e.data());
     const bool sec = o_.use_sectors != 0;
-    dmrg2d_block bl{Lb.m, Lb.H.data(), (int)le.size(), le.data(), nullptr,
-                    sec ? Lb.qn.data() : nullptr};
-    dmrg2d_block br{Rb.m, Rb.H.data(), (int)re.size(), re.data(), nullptr,
-                    sec ? Rb.qn.data() : nullptr};
-    // S^z_tot = 0: half the superblock's sites up
-    const int32_t target = M_.n_legs * (Lb.cols + Rb.cols + 2) / 2;
+    dmrg2d_block bl{Lb.m, Lb.H.data(), (int)le.size(), le.data(),
+                    hub_ ? Lb.parity.data() : nullptr, sec ? Lb.qn.data() : nullptr};
+    dmrg2d_block br{Rb.m, Rb.H.data(), (int)re.size(), re.data(),
+                    hub_ ? Rb.parity.data() : nullptr, sec ? Rb.qn.data() : nullptr};
+    // spins: S^z_tot = 0 (half the superblock's sites up); electrons: the ladder's filling
+    // (N_up, N_dn), on a superblock of fewer columns (warm-up) the same filling rounded
+    // half up: floor(N cols / L + 1/2)
+    const int cols = Lb.cols + Rb.cols + 2;
+    int32_t target[2] = {M_.n_legs * cols / 2, 0};
+    if (hub_) {
+      target[0] = (int32_t)std::floor((double)o_.n_up * cols / o_.n_columns + 0.5);
+      target[1] = (int32_t)std::floor((double)o_.n_dn * cols / o_.n_columns + 0.5);
+    }
     dmrg2d_ops* ops = nullptr;
     auto tb = std::chrono::steady_clock::now();
-    D2_TRY(dmrg2d_build_ops(&M_, &bl, &br, sec ? &target : nullptr, &ops, strm_));
+    D2_TRY(dmrg2d_build_ops(&M_, &bl, &br, sec ? target : nullptr, &ops, strm_));
     build_seconds += since(tb);
     struct FreeOps {
       dmrg2d_ops* p;
@@ -670,24 +739,40 @@ class Sweeper {
     // observables of this step's ground state (<S_tot^2> only where no block is grown:
     // the last step of each sweep)
     const auto to = std::chrono::steady_clock::now();
-    std::vector<double> leg, rung;
-    double s2 = 0.0;
-    D2_TRY(observables(xd->p, Lb, Rb, out == nullptr, &leg, &rung, &s2));
-    for (double& v : leg) v /= norm2;
-    for (double& v : rung) v /= norm2;
-    s2 /= norm2;
+    std::vector<double> leg, rung, dens;
+    double s2 = std::nan("");
+    if (hub_) {  // site densities of the central columns (normalised by the call)
+      DBuf dd;
+      D2_TRY(dd.alloc((size_t)(8 * M_.n_legs + 2)));
+      D2_TRY(dmrg2d_site_densities(ops, x.p, dd.p, strm_));
+      dens.resize(dd.n);
+      D2_CUDA(cudaMemcpyAsync(dens.data(), dd.p, dd.n * sizeof(double), cudaMemcpyDeviceToHost,
+                              strm_));
+      D2_CUDA(cudaStreamSynchronize(strm_));
+    } else {
+      D2_TRY(observables(xd->p, Lb, Rb, out == nullptr, &leg, &rung, &s2));
+      for (double& v : leg) v /= norm2;
+      for (double& v : rung) v /= norm2;
+      s2 /= norm2;
+    }
     obs_seconds += since(to);
-    record(energy, 1.0 - kept, l, sweep, stats.iters, leg, rung, s2);
+    record(energy, 1.0 - kept, l, sweep, stats.iters, leg, rung, s2, dens);
     if (!out) return DMRG2D_OK;
     // ---- renormalisation: U^T O U for H_enl and the new boundary operators ----------------
     const auto tr = std::chrono::steady_clock::now();
+    const Block& B = grow_left ? Lb : Rb;
+    DBuf dHB;
+    D2_TRY(dHB.upload(B.H, strm_));
+    if (hub_) {
+      D2_TRY(renormalize_hubbard(B, grow_left, U, dHB, mb, n, k, labels, out));
+      out->U = Up;
+      renorm_seconds += since(tr);
+      return DMRG2D_OK;
+    }
     const double one = 1.0, zero = 0.0;
     DBuf HU, T;
     D2_TRY(HU.alloc((size_t)(n * k)));
     D2_TRY(T.alloc((size_t)(n * k)));
-    const Block& B = grow_left ? Lb : Rb;
-    DBuf dHB;
-    D2_TRY(dHB.upload(B.H, strm_));
     // H_enl U = (1 (x) H_B) U + (H_col (x) 1) U
     //         + J sum_y [ (Sz_y (x) SzB_y) + 1/2 (S-_y (x) S+B_y) + 1/2 (S+_y (x) S-B_y) ] U
     D2_TRY(kron_blk(dHB.p, false, U.p, HU.p, mb, k));
@@ -748,10 +833,102 @@ class Sweeper {
     return DMRG2D_OK;
   }
 
+  // dst (row-major k x k) = U^T XU, symmetrised when asked; U, XU: n x k column-major
+  int project(const DBuf& U, const double* XU, int64_t n, int k, Mat* dst, bool symmetrise) {
+    const double one = 1.0, zero = 0.0;
+    DBuf small;
+    D2_TRY(small.alloc((size_t)k * k));
+    Mat hs((size_t)k * k);
+    D2_BLAS(cublasDgemm(libs_.bl, CUBLAS_OP_T, CUBLAS_OP_N, k, k, (int)n, &one, U.p, (int)n, XU,
+                        (int)n, &zero, small.p, k));
+    D2_CUDA(cudaMemcpyAsync(hs.data(), small.p, (size_t)k * k * sizeof(double),
+                            cudaMemcpyDeviceToHost, strm_));
+    D2_CUDA(cudaStreamSynchronize(strm_));
+    dst->assign((size_t)k * k, 0.0);
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) {
+        const double a = hs[(size_t)i + (size_t)j * k];
+        (*dst)[(size_t)i * k + j] = symmetrise ? 0.5 * (a + hs[(size_t)j + (size_t)i * k]) : a;
+      }
+    return DMRG2D_OK;
+  }
+
+  // Electrons: the new block from the growing block B (mb states) and a column, U (n x k,
+  // n = mb d, block index fast).  H_enl = 1 (x) H_B + H_col (x) 1 - t sum_j h_j with the
+  // hopping between B's boundary mode j and the column's mode j:
+  //   block 1 grows: h_j = c_j (x) E_j + c^dag_j (x) E_j^T, E_j = c^dag_{B,j} P_B, and the
+  //                  new boundary operators are c^dag_j (x) P_B (the column's modes come
+  //                  after block 1's: their string runs over the whole block);
+  //   block 4 grows: h_j = (c^dag_j P) (x) c_{B,j} + (P c_j) (x) c^dag_{B,j}, and the new
+  //                  boundary operators are c^dag_j (x) 1 (the column comes first).
+  // Labels (N_up * 4096 + N_dn, from the density matrix's sectors) give the new block's
+  // (N_up, N_dn) and parity.
+  int renormalize_hubbard(const Block& B, bool grow_left, const DBuf& U, const DBuf& dHB, int mb,
+                          int64_t n, int k, const std::vector<int32_t>& labels, Block* out) {
+    DBuf HU, T, T2;
+    D2_TRY(HU.alloc((size_t)(n * k)));
+    D2_TRY(T.alloc((size_t)(n * k)));
+    D2_TRY(kron_blk(dHB.p, false, U.p, HU.p, mb, k));
+    D2_TRY(kron_col(dH_col_.p, false, U.p, HU.p, mb, k, 1.0, 1.0));
+    const double t = M_.t;
+    const int nm = (int)hc_.cd.size();
+    DBuf dPb;
+    if (grow_left) {
+      Mat Pb((size_t)mb * mb, 0.0);
+      for (int i = 0; i < mb; ++i) Pb[(size_t)i * mb + i] = B.parity[(size_t)i];
+      D2_TRY(dPb.upload(Pb, strm_));
+      D2_TRY(T2.alloc((size_t)(n * k)));
+    }
+    for (int j = 0; j < nm; ++j) {
+      DBuf dE;
+      if (grow_left) {
+        Mat E = B.edge[(size_t)j];  // c^dag_{B,j} P_B: column c of the matrix times P_B[c]
+        for (int r = 0; r < mb; ++r)
+          for (int c = 0; c < mb; ++c) E[(size_t)r * mb + c] *= B.parity[(size_t)c];
+        D2_TRY(dE.upload(E, strm_));
+        D2_TRY(kron_blk(dE.p, false, U.p, T.p, mb, k));                  // (1 (x) E_j) U
+        D2_TRY(kron_col(dcd_[j].p, true, T.p, HU.p, mb, k, -t, 1.0));    // c_j (x) E_j
+        D2_TRY(kron_blk(dE.p, true, U.p, T.p, mb, k));                   // (1 (x) E_j^T) U
+        D2_TRY(kron_col(dcd_[j].p, false, T.p, HU.p, mb, k, -t, 1.0));   // c^dag_j (x) E_j^T
+      } else {
+        D2_TRY(dE.upload(B.edge[(size_t)j], strm_));                     // c^dag_{B,j}
+        D2_TRY(kron_blk(dE.p, true, U.p, T.p, mb, k));                   // (1 (x) c_{B,j}) U
+        D2_TRY(kron_col(dcdP_[j].p, false, T.p, HU.p, mb, k, -t, 1.0));  // c^dag_j P
+        D2_TRY(kron_blk(dE.p, false, U.p, T.p, mb, k));                  // (1 (x) c^dag_{B,j}) U
+        D2_TRY(kron_col(dcdP_[j].p, true, T.p, HU.p, mb, k, -t, 1.0));   // P c_j
+      }
+    }
+    out->m = k;
+    out->m_prev = mb;
+    out->cols = B.cols + 1;
+    D2_TRY(project(U, HU.p, n, k, &out->H, true));
+    out->edge.assign((size_t)nm, Mat());
+    for (int j = 0; j < nm; ++j) {
+      if (grow_left) {
+        D2_TRY(kron_blk(dPb.p, false, U.p, T2.p, mb, k));                // (1 (x) P_B) U
+        D2_TRY(kron_col(dcd_[j].p, false, T2.p, T.p, mb, k, 1.0, 0.0));  // c^dag_j (x) P_B
+      } else {
+        D2_TRY(kron_col(dcd_[j].p, false, U.p, T.p, mb, k, 1.0, 0.0));   // c^dag_j (x) 1
+      }
+      D2_TRY(project(U, T.p, n, k, &out->edge[(size_t)j], false));
+    }
+    out->qn.clear();
+    out->parity.clear();
+    for (int32_t lab : labels) {
+      const int nu = lab / 4096, nd = lab % 4096;
+      out->qn.push_back(nu);
+      out->qn.push_back(nd);
+      out->parity.push_back((nu + nd) % 2 ? -1.0 : 1.0);
+    }
+    return DMRG2D_OK;
+  }
+
   void record(double e, double trunc, int l, int sweep, int iters, const std::vector<double>& leg,
-              const std::vector<double>& rung, double s2) {
+              const std::vector<double>& rung, double s2, const std::vector<double>& dens) {
     const int i = rep_->n_steps++;
     if (i < rep_->cap) {
+      if (rep_->densities && !dens.empty())
+        for (size_t j = 0; j < dens.size(); ++j) rep_->densities[(size_t)i * dens.size() + j] = dens[j];
       const int nl = (int)col_.sz.size(), nr = std::max(nl - 1, 1);
       if (rep_->leg_bond)
         for (int y = 0; y < nl; ++y) rep_->leg_bond[(size_t)i * nl + y] = leg[(size_t)y];
@@ -824,6 +1001,9 @@ class Sweeper {
   Libs libs_;
   DBuf dH_col_;
   std::vector<DBuf> dsz_, dsp_;
+  bool hub_ = false;              // Hubbard ladder (electrons) instead of spins
+  HubbardColumnOps hc_;
+  std::vector<DBuf> dcd_, dcdP_;  // per mode j: c^dag_j and c^dag_j P of the column
 };
 
 }  // namespace
@@ -836,10 +1016,19 @@ extern "C" int dmrg2d_sweep(const dmrg2d_model* model, const dmrg2d_sweep_opts* 
                             dmrg2d_sweep_report* report, void* stream) {
   if (!model || !opts || !report) return set_error(DMRG2D_EINVAL, "sweep: NULL argument");
   clear_error();
-  if (model->kind != DMRG2D_HEISENBERG)
-    return set_error(DMRG2D_EUNSUPPORTED, "sweep: Heisenberg ladders only");
-  if (model->n_legs < 1 || model->n_legs > 8)
-    return set_error(DMRG2D_EINVAL, "sweep: n_legs must be in [1, 8]");
+  if (model->kind != DMRG2D_HEISENBERG && model->kind != DMRG2D_HUBBARD)
+    return set_error(DMRG2D_EUNSUPPORTED, "sweep: Heisenberg or Hubbard ladders only");
+  if (model->kind == DMRG2D_HUBBARD) {
+    if (!opts->use_sectors)
+      return set_error(DMRG2D_EUNSUPPORTED,
+                       "sweep: Hubbard ladders run in a target (N_up, N_dn) sector (use_sectors)");
+    const int sites = model->n_legs * opts->n_columns;
+    if (opts->n_up < 0 || opts->n_dn < 0 || opts->n_up > sites || opts->n_dn > sites)
+      return set_error(DMRG2D_EINVAL, "sweep: n_up, n_dn must be in [0, %d]", sites);
+  }
+  if (model->n_legs < 1 || model->n_legs > (model->kind == DMRG2D_HUBBARD ? 4 : 8))
+    return set_error(DMRG2D_EINVAL, "sweep: n_legs must be in [1, %d]",
+                     model->kind == DMRG2D_HUBBARD ? 4 : 8);
   if (opts->n_columns < 4 || opts->n_columns % 2)
     return set_error(DMRG2D_EINVAL, "sweep: n_columns must be even and >= 4");
   if (opts->m_warmup < 1 || opts->n_sweeps < 0 || (opts->n_sweeps > 0 && !opts->m_sweep))

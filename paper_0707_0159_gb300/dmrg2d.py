@@ -43,7 +43,7 @@ class SweepOpts(C.Structure):
     _fields_ = [("n_columns", C.c_int), ("m_warmup", C.c_int), ("n_sweeps", C.c_int),
                 ("m_sweep", C.POINTER(C.c_int)), ("precision", C.c_int), ("tol", C.c_double),
                 ("max_iter", C.c_int), ("krylov_dim", C.c_int), ("seed", C.c_uint64),
-                ("use_sectors", C.c_int)]
+                ("use_sectors", C.c_int), ("n_up", C.c_int), ("n_dn", C.c_int)]
 
 
 class SweepReport(C.Structure):
@@ -51,7 +51,7 @@ class SweepReport(C.Structure):
                 ("trunc", C.POINTER(C.c_double)), ("l", C.POINTER(C.c_int)),
                 ("sweep", C.POINTER(C.c_int)), ("iters", C.POINTER(C.c_int)),
                 ("leg_bond", C.POINTER(C.c_double)), ("rung_bond", C.POINTER(C.c_double)),
-                ("s2", C.POINTER(C.c_double)),
+                ("s2", C.POINTER(C.c_double)), ("densities", C.POINTER(C.c_double)),
                 ("seconds", C.c_double),
                 ("solve_seconds", C.c_double), ("build_seconds", C.c_double),
                 ("dm_seconds", C.c_double), ("renorm_seconds", C.c_double),
@@ -490,20 +490,28 @@ def mlp_make_batch(ops: Ops, x_k, r_k, theta, x_final, D, idx, X, w, T, stream=N
 
 
 def sweep(model: dict, n_columns: int, m_warmup: int, m_sweeps, precision=FP64, tol=1e-10,
-          max_iter=300, krylov_dim=100, seed=1, cap=4096, sectors=False, stream=None) -> dict:
+          max_iter=300, krylov_dim=100, seed=1, cap=4096, sectors=False, n_up=0, n_dn=0,
+          stream=None) -> dict:
     """dmrg2d_sweep: warm-up plus one finite sweep per entry of m_sweeps on an n-leg
-    Heisenberg ladder of n_columns columns.  Returns the per-step energy, truncation
-    error, block-1 length and sweep index (-1 = warm-up), and the timings."""
+    Heisenberg ladder (or, with sectors=True and the filling n_up, n_dn, a Hubbard ladder)
+    of n_columns columns.  Returns the per-step energy, truncation error, block-1 length
+    and sweep index (-1 = warm-up), the observables and the timings; for Hubbard ladders
+    "n" (steps x 2 columns x n_legs x [up, down]), "h", "sd" (steps x 2 x n_legs) and "S"
+    (steps x 2) are the central columns' site densities."""
     precision = PRECISION.get(precision, precision)
     ms = (C.c_int * max(1, len(m_sweeps)))(*[int(m) for m in m_sweeps])
     opts = SweepOpts(int(n_columns), int(m_warmup), len(m_sweeps), ms, int(precision), float(tol),
-                     int(max_iter), int(krylov_dim), int(seed), int(bool(sectors)))
+                     int(max_iter), int(krylov_dim), int(seed), int(bool(sectors)), int(n_up),
+                     int(n_dn))
     e, t = (C.c_double * cap)(), (C.c_double * cap)()
     ll, sw, it = (C.c_int * cap)(), (C.c_int * cap)(), (C.c_int * cap)()
     nl = int(model["n_legs"])
     nr = max(nl - 1, 1)
     leg, rung, s2 = (C.c_double * (cap * nl))(), (C.c_double * (cap * nr))(), (C.c_double * cap)()
-    rep = SweepReport(cap, 0, e, t, ll, sw, it, leg, rung, s2, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0)
+    nd = 8 * nl + 2
+    dens = (C.c_double * (cap * nd))()
+    rep = SweepReport(cap, 0, e, t, ll, sw, it, leg, rung, s2, dens, 0.0, 0.0, 0.0, 0.0, 0.0,
+                      0.0)
     mdl = _model(model)
     _check(lib().dmrg2d_sweep(C.byref(mdl), C.byref(opts), C.byref(rep), _stream(stream)))
     n = min(rep.n_steps, cap)
@@ -514,4 +522,12 @@ def sweep(model: dict, n_columns: int, m_warmup: int, m_sweeps, precision=FP64, 
             "s2": list(s2[:n]), "obs_seconds": rep.obs_seconds,
             "n_steps": rep.n_steps, "seconds": rep.seconds, "solve_seconds": rep.solve_seconds,
             "build_seconds": rep.build_seconds, "dm_seconds": rep.dm_seconds,
-            "renorm_seconds": rep.renorm_seconds}
+            "renorm_seconds": rep.renorm_seconds, **_sweep_densities(dens, n, nl)}
+
+
+def _sweep_densities(buf, n: int, nl: int) -> dict:
+    """Split the report's per-step density records (layout of dmrg2d_site_densities)."""
+    a = np.frombuffer(buf, dtype=np.float64, count=n * (8 * nl + 2)).reshape(n, 8 * nl + 2)
+    per = a[:, :8 * nl].reshape(n, 2, nl, 4)
+    return {"n": per[..., :2].copy(), "h": per[..., 2].copy(), "sd": per[..., 3].copy(),
+            "S": a[:, 8 * nl:].copy()}
