@@ -116,3 +116,12 @@ def test_partition_and_bench_bookkeeping_gloo_two_ranks():
         assert err <= 1e-13
         assert slowest == 2.0                      # max over ranks of (1.0, 2.0) ms
         assert job == pytest.approx(2 * 2e12 / 2e-3 / 1e12)
+
+
+def test_bench_cpulist_parser():
+    """The sysfs CPU-list format the benchmark reads to place pinned buffers near the GPU."""
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    assert bench.parse_cpulist("0-3,8,10-11\n") == {0, 1, 2, 3, 8, 10, 11}
+    assert bench.parse_cpulist("5") == {5}
+    assert bench.parse_cpulist("") == set()
