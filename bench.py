@@ -36,7 +36,7 @@ sys.path.insert(0, ROOT)
 METRIC = "superblock H·v TFLOP/s & time to ground energy at 1e-8 rel. vs plain FP64"
 
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture of
-# this workload (profiles/hv_tc_pair_kernel_ladder3_hubbard_m256.md), keyed by tile
+# this workload (dram__bytes_read.sum + dram__bytes_write.sum), keyed by tile
 # configuration name and dtype.  They hold only for the kernel source they were taken
 # on: `traffic` is reported as null when csrc/hv_tc.cu no longer has this SHA-256.
 NCU_TRAFFIC = {

@@ -171,6 +171,10 @@ typedef struct dmrg2d_solver_opts {
                           1 = one pass, 0 = the three-term recurrence only)          */
   int refine_precision;/* mixed: H·v of the outer loop's residuals, DMRG2D_FP64 or
                           DMRG2D_FP64X (float pairs, dense superblocks)              */
+  int thick_keep;      /* plain Lanczos, at a full basis: 0 = explicit restart from the
+                          lowest Ritz vector; p in 1..32 = thick restart (Wu and Simon)
+                          keeping the p lowest Ritz vectors and the next Lanczos vector,
+                          the kept space re-tridiagonalised so the recurrence goes on  */
 } dmrg2d_solver_opts;
 
 typedef struct dmrg2d_solver_stats {
@@ -191,6 +195,20 @@ int dmrg2d_lanczos_ground(const dmrg2d_ops* ops, const dmrg2d_solver_opts* opts,
                           double* x_inout, double* energy_out,
                           dmrg2d_solver_stats* stats, void* stream);
 
+/* Lowest eigenpair of the symmetric tridiagonal matrix T (diagonal alpha[0..k),
+ * off-diagonal beta[0..k-1)) — the small eigenproblem inside every Lanczos solve of the
+ * superblock (the paper's exact diagonalisation names no eigensolver).  One block: the
+ * eigenvalue by multisection on Sturm counts (257 points per round), the eigenvector by
+ * the twisted factorisation of T - theta (inverse iteration as the fallback).
+ *   alpha, beta: device, k doubles each (beta[k-1] is the coupling of the Krylov space to
+ *   the next Lanczos vector: it enters only the residual estimate out[1]).
+ *   s: device, k doubles, receives the unit eigenvector (first nonzero entry positive).
+ *   out: device, 3 + 5k doubles: out[0] = eigenvalue, out[1] = |beta[k-1] s[k-1]|,
+ *   out[2] = 0 (ok) or 1 (a non-finite entry); the rest is workspace.
+ * 1 <= k <= 512 (else ESHAPE).  Asynchronous on `stream`; allocates nothing. */
+int dmrg2d_tridiag_lowest(const double* alpha, const double* beta, int k, double* s,
+                          double* out, void* stream);
+
 /* Allocation-free variant of dmrg2d_lanczos_ground for small superblocks.  The
  * paper has no counterpart; it exists for callers that cannot call cudaMalloc:
  * applications whose device memory is owned by another allocator (for example a
@@ -203,8 +221,13 @@ int dmrg2d_lanczos_ground(const dmrg2d_ops* ops, const dmrg2d_solver_opts* opts,
  * doubles (16 MiB) that every GPU which loads the library holds until the process
  * exits.
  *   Limits: plain FP64 Lanczos only (precision = DMRG2D_FP64, refine = 0, else
- *   EUNSUPPORTED); (krylov_dim + 2) * n_vec + 1226 * (krylov_dim + 1) + 64 doubles
- *   must fit in the array, else ESHAPE with the sizes in dmrg2d_last_error().
+ *   EUNSUPPORTED); krylov_dim, after clamping to max_iter + 1, at most 512 (else
+ *   ESHAPE); (krylov_dim + 2) * n_vec + 1226 * (krylov_dim + 1) + 64 doubles must fit
+ *   in the array, else ESHAPE with the sizes in dmrg2d_last_error().
+ *   Device: the ops object's device must be current (else EINVAL), since the array is
+ *   one per device.
+ *   Sector-restricted ops: the padding rows of x_inout are set to zero first, as in
+ *   dmrg2d_lanczos_ground.
  *   Set-up: the first call on each device looks up the array's device address
  *   (cudaGetSymbolAddress) with that device current; make that first call before
  *   any stream capture.

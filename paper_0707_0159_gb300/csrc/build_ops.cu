@@ -553,4 +553,5 @@ extern "C" void dmrg2d_default_solver_opts(dmrg2d_solver_opts* o) {
   o->check_every = 5;
   o->start_reorth = 0;
   o->refine_precision = DMRG2D_FP64;
+  o->thick_keep = 0;
 }

@@ -397,51 +397,43 @@ __global__ void k_cg_direction(float* __restrict__ p, const float* __restrict__ 
 }
 
 // ---- lowest eigenpair of the Lanczos tridiagonal T_k (diag alpha, off-diag beta) ----
-// Sturm-sequence bisection for the eigenvalue, inverse iteration (tridiagonal LU with
-// partial pivoting) for the eigenvector.  out[0] = theta, out[1] = |beta_{k-1} s_{k-1}|,
-// out[2] = status (0 ok, 1 NaN).  scratch: 6*k doubles.
-__device__ int sturm_count(const double* a, const double* b, int k, double x) {
+// One block.  The eigenvalue by multisection: every thread evaluates the Sturm count
+// (the number of negative pivots of the LDL^T factorisation of T - x, Sylvester's law of
+// inertia) at its own point of the current interval, which shrinks 257-fold per round.
+// The eigenvector by the twisted factorisation of T - theta (Dhillon and Parlett): the
+// top-down LDL^T (thread 0) and bottom-up UDU^T (thread 32) pivots give the twist
+// index r with the smallest |gamma_r|, and z solves (T - theta) z = gamma_r e_r with
+// z_r = 1 by two product recurrences.  If z is not finite, inverse iteration with
+// partial pivoting on one thread is the fallback.
+// out[0] = theta, out[1] = |beta_{k-1} s_{k-1}| (the Ritz residual), out[2] = status
+// (0 ok, 1 NaN).  k <= TD_MAX.  scratch (fallback only): 5*k doubles.
+constexpr int TD_THREADS = 256;
+constexpr int TD_MAX = 512;
+constexpr int TR_KEEP_MAX = 32;  // Ritz vectors kept at a thick restart
+
+// Negative pivots of LDL^T(T - x) = eigenvalues of T below x; b2 = squared off-diagonal.
+// A pivot smaller than pivmin in magnitude is replaced by -pivmin.
+__device__ int sturm_count(const double* a, const double* b2, int k, double x, double pivmin) {
   int cnt = 0;
   double q = a[0] - x;
-  if (q < 0) ++cnt;
-  for (int i = 1; i < k; ++i) {
-    if (q == 0.0) q = 1e-300;
-    q = (a[i] - x) - b[i - 1] * b[i - 1] / q;
+  for (int i = 1;; ++i) {
+    if (fabs(q) < pivmin) q = -pivmin;
     if (q < 0) ++cnt;
+    if (i >= k) break;
+    q = (a[i] - x) - b2[i - 1] / q;
   }
   return cnt;
 }
 
-__global__ void k_tridiag_ground(const double* __restrict__ alpha, const double* __restrict__ beta,
-                                 int k, double* __restrict__ s, double* __restrict__ out,
-                                 double* __restrict__ scr) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double lo = 1e300, hi = -1e300;
-  bool bad = false;
-  for (int i = 0; i < k; ++i) {
-    const double r = (i > 0 ? fabs(beta[i - 1]) : 0.0) + (i + 1 < k ? fabs(beta[i]) : 0.0);
-    lo = fmin(lo, alpha[i] - r);
-    hi = fmax(hi, alpha[i] + r);
-    if (!isfinite(alpha[i]) || !isfinite(beta[i])) bad = true;
-  }
-  if (bad) {
-    out[0] = nan("");
-    out[1] = nan("");
-    out[2] = 1.0;
-    return;
-  }
-  for (int it = 0; it < 200 && hi - lo > 2.2e-16 * fmax(fabs(lo), fabs(hi)) + 1e-300; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (sturm_count(alpha, beta, k, mid) >= 1) hi = mid; else lo = mid;
-  }
-  const double theta = 0.5 * (lo + hi);
-  // inverse iteration: solve (T - theta) z = s, with gtsv-style partial pivoting
-  double* dl = scr;          // sub-diagonal
-  double* dd = scr + k;      // diagonal
-  double* du = scr + 2 * k;  // super-diagonal
-  double* du2 = scr + 3 * k; // second super-diagonal (fill-in)
+// Fallback eigenvector: three steps of inverse iteration, (T - theta) z = s, tridiagonal
+// LU with partial pivoting (gtsv style), on one thread.  scr: 5*k doubles.
+__device__ bool inverse_iteration(const double* alpha, const double* beta, int k, double theta,
+                                  double tiny, double* s, double* scr) {
+  double* dl = scr;
+  double* dd = scr + k;
+  double* du = scr + 2 * k;
+  double* du2 = scr + 3 * k;
   double* z = scr + 4 * k;
-  const double tiny = 1e-14 * fmax(fabs(lo), fabs(hi)) + 1e-300;
   for (int i = 0; i < k; ++i) s[i] = 1.0 / sqrt((double)k);
   for (int rep = 0; rep < 3; ++rep) {
     for (int i = 0; i < k; ++i) {
@@ -451,7 +443,7 @@ __global__ void k_tridiag_ground(const double* __restrict__ alpha, const double*
       du2[i] = 0.0;
       z[i] = s[i];
     }
-    for (int i = 0; i + 1 < k; ++i) {   // forward elimination with row swaps
+    for (int i = 0; i + 1 < k; ++i) {
       if (fabs(dd[i]) >= fabs(dl[i])) {
         if (dd[i] == 0.0) dd[i] = tiny;
         const double f = dl[i] / dd[i];
@@ -480,23 +472,458 @@ __global__ void k_tridiag_ground(const double* __restrict__ alpha, const double*
     double nrm = 0.0;
     for (int i = 0; i < k; ++i) nrm += z[i] * z[i];
     nrm = sqrt(nrm);
-    if (!(nrm > 0.0) || !isfinite(nrm)) {
-      out[2] = 1.0;
-      break;
-    }
+    if (!(nrm > 0.0) || !isfinite(nrm)) return false;
     for (int i = 0; i < k; ++i) s[i] = z[i] / nrm;
   }
-  // fix the sign so the first nonzero component is positive (deterministic Ritz vector)
-  double sg = 1.0;
-  for (int i = 0; i < k; ++i)
-    if (s[i] != 0.0) {
-      sg = s[i] > 0 ? 1.0 : -1.0;
+  return true;
+}
+
+// Twisted-factorisation eigenvector of the tridiagonal (a, b) for the eigenvalue theta,
+// on one thread: z (unnormalised, z_r = 1).  Dp, Dm, Lf, Ub: k doubles each.
+__device__ void twisted_vector(const double* a, const double* b, int k, double theta, double tiny,
+                               double* Dp, double* Dm, double* Lf, double* Ub, double* z) {
+  double d = a[0] - theta;
+  for (int i = 0; i + 1 < k; ++i) {
+    if (fabs(d) < tiny) d = d < 0 ? -tiny : tiny;
+    Dp[i] = d;
+    Lf[i] = b[i] / d;
+    d = (a[i + 1] - theta) - Lf[i] * b[i];
+  }
+  Dp[k - 1] = d;
+  d = a[k - 1] - theta;
+  for (int i = k - 2; i >= 0; --i) {
+    if (fabs(d) < tiny) d = d < 0 ? -tiny : tiny;
+    Dm[i + 1] = d;
+    Ub[i] = b[i] / d;
+    d = (a[i] - theta) - Ub[i] * b[i];
+  }
+  Dm[0] = d;
+  int r = 0;
+  double g = INFINITY;
+  for (int i = 0; i < k; ++i) {
+    const double gi = fabs(Dp[i] + Dm[i] - (a[i] - theta));
+    if (gi < g) {
+      g = gi;
+      r = i;
+    }
+  }
+  z[r] = 1.0;
+  for (int i = r - 1; i >= 0; --i) z[i] = -Lf[i] * z[i + 1];
+  for (int i = r; i + 1 < k; ++i) z[i + 1] = -Ub[i] * z[i];
+}
+
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Shared set-up of the tridiagonal kernels: a, bb (off-diagonal, bb[k-1] = 0), b2 = bb^2
+// in shared memory; Gershgorin interval and pivmin (by thread 0 into *lo, *hi, *pivmin);
+// returns false (uniformly) if an entry of alpha[0..k) or beta[0..k) is not finite.
+__device__ bool td_setup(const double* __restrict__ alpha, const double* __restrict__ beta, int k,
+                         double* a, double* bb, double* b2, double* lo, double* hi,
+                         double* pivmin) {
+  __shared__ double r_lo[TD_THREADS / 32], r_hi[TD_THREADS / 32], r_b[TD_THREADS / 32];
+  __shared__ int bad;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  bool mybad = false;
+  for (int i = tid; i < k; i += TD_THREADS) {
+    const double ai = alpha[i], bi = beta[i];
+    if (!isfinite(ai) || !isfinite(bi)) mybad = true;
+    a[i] = ai;
+    bb[i] = i + 1 < k ? bi : 0.0;
+    b2[i] = bb[i] * bb[i];
+  }
+  if (mybad) atomicOr(&bad, 1);
+  __syncthreads();
+  double l = 1e300, h = -1e300, bm = 0.0;
+  for (int i = tid; i < k; i += TD_THREADS) {
+    const double r = (i > 0 ? fabs(bb[i - 1]) : 0.0) + fabs(bb[i]);
+    l = fmin(l, a[i] - r);
+    h = fmax(h, a[i] + r);
+    bm = fmax(bm, b2[i]);
+  }
+  l = warp_min(l);
+  h = warp_max(h);
+  bm = warp_max(bm);
+  if (lane == 0) {
+    r_lo[w] = l;
+    r_hi[w] = h;
+    r_b[w] = bm;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int i = 1; i < TD_THREADS / 32; ++i) {
+      l = fmin(l, r_lo[i]);
+      h = fmax(h, r_hi[i]);
+      bm = fmax(bm, r_b[i]);
+    }
+    *lo = l;
+    *hi = h;
+    *pivmin = 2.2250738585072014e-308 * fmax(1.0, bm);
+  }
+  __syncthreads();
+  return bad == 0;
+}
+
+__global__ void __launch_bounds__(TD_THREADS)
+k_tridiag_ground(const double* __restrict__ alpha, const double* __restrict__ beta, int k,
+                 double* __restrict__ s, double* __restrict__ out, double* __restrict__ scr) {
+  __shared__ double a[TD_MAX], bb[TD_MAX], b2[TD_MAX];
+  __shared__ double Dp[TD_MAX], Dm[TD_MAX], Lf[TD_MAX], Ub[TD_MAX], z[TD_MAX];
+  __shared__ double sh_lo, sh_hi, sh_piv, sh_red[TD_THREADS / 32];
+  __shared__ int sh_first, sh_r[TD_THREADS / 32];
+  __shared__ double sh_g[TD_THREADS / 32];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (!td_setup(alpha, beta, k, a, bb, b2, &sh_lo, &sh_hi, &sh_piv)) {
+    if (tid == 0) {
+      out[0] = nan("");
+      out[1] = nan("");
+      out[2] = 1.0;
+    }
+    return;
+  }
+  const double pivmin = sh_piv;
+  // ---- multisection for the lowest eigenvalue ----
+  for (int it = 0; it < 16; ++it) {
+    const double L = sh_lo, H = sh_hi;
+    if (!(H - L > 4.4e-16 * fmax(fabs(L), fabs(H)) + 1e-300)) break;
+    const double x = L + (H - L) * (double)(tid + 1) / (double)(TD_THREADS + 1);
+    const bool below = sturm_count(a, b2, k, x, pivmin) >= 1;
+    if (tid == 0) sh_first = TD_THREADS;
+    __syncthreads();
+    if (below) atomicMin(&sh_first, tid);
+    __syncthreads();
+    if (tid == 0) {
+      const int f = sh_first;
+      sh_lo = f == 0 ? L : L + (H - L) * (double)f / (double)(TD_THREADS + 1);
+      sh_hi = f == TD_THREADS ? H : L + (H - L) * (double)(f + 1) / (double)(TD_THREADS + 1);
+    }
+    __syncthreads();
+  }
+  const double theta = 0.5 * (sh_lo + sh_hi);
+  const double tiny = 1e-14 * fmax(fabs(sh_lo), fabs(sh_hi)) + 1e-300;
+  // ---- twisted factorisation of T - theta ----
+  if (tid == 0) {  // top-down LDL^T
+    double d = a[0] - theta;
+    for (int i = 0; i + 1 < k; ++i) {
+      if (fabs(d) < tiny) d = d < 0 ? -tiny : tiny;
+      Dp[i] = d;
+      Lf[i] = bb[i] / d;
+      d = (a[i + 1] - theta) - Lf[i] * bb[i];
+    }
+    Dp[k - 1] = d;
+  } else if (tid == 32) {  // bottom-up UDU^T
+    double d = a[k - 1] - theta;
+    for (int i = k - 2; i >= 0; --i) {
+      if (fabs(d) < tiny) d = d < 0 ? -tiny : tiny;
+      Dm[i + 1] = d;
+      Ub[i] = bb[i] / d;
+      d = (a[i] - theta) - Ub[i] * bb[i];
+    }
+    Dm[0] = d;
+  }
+  __syncthreads();
+  double g = INFINITY;  // twist index: smallest |gamma_r|, ties to the smaller r
+  int r = k;
+  for (int i = tid; i < k; i += TD_THREADS) {
+    const double gi = fabs(Dp[i] + Dm[i] - (a[i] - theta));
+    if (gi < g) {
+      g = gi;
+      r = i;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double og = __shfl_down_sync(0xffffffffu, g, o);
+    const int orr = __shfl_down_sync(0xffffffffu, r, o);
+    if (og < g || (og == g && orr < r)) {
+      g = og;
+      r = orr;
+    }
+  }
+  if (lane == 0) {
+    sh_g[w] = g;
+    sh_r[w] = r;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int i = 1; i < TD_THREADS / 32; ++i)
+      if (sh_g[i] < g || (sh_g[i] == g && sh_r[i] < r)) {
+        g = sh_g[i];
+        r = sh_r[i];
+      }
+    sh_first = r;
+  }
+  __syncthreads();
+  r = sh_first;
+  if (r < k) {
+    if (tid == 0) {
+      double v = 1.0;
+      z[r] = 1.0;
+      for (int i = r - 1; i >= 0; --i) {
+        v = -Lf[i] * v;
+        z[i] = v;
+      }
+    } else if (tid == 32) {
+      double v = 1.0;
+      for (int i = r; i + 1 < k; ++i) {
+        v = -Ub[i] * v;
+        z[i + 1] = v;
+      }
+    }
+  }
+  __syncthreads();
+  double nn = 0.0;
+  if (r < k)
+    for (int i = tid; i < k; i += TD_THREADS) nn += z[i] * z[i];
+  nn = warp_sum(nn);
+  if (lane == 0) sh_red[w] = nn;
+  __syncthreads();
+  if (tid == 0) {
+    for (int i = 1; i < TD_THREADS / 32; ++i) nn += sh_red[i];
+    sh_red[0] = (r < k && isfinite(nn) && nn > 0.0) ? sqrt(nn) : -1.0;
+  }
+  __syncthreads();
+  const double nrm = sh_red[0];
+  if (nrm < 0.0) {  // fallback: inverse iteration on one thread
+    if (tid == 0) {
+      const bool ok = inverse_iteration(alpha, beta, k, theta, tiny, s, scr);
+      double sg = 1.0;
+      for (int i = 0; i < k; ++i)
+        if (s[i] != 0.0) {
+          sg = s[i] > 0 ? 1.0 : -1.0;
+          break;
+        }
+      for (int i = 0; i < k; ++i) s[i] *= sg;
+      out[0] = theta;
+      out[1] = fabs(beta[k - 1] * s[k - 1]);
+      out[2] = ok ? 0.0 : 1.0;
+    }
+    return;
+  }
+  // sign: the first nonzero component positive (deterministic Ritz vector)
+  if (tid == 0) sh_first = k;
+  __syncthreads();
+  for (int i = tid; i < k; i += TD_THREADS)
+    if (z[i] != 0.0) {
+      atomicMin(&sh_first, i);
       break;
     }
-  for (int i = 0; i < k; ++i) s[i] *= sg;
-  out[0] = theta;
-  out[1] = fabs(beta[k - 1] * s[k - 1]);
-  if (out[2] != 1.0) out[2] = 0.0;
+  __syncthreads();
+  const double f = (sh_first < k && z[sh_first] < 0.0 ? -1.0 : 1.0) / nrm;
+  for (int i = tid; i < k; i += TD_THREADS) s[i] = z[i] * f;
+  if (tid == 0) {
+    out[0] = theta;
+    out[1] = fabs(beta[k - 1] * z[k - 1] * f);
+    out[2] = 0.0;
+  }
+}
+
+// ---- thick restart (Wu and Simon's thick-restart Lanczos) -----------------------------
+// At a full basis of k vectors: keep the space of the p lowest Ritz vectors plus the next
+// Lanczos vector q_k.  The kept space is re-tridiagonalised so that the recurrence goes on
+// unchanged: with S (k x p, orthonormalised) the Ritz coefficient vectors, P = S^T T S and
+// the couplings c = beta_{k-1} S[k-1, :] to q_k, a Lanczos process on P started from
+// c / |c| gives W (p x p) with W^T P W tridiagonal and W^T c = |c| e_0.  The new basis
+// is Z = Q S W in reverse order (z_{p-1}, ..., z_0), then q_k: its projected matrix is
+// tridiagonal, with |c| coupling z_0 to q_k.
+// Writes M (k x p', column-major, ld k: new vector i = Q M[:, i]), the new alpha[0..p'),
+// beta[0..p') (beta[p'-1] = |c|) and out[0] = p' (p' < p if the small Lanczos process
+// breaks down or the Ritz vectors are numerically dependent; 0: no restart possible).
+// scr: p * (6 k + p) doubles.
+__global__ void __launch_bounds__(TD_THREADS)
+k_thick_restart(double* __restrict__ alpha, double* __restrict__ beta, int k, int p,
+                double* __restrict__ M, double* __restrict__ scr, double* __restrict__ out) {
+  __shared__ double a[TD_MAX], bb[TD_MAX], b2[TD_MAX];
+  __shared__ double sh_lo, sh_hi, sh_piv, sh_bk, sh_red[TD_THREADS / 32];
+  __shared__ double th[TR_KEEP_MAX], P[TR_KEEP_MAX][TR_KEEP_MAX + 1],
+      W[TR_KEEP_MAX][TR_KEEP_MAX + 1], cvec[TR_KEEP_MAX], al[TR_KEEP_MAX], be[TR_KEEP_MAX];
+  __shared__ int sh_p, sh_pp;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (tid == 0) sh_bk = beta[k - 1];
+  if (!td_setup(alpha, beta, k, a, bb, b2, &sh_lo, &sh_hi, &sh_piv) || p < 1 || k < 2) {
+    if (tid == 0) out[0] = 0.0;
+    return;
+  }
+  if (p > TR_KEEP_MAX) p = TR_KEEP_MAX;
+  if (p > k - 1) p = k - 1;
+  const double pivmin = sh_piv;
+  // 1. the p lowest eigenvalues, one warp each (32-section, 33-fold per round)
+  for (int i = w; i < p; i += TD_THREADS / 32) {
+    double L = sh_lo, H = sh_hi;
+    for (int it = 0; it < 40; ++it) {
+      if (!(H - L > 4.4e-16 * fmax(fabs(L), fabs(H)) + 1e-300)) break;
+      const double x = L + (H - L) * (double)(lane + 1) / 33.0;
+      const unsigned m = __ballot_sync(0xffffffffu, sturm_count(a, b2, k, x, pivmin) >= i + 1);
+      const int f = m ? __ffs(m) - 1 : 32;
+      const double nL = f == 0 ? L : L + (H - L) * (double)f / 33.0;
+      const double nH = f == 32 ? H : L + (H - L) * (double)(f + 1) / 33.0;
+      L = nL;
+      H = nH;
+    }
+    if (lane == 0) th[i] = 0.5 * (L + H);
+  }
+  __syncthreads();
+  // 2. their eigenvectors (twisted factorisation, one thread each) into S (k x p)
+  double* S = scr;
+  double* TS = scr + (size_t)p * k;
+  const double tiny = 1e-14 * fmax(fabs(sh_lo), fabs(sh_hi)) + 1e-300;
+  if (tid < p) {
+    double* base = scr + 2 * (size_t)p * k + 4 * (size_t)k * tid;
+    twisted_vector(a, bb, k, th[tid], tiny, base, base + k, base + 2 * k, base + 3 * k,
+                   S + (size_t)tid * k);
+  }
+  __syncthreads();
+  // 3. orthonormalise the columns (Gram-Schmidt twice); stop at a dependent column
+  auto block_dot = [&](const double* x, const double* y) -> double {
+    double v = 0.0;
+    for (int i = tid; i < k; i += TD_THREADS) v += x[i] * y[i];
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh_red[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int i = 0; i < TD_THREADS / 32; ++i) t += sh_red[i];
+    return t;
+  };
+  if (tid == 0) sh_p = p;
+  __syncthreads();
+  for (int c = 0; c < p; ++c) {
+    double* sc = S + (size_t)c * k;
+    const double n0 = sqrt(block_dot(sc, sc));
+    if (!(n0 > 0.0) || !isfinite(n0)) {
+      if (tid == 0) sh_p = c;
+      break;
+    }
+    for (int i = tid; i < k; i += TD_THREADS) sc[i] /= n0;
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass)
+      for (int c2 = 0; c2 < c; ++c2) {
+        const double* s2 = S + (size_t)c2 * k;
+        const double dv = block_dot(s2, sc);
+        for (int i = tid; i < k; i += TD_THREADS) sc[i] -= dv * s2[i];
+        __syncthreads();
+      }
+    const double n1 = sqrt(block_dot(sc, sc));
+    if (!(n1 > 1e-8)) {
+      if (tid == 0) sh_p = c;
+      break;
+    }
+    for (int i = tid; i < k; i += TD_THREADS) sc[i] /= n1;
+    __syncthreads();
+  }
+  __syncthreads();
+  p = sh_p;
+  if (p < 1) {
+    if (tid == 0) out[0] = 0.0;
+    return;
+  }
+  // 4. TS = T S, P = S^T T S, c = beta_{k-1} S[k-1, :]
+  for (int e = tid; e < p * k; e += TD_THREADS) {
+    const int c = e / k, r = e - c * k;
+    const double* sc = S + (size_t)c * k;
+    double v = a[r] * sc[r];
+    if (r > 0) v += bb[r - 1] * sc[r - 1];
+    if (r + 1 < k) v += bb[r] * sc[r + 1];
+    TS[e] = v;
+  }
+  __syncthreads();
+  for (int e = tid; e < p * p; e += TD_THREADS) {
+    const int i = e / p, j = e - i * p;
+    const double* si = S + (size_t)i * k;
+    const double* tj = TS + (size_t)j * k;
+    double v = 0.0;
+    for (int r = 0; r < k; ++r) v += si[r] * tj[r];
+    P[i][j] = v;
+  }
+  for (int i = tid; i < p; i += TD_THREADS) cvec[i] = sh_bk * S[(size_t)i * k + k - 1];
+  __syncthreads();
+  // 5. Lanczos on the symmetrised P from c / |c| (full reorthogonalisation), one thread
+  if (tid == 0) {
+    double cn = 0.0, pn = 0.0;
+    for (int i = 0; i < p; ++i) cn += cvec[i] * cvec[i];
+    for (int i = 0; i < p; ++i)
+      for (int j = 0; j < p; ++j) pn = fmax(pn, fabs(P[i][j]));
+    cn = sqrt(cn);
+    int pp = 0;
+    if (cn > 0.0 && isfinite(cn)) {
+      for (int i = 0; i < p; ++i) W[i][0] = cvec[i] / cn;
+      pp = p;
+      double u[TR_KEEP_MAX];
+      for (int l = 0; l < p; ++l) {
+        for (int i = 0; i < p; ++i) {
+          double v = 0.0;
+          for (int j = 0; j < p; ++j) v += 0.5 * (P[i][j] + P[j][i]) * W[j][l];
+          u[i] = v;
+        }
+        double av = 0.0;
+        for (int i = 0; i < p; ++i) av += W[i][l] * u[i];
+        al[l] = av;
+        if (l + 1 == p) break;
+        for (int pass = 0; pass < 2; ++pass)
+          for (int l2 = 0; l2 <= l; ++l2) {
+            double dv = 0.0;
+            for (int i = 0; i < p; ++i) dv += W[i][l2] * u[i];
+            for (int i = 0; i < p; ++i) u[i] -= dv * W[i][l2];
+          }
+        double bn = 0.0;
+        for (int i = 0; i < p; ++i) bn += u[i] * u[i];
+        bn = sqrt(bn);
+        if (!(bn > 1e-12 * pn)) {
+          pp = l + 1;
+          break;
+        }
+        be[l] = bn;
+        for (int i = 0; i < p; ++i) W[i][l + 1] = u[i] / bn;
+      }
+    }
+    sh_pp = pp;
+    sh_red[0] = cn;
+  }
+  __syncthreads();
+  const int pp = sh_pp;
+  // 6. M[:, i] = S W[:, pp-1-i]; the new recurrence coefficients
+  for (int e = tid; e < pp * k; e += TD_THREADS) {
+    const int i = e / k, r = e - i * k;
+    const int l = pp - 1 - i;
+    double v = 0.0;
+    for (int c = 0; c < p; ++c) v += S[(size_t)c * k + r] * W[c][l];
+    M[(size_t)i * k + r] = v;
+  }
+  if (tid < pp) {
+    alpha[tid] = al[pp - 1 - tid];
+    beta[tid] = tid + 1 < pp ? be[pp - 2 - tid] : sh_red[0];
+  }
+  if (tid == 0) out[0] = (double)pp;
+}
+
+// In place: Q_c[e] = sum_{l<k} M[l + k c] Q_l[e] for c < p <= TR_KEEP_MAX.  Each element's
+// k old values are read before its p new ones are written, so the update is safe in place.
+__global__ void k_combo_multi(double* __restrict__ Q, int64_t stride, int k,
+                              const double* __restrict__ M, int p, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * VT + threadIdx.x; e < n; e += (int64_t)gridDim.x * VT) {
+    double acc[TR_KEEP_MAX];
+#pragma unroll
+    for (int c = 0; c < TR_KEEP_MAX; ++c) acc[c] = 0.0;
+    for (int l = 0; l < k; ++l) {
+      const double q = Q[(int64_t)l * stride + e];
+#pragma unroll
+      for (int c = 0; c < TR_KEEP_MAX; ++c)
+        if (c < p) acc[c] = fma(M[l + (int64_t)k * c], q, acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < TR_KEEP_MAX; ++c)
+      if (c < p) Q[(int64_t)c * stride + e] = acc[c];
+  }
 }
 
 // lowest eigenpair of a small symmetric matrix G (n x n, leading dim ldg) by cyclic Jacobi
@@ -765,11 +1192,17 @@ int dmalloc(DevBuf& b, size_t bytes) {
 // scal layout: [0] theta, [1] resid, [2] status, [3..] scratch scalars
 int lanczos(Ctx& C, int prec, double* x, int max_iter, int kdim, double tol, int fixed,
             int check_every, double* theta_out, double* resid_out, int* iters_out,
-            int gs_passes = 2) {
+            int gs_passes = 2, int thick_keep = 0) {
   const int64_t n = C.n;
   if (kdim < 2) kdim = 2;
   if (kdim > max_iter + 1) kdim = max_iter + 1;
-  DevBuf Qb, wb, ab, bb, hb, sb, tb;
+  if (thick_keep > TR_KEEP_MAX) thick_keep = TR_KEEP_MAX;
+  if (thick_keep > kdim - 1) thick_keep = kdim - 1;
+  DevBuf Qb, wb, ab, bb, hb, sb, tb, Mb, rb;
+  if (thick_keep > 0) {
+    D2_TRY(dmalloc(Mb, sizeof(double) * (size_t)(kdim + 1) * thick_keep));
+    D2_TRY(dmalloc(rb, sizeof(double) * (size_t)thick_keep * (6 * (kdim + 1) + thick_keep)));
+  }
   D2_TRY(dmalloc(Qb, sizeof(double) * (size_t)(kdim + 1) * n));
   D2_TRY(dmalloc(wb, sizeof(double) * n));
   D2_TRY(dmalloc(ab, sizeof(double) * (kdim + 1)));
@@ -809,7 +1242,7 @@ int lanczos(Ctx& C, int prec, double* x, int max_iter, int kdim, double tol, int
     const bool last = total >= max_iter;
     const bool full = j >= kdim;
     if (last || full || (!fixed && total % check_every == 0)) {
-      k_tridiag_ground<<<1, 1, 0, C.s>>>(alpha, beta, j, sv, out3, scr);
+      k_tridiag_ground<<<1, TD_THREADS, 0, C.s>>>(alpha, beta, j, sv, out3, scr);
       D2_CUDA(cudaGetLastError());
       D2_TRY(C.fetch(out3, 3));
       theta = C.hscal[0];
@@ -819,6 +1252,23 @@ int lanczos(Ctx& C, int prec, double* x, int max_iter, int kdim, double tol, int
         break;
       }
       const bool conv = !fixed && resid <= tol * fabs(theta);
+      if (full && !conv && !last && thick_keep > 0) {
+        // thick restart: q_j = w / beta_{j-1} joins the re-tridiagonalised Ritz space
+        D2_TRY(C.scale_inv(Q + (int64_t)j * n, w, beta + j - 1));
+        k_thick_restart<<<1, TD_THREADS, 0, C.s>>>(alpha, beta, j, thick_keep, (double*)Mb.p,
+                                                   (double*)rb.p, C.scal + 7);
+        D2_CUDA(cudaGetLastError());
+        D2_TRY(C.fetch(C.scal + 7, 1));
+        const int pk = (int)C.hscal[0];
+        if (pk >= 1) {
+          k_combo_multi<<<vgrid(n), VT, 0, C.s>>>(Q, n, j, (const double*)Mb.p, pk, n);
+          D2_CUDA(cudaGetLastError());
+          D2_CUDA(cudaMemcpyAsync(Q + (int64_t)pk * n, Q + (int64_t)j * n, sizeof(double) * n,
+                                  cudaMemcpyDeviceToDevice, C.s));
+          j = pk;
+          continue;
+        }
+      }
       if (conv || last || full) {
         D2_TRY(C.combo(x, Q, n, j, sv, 0));  // Ritz vector
         if (conv) {
@@ -908,7 +1358,7 @@ int lanczos_lo(Ctx& C, int prec, double* x, int max_iter, int kdim, double tol, 
     const bool last = total >= max_iter;
     const bool full = j >= kdim;
     if (last || full || total % check_every == 0) {
-      k_tridiag_ground<<<1, 1, 0, C.s>>>(alpha, beta, j, sv, out3, scr);
+      k_tridiag_ground<<<1, TD_THREADS, 0, C.s>>>(alpha, beta, j, sv, out3, scr);
       D2_CUDA(cudaGetLastError());
       D2_TRY(C.fetch(out3, 3));
       theta = C.hscal[0];
@@ -1153,6 +1603,8 @@ extern "C" int dmrg2d_lanczos_ground(const dmrg2d_ops* ops, const dmrg2d_solver_
   if (o.max_iter < 1) return set_error(DMRG2D_EINVAL, "max_iter < 1");
   if (o.krylov_dim > 512 || o.inner_iter > 511)
     return set_error(DMRG2D_EINVAL, "krylov_dim > 512 or inner_iter > 511");
+  if (o.thick_keep < 0 || o.thick_keep > 32)
+    return set_error(DMRG2D_EINVAL, "thick_keep must be in [0, 32]");
   if (o.precision != DMRG2D_FP64 && o.precision != DMRG2D_FP32 && o.precision != DMRG2D_TF32 &&
       o.precision != DMRG2D_BF16)
     return set_error(DMRG2D_EINVAL, "unknown precision %d", o.precision);
@@ -1194,7 +1646,7 @@ extern "C" int dmrg2d_lanczos_ground(const dmrg2d_ops* ops, const dmrg2d_solver_
     double resid = 0.0;
     int iters = 0;
     st = lanczos(C, o.precision, x_inout, o.max_iter, o.krylov_dim, o.tol, o.fixed_steps,
-                 o.check_every, &energy, &resid, &iters);
+                 o.check_every, &energy, &resid, &iters, 2, o.thick_keep);
     local.iters = iters;
     local.resid = resid;
   }
@@ -1210,6 +1662,18 @@ extern "C" int dmrg2d_lanczos_ground(const dmrg2d_ops* ops, const dmrg2d_solver_
   *energy_out = energy;
   if (stats) *stats = local;
   return st;
+}
+
+extern "C" int dmrg2d_tridiag_lowest(const double* alpha, const double* beta, int k, double* s,
+                                     double* out, void* stream) {
+  if (!alpha || !beta || !s || !out) return set_error(DMRG2D_EINVAL, "NULL argument");
+  if (k < 1 || k > TD_MAX) return set_error(DMRG2D_ESHAPE, "k = %d outside [1, %d]", k, TD_MAX);
+  clear_error();
+  const cudaStream_t st = (cudaStream_t)stream;
+  // the fallback's scratch lives past the 3 outputs: out[3 .. 3 + 5k)
+  k_tridiag_ground<<<1, TD_THREADS, 0, st>>>(alpha, beta, k, s, out, out + 3);
+  D2_CUDA(cudaGetLastError());
+  return DMRG2D_OK;
 }
 
 // ---- allocation-free Lanczos for small superblocks ----------------------------------------
@@ -1281,7 +1745,7 @@ int lanczos_in_place(Ctx& C, double* ws, double* x, int max_iter, int kdim, doub
     const bool last = total >= max_iter;
     const bool full = j >= kdim;
     if (last || full || (!fixed && total % check_every == 0)) {
-      k_tridiag_ground<<<1, 1, 0, C.s>>>(alpha, beta, j, sv, out3, scr);
+      k_tridiag_ground<<<1, TD_THREADS, 0, C.s>>>(alpha, beta, j, sv, out3, scr);
       D2_CUDA(cudaGetLastError());
       D2_TRY(C.fetch(out3, 3));
       theta = C.hscal[0];
@@ -1331,19 +1795,32 @@ extern "C" int dmrg2d_lanczos_ground_noalloc(const dmrg2d_ops* ops, const dmrg2d
   if (opts) o = *opts; else dmrg2d_default_solver_opts(&o);
   if (o.precision != DMRG2D_FP64 || o.refine)
     return set_error(DMRG2D_EUNSUPPORTED, "the allocation-free solver runs plain FP64 Lanczos only");
+  if (o.thick_keep != 0)
+    return set_error(DMRG2D_EUNSUPPORTED,
+                     "the allocation-free solver restarts explicitly (thick_keep must be 0)");
   if (o.max_iter < 1) return set_error(DMRG2D_EINVAL, "max_iter < 1");
   int kdim = o.krylov_dim < 2 ? 2 : o.krylov_dim;
   if (kdim > o.max_iter + 1) kdim = o.max_iter + 1;
+  if (kdim > 512)  // the reduction partials and the tridiagonal workspace are sized for 512
+    return set_error(DMRG2D_ESHAPE,
+                     "allocation-free Lanczos: krylov_dim %d (after clamping to max_iter + 1) "
+                     "exceeds 512", kdim);
   const int64_t n = ops->n_vec;
   const int64_t need = (int64_t)(kdim + 2) * n + 10 * (int64_t)(kdim + 1) +
                        (int64_t)RED_BLOCKS * (kdim + 1) + 64;
-  if (kdim > 512 || need > (int64_t)DMRG2D_NOALLOC_SCRATCH_DOUBLES)
+  if (need > (int64_t)DMRG2D_NOALLOC_SCRATCH_DOUBLES)
     return set_error(DMRG2D_ESHAPE,
                      "allocation-free Lanczos needs %lld scratch doubles for n_vec=%lld, "
                      "krylov_dim=%d; the static scratch holds %lld (reduce krylov_dim or use "
                      "dmrg2d_lanczos_ground)",
                      (long long)need, (long long)n, kdim,
                      (long long)DMRG2D_NOALLOC_SCRATCH_DOUBLES);
+  int cur = -1;
+  D2_CUDA(cudaGetDevice(&cur));
+  if (cur != ops->device)
+    return set_error(DMRG2D_EINVAL,
+                     "allocation-free Lanczos: device %d is current but the ops were built on "
+                     "device %d (the static scratch is per device)", cur, ops->device);
   double* ws = nullptr;
   D2_TRY(noalloc_scratch(&ws));
   const auto t0 = std::chrono::steady_clock::now();
@@ -1361,6 +1838,7 @@ extern "C" int dmrg2d_lanczos_ground_noalloc(const dmrg2d_ops* ops, const dmrg2d
   C.part = ws + vec_part;
   C.scal = C.part + (int64_t)RED_BLOCKS * (kdim + 1);
   D2_CUDA(cudaMemsetAsync(C.scal, 0, 64 * sizeof(double), C.s));
+  D2_TRY(sec_zero_padding(ops, x_inout, C.s));  // restricted layouts: padding rows stay zero
   double energy = 0.0, resid = 0.0;
   int iters = 0;
   int st = lanczos_in_place(C, ws, x_inout, o.max_iter, kdim, o.tol, o.fixed_steps, o.check_every,

@@ -69,7 +69,8 @@ class SolverOpts(C.Structure):
     _fields_ = [("max_iter", C.c_int), ("krylov_dim", C.c_int), ("tol", C.c_double),
                 ("fixed_steps", C.c_int), ("precision", C.c_int), ("refine", C.c_int),
                 ("inner_iter", C.c_int), ("outer_max", C.c_int), ("check_every", C.c_int),
-                ("start_reorth", C.c_int), ("refine_precision", C.c_int)]
+                ("start_reorth", C.c_int), ("refine_precision", C.c_int),
+                ("thick_keep", C.c_int)]
 
 
 class DavidsonOpts(C.Structure):
@@ -99,6 +100,8 @@ SIGNATURES = {
                                                 C.POINTER(C.c_double), C.POINTER(SolverStats),
                                                 C.c_void_p]),
     "dmrg2d_default_solver_opts": (None, [C.POINTER(SolverOpts)]),
+    "dmrg2d_tridiag_lowest": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                                        C.c_void_p]),
     "dmrg2d_wait_selftest": (C.c_int, [C.c_double, C.c_void_p]),
     "dmrg2d_sweep": (C.c_int, [C.POINTER(Model), C.POINTER(SweepOpts), C.POINTER(SweepReport),
                                C.c_void_p]),
@@ -359,6 +362,24 @@ def lanczos_ground_noalloc(ops: Ops, x, stream=None, **opts):
     if code not in (0, -5):
         _check(code)
     return e.value, {k: getattr(st, k) for k, _ in SolverStats._fields_}, code
+
+
+def tridiag_lowest(alpha, beta, stream=None):
+    """Lowest eigenpair of the tridiagonal (alpha, beta[:k-1]) on the device
+    (dmrg2d_tridiag_lowest); alpha, beta: CUDA float64 tensors of k elements.
+    Returns (eigenvalue, eigenvector tensor, residual estimate |beta[k-1] s[k-1]|, status)."""
+    import torch
+    k = alpha.numel()
+    for t in (alpha, beta):
+        if not t.is_cuda or str(t.dtype) != "torch.float64" or t.numel() != k:
+            raise ValueError("alpha, beta: CUDA float64 tensors of equal length")
+    s = torch.empty(k, dtype=torch.float64, device=alpha.device)
+    out = torch.empty(3 + 5 * k, dtype=torch.float64, device=alpha.device)
+    _check(lib().dmrg2d_tridiag_lowest(C.c_void_p(alpha.data_ptr()), C.c_void_p(beta.data_ptr()),
+                                       int(k), C.c_void_p(s.data_ptr()),
+                                       C.c_void_p(out.data_ptr()), _stream(stream)))
+    o = out[:3].cpu().numpy()
+    return float(o[0]), s, float(o[1]), int(o[2])
 
 
 PRECOND = {"none": 0, "jacobi": 1, "mlp": 2}

@@ -118,3 +118,109 @@ def test_mixed_precision_reaches_fp64_energy(ladder2_m128, prec, rprec):
     assert abs(e - e64) <= 1e-8 * abs(e64), (e, e64, st)
     assert st["resid"] <= 1e-8 * abs(e)
     assert st["n_hv_fp64"] < st64["n_hv_fp64"], (st, st64)
+
+
+# ---- the small eigensolve (a tridiagonal's lowest eigenpair) ------------------------------
+
+def _tridiag_gpu(a, b):
+    at = torch.tensor(np.asarray(a, float), device=DEV)
+    bt = torch.tensor(np.asarray(b, float), device=DEV)
+    th, s, res, status = dmrg2d.tridiag_lowest(at, bt)
+    return th, s.cpu().numpy(), res, status
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 50, 257, 512])
+def test_tridiag_lowest_laplacian_closed_form(k):
+    # T = tridiag(-1, 2, -1): lowest eigenvalue 2 - 2 cos(pi / (k + 1)), eigenvector
+    # sin(j pi / (k + 1)), j = 1..k
+    a, b = np.full(k, 2.0), np.full(k, -1.0)
+    b[k - 1] = 0.5                      # the residual coupling, not part of T
+    th, s, res, status = _tridiag_gpu(a, b)
+    assert status == 0
+    lam = 2.0 - 2.0 * np.cos(np.pi / (k + 1))
+    assert abs(th - lam) <= 1e-14 * 4
+    v = np.sin(np.arange(1, k + 1) * np.pi / (k + 1))
+    v /= np.linalg.norm(v)
+    assert np.abs(s - v).max() <= 1e-10
+    assert abs(res - 0.5 * abs(v[-1])) <= 1e-12
+
+
+@pytest.mark.parametrize("k,seed,scale", [(7, 0, 1.0), (64, 1, 1e3), (200, 2, 1e-2), (512, 3, 1.0)])
+def test_tridiag_lowest_against_eigh(k, seed, scale):
+    rng = np.random.default_rng(seed)
+    a, b = scale * rng.standard_normal(k), scale * rng.standard_normal(k)
+    if k > 20:
+        b[k // 2] = 0.0                 # a reducible T: the lowest pair may sit in either part
+    th, s, res, status = _tridiag_gpu(a, b)
+    T = np.diag(a) + np.diag(b[:k - 1], 1) + np.diag(b[:k - 1], -1)
+    w, V = np.linalg.eigh(T)
+    assert status == 0
+    assert abs(th - w[0]) <= 1e-13 * np.abs(w).max()
+    assert np.linalg.norm(T @ s - th * s) <= 1e-12 * np.abs(w).max()
+    assert abs(np.linalg.norm(s) - 1.0) <= 1e-13
+    first = s[np.flatnonzero(s)[0]]
+    assert first > 0
+    if w[1] - w[0] > 1e-6 * np.abs(w).max():     # a simple eigenvalue: the vector is unique
+        assert abs(abs(s @ V[:, 0]) - 1.0) <= 1e-10
+
+
+def test_tridiag_lowest_rejects_bad_sizes_and_reports_nan():
+    a = torch.zeros(513, dtype=torch.float64, device=DEV)
+    with pytest.raises(dmrg2d.Dmrg2dError) as e:
+        dmrg2d.tridiag_lowest(a, a.clone())
+    assert e.value.code == -2
+    a = torch.tensor([1.0, float("nan"), 2.0], dtype=torch.float64, device=DEV)
+    th, s, res, status = dmrg2d.tridiag_lowest(a, torch.ones_like(a))
+    assert status == 1 and np.isnan(th)
+
+
+# ---- thick restart --------------------------------------------------------------------------
+
+def test_thick_restart_reaches_the_oracle_energy_in_fewer_steps():
+    mdl, left, right, _ = synth.workload_ladder2_heisenberg_m64()
+    ops = dmrg2d.build_ops(mdl, left, right)
+    sb = Superblock(mdl, left, right)
+    v0 = synth.start_vector(ops.info["n_vec"], 4)
+    e_ref, _, _ = oracle_lanczos(sb.apply, v0, max_iter=400, tol=1e-12)
+    e_x, _, st_x, c_x = gpu_ground(ops, v0, max_iter=3000, krylov_dim=30, tol=1e-11)
+    e_t, x_t, st_t, c_t = gpu_ground(ops, v0, max_iter=3000, krylov_dim=30, tol=1e-11,
+                                     thick_keep=8)
+    assert c_x == 0 and c_t == 0
+    assert abs(e_t - e_ref) <= 1e-10 * abs(e_ref), (e_t, e_ref)
+    assert abs(e_x - e_ref) <= 1e-10 * abs(e_ref), (e_x, e_ref)
+    assert st_t["iters"] < st_x["iters"], (st_t, st_x)
+    r = sb.apply(x_t) - e_t * x_t        # an eigenvector of the oracle's H
+    assert np.linalg.norm(r) <= 1e-9 * abs(e_t)
+    # deterministic, and every kept-space size gives the same eigenpair
+    e_t2, x_t2, _, _ = gpu_ground(ops, v0, max_iter=3000, krylov_dim=30, tol=1e-11, thick_keep=8)
+    assert e_t2 == e_t and np.array_equal(x_t2, x_t)
+    for keep in (1, 20, 29):
+        e_k, _, st_k, c_k = gpu_ground(ops, v0, max_iter=3000, krylov_dim=30, tol=1e-11,
+                                       thick_keep=keep)
+        assert c_k == 0 and abs(e_k - e_ref) <= 1e-10 * abs(e_ref), (keep, e_k, st_k)
+
+
+def test_thick_restart_on_a_sector_superblock():
+    # sector layout: the kept Ritz vectors and the continuation vector stay zero on padding
+    grid = [(a, b) for a in (-1, 0, 1) for b in (-1, 0, 1)]
+    offs, sizes = synth.sector_sizes(grid, (1.0, 1.0), 12, 4, lo=1)
+    lab = synth.labels_from_sectors((2, 2), offs, sizes)
+    mdl = synth.model("hubbard", 2, t=1.0, U=8.0)
+    left, right = synth.hubbard_block(12, 2, 4, lab), synth.hubbard_block(12, 2, 5, lab)
+    ops = dmrg2d.build_ops(mdl, left, right, target=(5, 6))
+    pad = dmrg2d.sector_dense_index(ops) < 0
+    v0 = np.where(pad, 0.0, synth.start_vector(ops.info["n_vec"], 2))
+    e_full, _, _, c0 = gpu_ground(ops, v0, max_iter=400, krylov_dim=400, tol=1e-11)
+    e, x, st, code = gpu_ground(ops, v0, max_iter=3000, krylov_dim=24, tol=1e-11, thick_keep=6)
+    assert c0 == 0 and code == 0
+    assert abs(e - e_full) <= 1e-10 * abs(e_full)
+    assert np.all(x[pad] == 0.0)
+
+
+def test_thick_keep_is_validated():
+    mdl, left, right, _ = synth.workload_ladder2_heisenberg_m64()
+    ops = dmrg2d.build_ops(mdl, left, right)
+    x = torch.from_numpy(synth.start_vector(ops.info["n_vec"], 4)).to(DEV)
+    with pytest.raises(dmrg2d.Dmrg2dError) as e:
+        dmrg2d.lanczos_ground(ops, x, thick_keep=33)
+    assert e.value.code == -1
