@@ -164,6 +164,12 @@ __global__ void k_scatter_col(const double* __restrict__ Q, int ldq, int qcol, i
     U[idx[i] + ldu * col] = Q[i + (int64_t)ldq * qcol];
 }
 
+// U[pos[i]] = 1 (the unit-vector columns of zero-weight kept states)
+__global__ void k_set_ones(double* __restrict__ U, const int64_t* __restrict__ pos, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    U[pos[i]] = 1.0;
+}
+
 // xorshift64* stream for the start vectors (values in (-1, 1))
 struct Rng {
   uint64_t s;
@@ -257,10 +263,9 @@ class Sweeper {
     right[1] = column_block();
     for (int l = 1; l < half; ++l) {  // warm-up: block 1 and its mirror image grow together
       if (hub_) {  // electrons: block 4 grows from its own density matrix (a mirrored
-                   // block would have the reversed mode order)
+                   // block would have the reversed mode order); one ground state serves both
         Block nl, nr;
-        D2_TRY(step(left[l], right[l], true, o_.m_warmup, l, -1, &nl, nullptr));
-        D2_TRY(step(left[l], right[l], false, o_.m_warmup, l, -1, &nr, nullptr));
+        D2_TRY(step(left[l], right[l], true, o_.m_warmup, l, -1, &nl, nullptr, &nr));
         left[l + 1] = nl;
         right[l + 1] = nr;
         continue;
@@ -504,26 +509,74 @@ class Sweeper {
       r0 += qld[q];
       c0 += qcols[q];
     }
+    // Labels of the enlarged block that no V_q holds (the superblock's target leaves them
+    // empty, as the smaller superblocks of the warm-up do for labels only the full filling
+    // reaches): the density matrix is zero there, and their states are candidates of
+    // weight 0 (unit vectors), kept while m allows, so that later superblocks find them.
+    const Block& B = grow_left ? Lb : Rb;
+    const int64_t n = (int64_t)B.m * col_.d;
+    std::map<int, int> lab_q;  // label -> q
+    for (int q = 0; q < nQ; ++q) lab_q[lab[q]] = q;
+    std::map<int, std::vector<int64_t>> unreached;  // label -> its states (dense index)
+    for (int64_t e = 0; e < n; ++e) {
+      const int le = enlarged_label(B, e);
+      if (!lab_q.count(le)) unreached[le].push_back(e);
+    }
+    std::vector<int64_t> unit_idx;  // Cand with q < 0: unit vector at unit_idx[-q-1]
+    std::vector<int> unit_lab;
+    {  // candidates in label order (ties in weight keep the lower label, then the order)
+      std::vector<int> all_labels;
+      for (auto& kv : lab_q) all_labels.push_back(kv.first);
+      for (auto& kv : unreached) all_labels.push_back(kv.first);
+      std::sort(all_labels.begin(), all_labels.end());
+      std::vector<Cand> ordered;
+      for (int le : all_labels) {
+        auto it = lab_q.find(le);
+        if (it != lab_q.end()) {
+          for (const Cand& c : cand)
+            if (c.q == it->second) ordered.push_back(c);
+        } else {
+          for (int64_t e : unreached[le]) {
+            unit_idx.push_back(e);
+            unit_lab.push_back(le);
+            ordered.push_back({0.0, -(int)unit_idx.size(), 0});
+          }
+        }
+      }
+      cand.swap(ordered);
+    }
+    auto cand_label = [&](const Cand& c) { return c.q >= 0 ? lab[c.q] : unit_lab[-c.q - 1]; };
     std::stable_sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& b) { return a.w > b.w; });
-    const int k = std::min(*kio, (int)cand.size());  // states of the target-compatible sectors
+    const int k = std::min(*kio, (int)cand.size());
     *kio = k;
     std::vector<Cand> keep(cand.begin(), cand.begin() + k);
     std::stable_sort(keep.begin(), keep.end(), [&](const Cand& a, const Cand& b) {
-      return lab[a.q] < lab[b.q];  // group by label; stable keeps decreasing weight
+      return cand_label(a) < cand_label(b);  // group by label; stable keeps decreasing weight
     });
-    const int64_t n = (int64_t)(grow_left ? Lb.m : Rb.m) * col_.d;
     D2_TRY(U.alloc((size_t)(n * k)));
     D2_CUDA(cudaMemsetAsync(U.p, 0, (size_t)n * k * sizeof(double), strm_));
     *kept = 0.0;
     labels->clear();
+    std::vector<int64_t> ones;  // flat positions (row + n col) of the unit vectors' 1s
     for (int c = 0; c < k; ++c) {
       const Cand& cd = keep[(size_t)c];
-      k_scatter_col<<<64, 256, 0, strm_>>>(vecs[cd.q]->p, dim[cd.q], cd.j, dim[cd.q],
-                                           (const int64_t*)idx[cd.q]->p, U.p, n, c);
-      *kept += cd.w;
-      labels->push_back(lab[cd.q]);
+      if (cd.q >= 0) {
+        k_scatter_col<<<64, 256, 0, strm_>>>(vecs[cd.q]->p, dim[cd.q], cd.j, dim[cd.q],
+                                             (const int64_t*)idx[cd.q]->p, U.p, n, c);
+        *kept += cd.w;
+      } else {
+        ones.push_back(unit_idx[(size_t)(-cd.q - 1)] + n * c);
+      }
+      labels->push_back(cand_label(cd));
     }
     D2_CUDA(cudaGetLastError());
+    if (!ones.empty()) {
+      IBuf d_ones;
+      D2_TRY(d_ones.upload(ones, strm_));
+      k_set_ones<<<64, 256, 0, strm_>>>(U.p, (const int64_t*)d_ones.p, (int)ones.size());
+      D2_CUDA(cudaGetLastError());
+      D2_CUDA(cudaStreamSynchronize(strm_));  // d_ones is freed on return
+    }
     return DMRG2D_OK;
   }
 
@@ -609,7 +662,7 @@ class Sweeper {
 
   // One DMRG step on block 1 = L, block 4 = R; grows L (grow_left) or R into *out.
   int step(const Block& Lb, const Block& Rb, bool grow_left, int m_keep, int l, int sweep,
-           Block* out, const DBuf* guess) {
+           Block* out, const DBuf* guess, Block* out_other = nullptr) {
     // ---- HMED: superblock ground state -------------------------------------------------
     std::vector<const double*> le, re;
     for (auto& e : Lb.edge) le.push_back(e.data());
@@ -720,21 +773,9 @@ class Sweeper {
     double norm2 = 0.0;  // trace of rho = |x|^2
     D2_BLAS(cublasDdot(libs_.bl, (int)nv, x.p, 1, x.p, 1, &norm2));
     // ---- DMF + DMD: k leading eigenvectors of the growing half's density matrix ----------
-    const int mb = grow_left ? Lb.m : Rb.m;  // block that grows
-    const int64_t n = (int64_t)mb * d;
-    int k = (int)std::min<int64_t>(m_keep, n);
-    auto Up = std::make_shared<DBuf>();
-    DBuf& U = *Up;
-    std::vector<int32_t> labels;
-    double kept = 0.0;
-    if (sec) {  // k may shrink to the states the target sector leaves
-      D2_TRY(dmd_sectors(x.p, grow_left, Lb, Rb, qbase, qld, qcols, rowL, colR, &k, U, &kept,
-                         &labels));
-    } else {
-      D2_TRY(U.alloc((size_t)(n * k)));
-      D2_TRY(dmd_dense(x.p, grow_left, n, nd / n, k, U, &kept));
-    }
-    kept /= norm2;
+    const SecLayout lay{sec, nd, &qbase, &qld, &qcols, &rowL, &colR};
+    Grown g;
+    D2_TRY(dmd(grow_left, Lb, Rb, m_keep, x.p, norm2, lay, &g));
     dm_seconds += since(td);
     // observables of this step's ground state (<S_tot^2> only where no block is grown:
     // the last step of each sweep)
@@ -756,9 +797,68 @@ class Sweeper {
       s2 /= norm2;
     }
     obs_seconds += since(to);
-    record(energy, 1.0 - kept, l, sweep, stats.iters, leg, rung, s2, dens);
+    record(energy, 1.0 - g.kept, l, sweep, stats.iters, leg, rung, s2, dens);
     if (!out) return DMRG2D_OK;
-    // ---- renormalisation: U^T O U for H_enl and the new boundary operators ----------------
+    D2_TRY(renorm(grow_left, Lb, Rb, g, out));
+    if (out_other) {  // the other half from the same ground state (Hubbard warm-up)
+      const auto t2 = std::chrono::steady_clock::now();
+      Grown g2;
+      D2_TRY(dmd(!grow_left, Lb, Rb, m_keep, x.p, norm2, lay, &g2));
+      dm_seconds += since(t2);
+      D2_TRY(renorm(!grow_left, Lb, Rb, g2, out_other));
+    }
+    return DMRG2D_OK;
+  }
+
+  // The sector layout of a superblock vector (empty for a dense superblock), as dmd needs it.
+  struct SecLayout {
+    bool sec;
+    int64_t nd;  // elements of the dense V
+    const std::vector<long long>* qbase;
+    const std::vector<int>* qld;
+    const std::vector<int>* qcols;
+    const std::vector<int64_t>* rowL;
+    const std::vector<int64_t>* colR;
+  };
+  // What DMD hands to the renormalisation: U (n x k, n = mb d), the kept states' labels
+  // (sectors) and the kept weight (divided by |x|^2).
+  struct Grown {
+    std::shared_ptr<DBuf> U;
+    std::vector<int32_t> labels;
+    int k = 0, mb = 0;
+    int64_t n = 0;
+    double kept = 0.0;
+  };
+
+  // DMF + DMD of the half that grows (grow_left: block 1 + column 2), from the ground state
+  // x of the superblock of Lb and Rb (packed if lay.sec).
+  int dmd(bool grow_left, const Block& Lb, const Block& Rb, int m_keep, const double* x,
+          double norm2, const SecLayout& lay, Grown* g) {
+    const int d = col_.d;
+    g->mb = grow_left ? Lb.m : Rb.m;  // block that grows
+    g->n = (int64_t)g->mb * d;
+    int k = (int)std::min<int64_t>(m_keep, g->n);
+    g->U = std::make_shared<DBuf>();
+    double kept = 0.0;
+    if (lay.sec) {
+      D2_TRY(dmd_sectors(x, grow_left, Lb, Rb, *lay.qbase, *lay.qld, *lay.qcols, *lay.rowL,
+                         *lay.colR, &k, *g->U, &kept, &g->labels));
+    } else {
+      D2_TRY(g->U->alloc((size_t)(g->n * k)));
+      D2_TRY(dmd_dense(x, grow_left, g->n, lay.nd / g->n, k, *g->U, &kept));
+    }
+    g->k = k;
+    g->kept = kept / norm2;
+    return DMRG2D_OK;
+  }
+
+  // Renormalisation: the new block U^T O U from the block B that grew (Lb if grow_left).
+  int renorm(bool grow_left, const Block& Lb, const Block& Rb, Grown& g, Block* out) {
+    auto Up = g.U;
+    DBuf& U = *Up;
+    const int mb = g.mb, k = g.k;
+    const int64_t n = g.n;
+    const std::vector<int32_t>& labels = g.labels;
     const auto tr = std::chrono::steady_clock::now();
     const Block& B = grow_left ? Lb : Rb;
     DBuf dHB;

@@ -135,3 +135,54 @@ def test_hubbard_ladder_sweep_equals_ed():
     sweep reproduces ED at every step: energy, the central columns' hole density and the
     vanishing staggered spin density."""
     _hubbard_exact(2, 6, 1, 1, 16, 4, 3)
+
+
+def test_hubbard_chain_sweep_equals_ed_at_every_step():
+    """1 x 6 Hubbard chain, U = 8, 2 up + 2 down electrons, m = 64 (every state kept).
+    The warm-up's 4-site superblock targets the rounded filling (1, 1), so labels such as
+    (2, 0) carry no weight there; the blocks keep their states with weight 0, as the oracle
+    does, and every finite step then reproduces ED (energy, densities), the warm-up step
+    the oracle's energy."""
+    from oracle import dmrg_fermion as odf
+    from test_oracle_densities import ed_site_densities
+    mdl = synth.model("hubbard", 1, t=1.0, U=8.0)
+    out = dmrg2d.sweep(mdl, 6, 64, [64, 64], sectors=True, n_up=2, n_dn=2, tol=1e-12,
+                       max_iter=400, krylov_dim=200)
+    ref = odf.dmrg(mdl, 6, 2, 2, m_warmup=64, m_sweeps=[64, 64])
+    e_ed, n_ed = ed_site_densities(1, 6, 2, 2)
+    warm = [k for k, s in enumerate(out["sweep"]) if s < 0]
+    fin = [k for k, s in enumerate(out["sweep"]) if s >= 0]
+    assert len(warm) == 1 and len(fin) == 2 * 5
+    assert abs(out["energy"][warm[0]] - ref["energy"][0]) <= 1e-10 * abs(ref["energy"][0])
+    for k in fin:
+        assert abs(out["energy"][k] - e_ed) <= 1e-9 * abs(e_ed), (k, out["energy"][k], e_ed)
+        assert out["trunc"][k] <= 1e-12
+        l = out["l"][k]
+        assert np.allclose(out["n"][k], n_ed[l:l + 2], atol=1e-7), (k, l)
+        assert np.max(np.abs(out["sd"][k])) <= 1e-7
+
+
+@pytest.mark.parametrize("n_up,n_dn,m", [(3, 2, 8), (2, 1, 6)])
+def test_truncated_hubbard_ladder_sweep_matches_oracle(n_up, n_dn, m):
+    """2 x 6 Hubbard ladder, U = 8, truncated to m states, where every cut of the oracle's
+    run falls in a gap of the density-matrix spectrum (kept weight >= 1e-4, relative gap
+    >= 0.17 at (3, 2), m = 8; >= 8e-4 and 0.33 at (2, 1), m = 6): the kept subspaces are
+    unique, so the GPU sweep equals the oracle step by step (energies, truncation errors,
+    densities).  The oracle also records the full-lattice superblock at the end of its
+    warm-up, which the library measures as the first step of sweep 0."""
+    from oracle import dmrg_fermion as odf
+    mdl = synth.model("hubbard", 2, t=1.0, U=8.0)
+    out = dmrg2d.sweep(mdl, 6, m, [m, m], sectors=True, n_up=n_up, n_dn=n_dn, tol=1e-12,
+                       max_iter=600, krylov_dim=200)
+    ref = odf.dmrg(mdl, 6, n_up, n_dn, m_warmup=m, m_sweeps=[m, m])
+    keep = [k for k in range(len(ref["l"])) if not (ref["sweep"][k] < 0 and ref["l"][k] == 2)]
+    assert out["l"] == [ref["l"][k] for k in keep]
+    assert out["sweep"] == [ref["sweep"][k] for k in keep]
+    for i, k in enumerate(keep):
+        assert abs(out["energy"][i] - ref["energy"][k]) <= 1e-9 * abs(ref["energy"][k]), \
+            (i, out["energy"][i], ref["energy"][k])
+        last_of_sweep = k + 1 == len(ref["l"]) or ref["sweep"][k + 1] != ref["sweep"][k]
+        if not last_of_sweep:   # the oracle records 0 at its measure-only middle step
+            assert abs(out["trunc"][i] - ref["trunc"][k]) <= 1e-9, \
+                (i, out["trunc"][i], ref["trunc"][k])
+        assert np.allclose(out["n"][i], np.asarray(ref["n"][k]), atol=1e-7), i
