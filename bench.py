@@ -56,6 +56,23 @@ def ncu_traffic(config_name, dtype):
         return None
     return NCU_TRAFFIC["bytes"].get(f"{config_name}|{dtype}")
 WORKLOAD = "ladder3_hubbard_d64_m256_dense"
+# the synthetic superblocks of the benchmark: name -> (builder, H·v precision by default,
+# configuration keys of the JSON line)
+WORKLOADS = {
+    "ladder3_hubbard_d64_m256_dense": (
+        lambda synth: synth.workload_ladder3_hubbard_m256(), "tf32",
+        {"m": 256, "d": 64, "n_legs": 3, "t": 1.0, "U": 8.0}),
+    "ladder4_heisenberg_d16_m1024_sectors": (
+        lambda synth: synth.workload_ladder4_heisenberg_sectors(), "bf16",
+        {"m": 1024, "d": 16, "n_legs": 4, "J": 1.0, "sectors": "S^z_tot = 0, 7 block sectors"}),
+    "ladder3_hubbard_d64_m1024_sectors": (
+        lambda synth: synth.workload_ladder3_hubbard_sectors(), "tf32",
+        {"m": 1024, "d": 64, "n_legs": 3, "t": 1.0, "U": 8.0,
+         "sectors": "(N_up, N_dn) = (15, 15), 25 block sectors"}),
+    "ladder2_heisenberg_d4_m64": (
+        lambda synth: synth.workload_ladder2_heisenberg_m64(), "fp64",
+        {"m": 64, "d": 4, "n_legs": 2, "J": 1.0}),
+}
 
 
 def peaks():
@@ -113,15 +130,17 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(seconds: float = 15.0):
+def cpu_baseline(seconds: float = 15.0, workload: str = WORKLOAD):
     """The oracle's H·v on the same workload, timed on a bounded slab of its outputs.
 
     The slab is rows i1 < r of every tile in the first i3-column of V; its
-    algorithmic work is the fraction (r/m1)(1/d) of one H·v.
+    algorithmic work is the fraction (r/m1)(1/d) of one H·v.  The oracle applies the
+    dense superblock (it has no sector layout): for a sector workload the rate is that of
+    the dense form of the same blocks.
     """
     from oracle.superblock import Superblock
     from paper_0707_0159_gb300 import synth
-    mdl, left, right, _ = synth.workload_ladder3_hubbard_m256()
+    mdl, left, right, _ = WORKLOADS[workload][0](synth)
     sb = Superblock(mdl, left, right)
     v = synth.start_vector(sb.n_vec, 12)
     t0 = time.perf_counter()
@@ -172,17 +191,17 @@ def run_reference(args):
         return 0
     vals = []
     for _ in range(args.warmup):
-        cpu_baseline(seconds=3.0)
+        cpu_baseline(seconds=3.0, workload=args.workload)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(cpu_baseline(seconds=float(args.ref_seconds)))
+        vals.append(cpu_baseline(seconds=float(args.ref_seconds), workload=args.workload))
     total = time.perf_counter() - t0
     v = statistics.median([x["value"] for x in vals])
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s", "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded blocks, numpy default_rng)",
-            "config": {"workload": WORKLOAD, "m": 256, "d": 64, "n_legs": 3, "t": 1.0, "U": 8.0},
+            "config": {"workload": args.workload, **WORKLOADS[args.workload][2]},
             "cpu_baseline": dict(vals[-1], value=v),
             "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -253,16 +272,21 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     prec = dmrg2d.PRECISION[args.precision]
 
-    mdl, left, right, _ = synth.workload_ladder3_hubbard_m256()
-    ops = dmrg2d.build_ops(mdl, left, right)
+    build, _, wl_config = WORKLOADS[args.workload]
+    mdl, left, right, target = build(synth)
+    ops = dmrg2d.build_ops(mdl, left, right, target=target)
     info = ops.info
     n, flops = info["n_vec"], info["flops_per_apply"]
+    pad = dmrg2d.sector_dense_index(ops) < 0 if target is not None else None
     if prec in (dmrg2d.TF32, dmrg2d.BF16) and not info["tc_ok"]:
         raise RuntimeError("tensor-core path unavailable for this workload")
     in_dt = {dmrg2d.FP64: torch.float64, dmrg2d.FP32: torch.float32, dmrg2d.TF32: torch.float32,
              dmrg2d.BF16: torch.bfloat16}[prec]
     out_dt = torch.float64 if prec == dmrg2d.FP64 else torch.float32
-    v_host = torch.from_numpy(synth.start_vector(n, 12 + rank)).to(in_dt)
+    v_np = synth.start_vector(n, 12 + rank)
+    if pad is not None:
+        v_np[pad] = 0.0   # padding rows of a sector layout are zero on input
+    v_host = torch.from_numpy(v_np).to(in_dt)
     v = v_host.to(dev)
     y = torch.empty(n, dtype=out_dt, device=dev)
     stream = torch.cuda.current_stream()
@@ -281,6 +305,13 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
+    # inputs and outputs larger than L2 (129 MB) need no flush; smaller ones get an L2
+    # flush (a 512 MB write) between timed H·v, each H·v timed on its own
+    io_bytes = v.numel() * v.element_size() + y.numel() * y.element_size()
+    flush = io_bytes < 2 * 129 * 2 ** 20
+    l2_note = ("inputs larger than L2 (no flush)" if not flush else
+               "L2 flushed (512 MB write) between timed H·v, each timed on its own")
+    scratch = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev) if flush else None
     for _ in range(args.warmup):
         dmrg2d.apply_H(ops, v, y, prec)
     torch.cuda.synchronize()
@@ -290,16 +321,29 @@ def run_ours(args):
     clk.start()
     time.sleep(0.3)
     dmrg2d.profile_start(ops, args.steps)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        dmrg2d.apply_H(ops, v, y, prec)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    if not flush:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            dmrg2d.apply_H(ops, v, y, prec)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms = e0.elapsed_time(e1) / args.steps
+    else:
+        evs = []
+        for _ in range(args.steps):
+            scratch.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            dmrg2d.apply_H(ops, v, y, prec)
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        step_ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
     k_ms, k_n = dmrg2d.profile_stop(ops)
     clocks = clk.stop()
     barrier()
-    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dev)
+    ms = max_over_ranks(step_ms, dev)
     value = job_tflops(flops, ms, world)
 
     # ---- end to end through the same call: pinned host -> device -> H·v -> host ----
@@ -385,7 +429,8 @@ def run_ours(args):
         peak, pnote, bound = 2 * 152 * 128 * 2.07e9 / 1e12, "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz", "alu"
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak,
-            "traffic": ncu_traffic(tune["name"], out_dtype) if tune else None,
+            "traffic": (ncu_traffic(tune["name"], out_dtype)
+                        if tune and args.workload == WORKLOAD else None),
             "peak_source": pnote,
             "kernel_ms": kernel_ms, "kernel_launches": k_n}
 
@@ -394,19 +439,22 @@ def run_ours(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": out_dtype,
            "data": "synthetic (seeded blocks and vector, numpy default_rng)",
-           "config": {"workload": WORKLOAD, "m": 256, "d": 64, "n_legs": 3, "t": 1.0, "U": 8.0,
+           "config": {"workload": args.workload, **wl_config,
                       "n_vec": n, "flops_per_hv": flops, "parallelism": f"replicas{world}",
-                      "l2": "inputs larger than L2 (no flush)", "tile_config": tune},
+                      "l2": l2_note, "tile_config": tune},
            "clocks": clocks, "e2e": e2e,
-           "gpu_launches": k_n,
+           "gpu_launches": k_n * kernels_per_hv(tune, prec, target is not None),
            "roofline": roof}
 
-    if args.tte and rank == 0:
+    if args.tte and rank == 0 and prec != dmrg2d.FP64:
         out["time_to_energy"] = time_to_energy(ops, n, prec, args, dev)
+    if prec == dmrg2d.FP64 and rank == 0:   # the small superblock: latency per H·v and step
+        out["latency"] = {"us_per_hv": ms * 1e3, **lanczos_latency(ops, n, dev)}
     if args.sweep and rank == 0:
         out["dmrg_sweep"] = dmrg_sweep_run(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(seconds=float(args.ref_seconds))
+        out["cpu_baseline"] = cpu_baseline(seconds=float(args.ref_seconds),
+                                           workload=args.workload)
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
@@ -446,6 +494,33 @@ def dmrg_sweep_run(args):
             "leg_bond_profile_last_sweep": profile}
 
 
+def kernels_per_hv(tune, prec, sectors):
+    """Kernel launches of one dmrg2d_apply_H: the tensor-core configurations launch one
+    kernel, or two with the scalar moves in their own kernel (14..19), or three for the
+    segment kernels (22: two passes and the moves); the CUDA-core FP64/FP32 H·v one kernel
+    on a dense superblock and two (sub-blocks, moves) on a sector layout."""
+    if tune is None:
+        return 2 if sectors else 1
+    c = tune["chosen"]
+    return 3 if c == 22 else (2 if 14 <= c < 20 else 1)
+
+
+def lanczos_latency(ops, n, dev, steps=200):
+    """Plain FP64 Lanczos, fixed steps, from a seeded start: wall time per step (H·v, the
+    recurrence, two Gram-Schmidt passes and the tridiagonal eigenpair at the end)."""
+    import torch
+    from paper_0707_0159_gb300 import dmrg2d, synth
+    x = torch.from_numpy(synth.start_vector(n, 2)).to(dev)
+    dmrg2d.lanczos_ground(ops, x.clone(), max_iter=steps, krylov_dim=steps, fixed_steps=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e, st, code = dmrg2d.lanczos_ground(ops, x, max_iter=steps, krylov_dim=steps, fixed_steps=1)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"steps": steps, "us_per_step": dt / steps * 1e6, "energy": e, "status": code,
+            "hv_us_per_step": st["hv_ms"] / steps * 1e3}
+
+
 def time_to_energy(ops, n, prec, args, dev):
     """Ground energy to a residual of tol*|E| from the same start vector: the mixed
     solver (low-precision H·v + an outer Rayleigh-Ritz loop whose H·v is FP64 emulated
@@ -455,7 +530,10 @@ def time_to_energy(ops, n, prec, args, dev):
     from paper_0707_0159_gb300 import dmrg2d, synth
     v0 = torch.from_numpy(synth.start_vector(n, 3)).to(dev)
     res = {"tol_rel_residual": args.tte_tol}
-    for key, rprec in (("mixed", "fp64x"), ("mixed_fp64_refine", "fp64")):
+    # float-pair FP64 (FP64X) refinement H·v exists for dense superblocks only
+    dense = ops.info["n_sectors"] == 0
+    runs = (("mixed", "fp64x"), ("mixed_fp64_refine", "fp64")) if dense else (("mixed", "fp64"),)
+    for key, rprec in runs:
         x = v0.clone()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -468,15 +546,36 @@ def time_to_energy(ops, n, prec, args, dev):
                     "seconds": time.perf_counter() - t0, "energy": e_mp, "status": c_mp, **st_mp}
     e_mp = res["mixed"]["energy"]
     if args.tte_fp64:
+        # the plain FP64 method: thick-restart Lanczos, FP64 H·v and FP64 vectors throughout
         x = v0.clone()
+        clk = Clocks(dev.index or 0)
+        clk.start()
         t0 = time.perf_counter()
         e64, st64, c64 = dmrg2d.lanczos_ground(ops, x, precision=dmrg2d.FP64, tol=args.tte_tol,
-                                               max_iter=args.tte_fp64_max_iter, krylov_dim=100,
-                                               check_every=5)
+                                               max_iter=args.tte_fp64_max_iter,
+                                               krylov_dim=args.tte_fp64_kdim,
+                                               thick_keep=args.tte_fp64_keep, check_every=5)
         torch.cuda.synchronize()
-        res["fp64"] = {"seconds": time.perf_counter() - t0, "energy": e64, "status": c64, **st64}
+        res["fp64"] = {"seconds": time.perf_counter() - t0, "energy": e64, "status": c64,
+                       "method": f"thick-restart Lanczos, krylov_dim {args.tte_fp64_kdim}, "
+                                 f"{args.tte_fp64_keep} Ritz vectors kept", **st64,
+                       "clocks": clk.stop()}
         res["energy_rel_diff"] = abs(e_mp - e64) / abs(e64)
         res["speedup"] = res["fp64"]["seconds"] / res["mixed"]["seconds"]
+        if args.tte_ref_tol > 0:
+            # the same FP64 solve continued from its own vector to a tighter residual: the
+            # reference energy both solvers are judged against (not part of either time)
+            t0 = time.perf_counter()
+            e_ref, st_ref, c_ref = dmrg2d.lanczos_ground(
+                ops, x, precision=dmrg2d.FP64, tol=args.tte_ref_tol,
+                max_iter=args.tte_fp64_max_iter, krylov_dim=args.tte_fp64_kdim,
+                thick_keep=args.tte_fp64_keep, check_every=5)
+            torch.cuda.synchronize()
+            res["fp64_reference"] = {"seconds": time.perf_counter() - t0, "energy": e_ref,
+                                     "status": c_ref, **st_ref}
+            res["mixed_vs_reference_rel"] = {k: abs(res[k]["energy"] - e_ref) / abs(e_ref)
+                                             for k in ("mixed", "mixed_fp64_refine", "fp64")
+                                             if k in res}
     return res
 
 
@@ -486,14 +585,24 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default=os.environ.get("DMRG2D_BENCH_PREC", "tf32"),
-                    choices=["tf32", "bf16", "fp32", "fp64"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS),
+                    help="synthetic superblock (default: the dense 3-leg Hubbard, m = 256)")
+    ap.add_argument("--precision", default=os.environ.get("DMRG2D_BENCH_PREC"),
+                    choices=["tf32", "bf16", "fp32", "fp64"],
+                    help="H·v precision (default: the workload's)")
     ap.add_argument("--tte", action="store_true", default=True,
                     help="time the mixed-precision ground-state solve (default on)")
     ap.add_argument("--no-tte", dest="tte", action="store_false")
     ap.add_argument("--tte-fp64", action="store_true", help="with --tte: also the plain FP64 solve")
     ap.add_argument("--tte-tol", type=float, default=1e-7)
-    ap.add_argument("--tte-fp64-max-iter", type=int, default=900)
+    ap.add_argument("--tte-fp64-max-iter", type=int, default=3000)
+    ap.add_argument("--tte-fp64-kdim", type=int, default=48,
+                    help="plain FP64 Lanczos: basis vectors before a thick restart")
+    ap.add_argument("--tte-fp64-keep", type=int, default=12,
+                    help="plain FP64 Lanczos: Ritz vectors kept at a thick restart")
+    ap.add_argument("--tte-ref-tol", type=float, default=1e-10,
+                    help="with --tte-fp64: continue the FP64 solve to this residual for the "
+                         "reference energy (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep", action="store_true", help="also run the DMRG sweep (4 x 12 ladder)")
     ap.add_argument("--sweep-m", default="128,512,512,1024,1024",
@@ -503,6 +612,8 @@ def main():
                     help="tensor-core tile configuration index instead of the autotuner")
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     args = ap.parse_args()
+    if args.precision is None:
+        args.precision = WORKLOADS[args.workload][1]
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

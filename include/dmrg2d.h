@@ -62,9 +62,14 @@ enum {
   DMRG2D_TF32 = 1,   /* v float, y float; tcgen05 kind::tf32, FP32 accumulate in TMEM */
   DMRG2D_BF16 = 2,   /* v bf16 (uint16 bits), y float; tcgen05 kind::f16, FP32 acc  */
   DMRG2D_FP32 = 3,   /* v float, y float; FP32 FMA on CUDA cores                      */
-  DMRG2D_FP64X = 4   /* v, y double; float-pair arithmetic (~48-bit significands) on
+  DMRG2D_FP64X = 4,  /* v, y double; float-pair arithmetic (~48-bit significands) on
                         the FP32 CUDA cores: FP64 emulated for the mixed solver's
                         residuals; dense superblocks only                             */
+  DMRG2D_BF16X3 = 5  /* split BF16: v = [v_hi | v_lo], 2 n_vec bf16 values with
+                        v_hi = bf16(x), v_lo = bf16(x - v_hi) (dmrg2d_convert_input);
+                        y float; three BF16 tensor-core products into FP32,
+                        H_hi v_hi + H_hi v_lo + H_lo v_hi (the operators split the same
+                        way): relative error ~1e-5 instead of BF16's ~2e-3              */
 };
 
 typedef struct dmrg2d_model {
@@ -148,11 +153,20 @@ int dmrg2d_sector_dense_index(const dmrg2d_ops* ops, int64_t* out);
 /* y = H v (paper: H_l V + V H_r^T + H_c V_c).  v and y are caller-owned device
  * buffers of info.n_vec elements in the layout above; they must not overlap.
  * Element types by precision: FP64 double/double; FP32 and TF32 float/float;
- * BF16 bf16/float.  TF32 and BF16 need info.tc_ok (else EUNSUPPORTED).
+ * BF16 bf16/float; BF16X3 2 n_vec bf16 (hi part, then lo part)/float.  TF32, BF16 and
+ * BF16X3 need info.tc_ok (else EUNSUPPORTED); BF16X3 uses the tile configuration
+ * chosen for BF16 without the operator pool or the two-pass form (three launches).
  * Algorithmic flops: 2*n_blk_left*m1^2*(d*m4) + 2*n_blk_right*m4^2*(m1*d)
  * + 2*n_scalar*m1*m4.  Asynchronous on `stream`; allocates nothing; no host
  * synchronisation, so the call can be captured in a CUDA graph. */
 int dmrg2d_apply_H(const dmrg2d_ops* ops, const void* v, void* y, int precision, void* stream);
+
+/* The input format of apply_H at `precision` from an FP64 vector x (device, n doubles):
+ * FP32 rounds to float; TF32 rounds to the nearest TF32 value (stored as float); BF16
+ * rounds to bf16; BF16X3 writes 2n bf16, hi = bf16(x) then lo = bf16(x - hi); FP64 and
+ * FP64X copy.  out: device buffer of that format.  Asynchronous; allocates nothing.
+ * EINVAL for an unknown precision or a NULL pointer. */
+int dmrg2d_convert_input(const double* x, void* out, int precision, int64_t n, void* stream);
 
 /* Ground state of H by Lanczos (implied by the paper's "exact diagonalization"
  * of the superblock; the algorithm is not named there). */
@@ -258,7 +272,12 @@ int dmrg2d_lanczos_ground_noalloc(const dmrg2d_ops* ops, const dmrg2d_solver_opt
  * instead of the grouped kernel's epilogue; 20 and 21 are the dense kernel / CTA-pair
  * kernel in two passes over the output: H_l V with the moves inside a block column and
  * H_c in column-slab order, then V H_r^T with the moves inside a block row in row-slab
- * order, added to the stored Y (each pass finds the V tiles it reads in L2).
+ * order, added to the stored Y (each pass finds the V tiles it reads in L2); 22
+ * (sector-restricted superblocks) is the pair of segment kernels for sectors of tens of
+ * states: H_l V with the MMA's M = 128 along the columns of each V_q and N = one row
+ * segment (the grouped kernel's operands with their roles swapped), then V H_r^T with M
+ * along the rows and N = one column segment, N rounded up to 16, K steps past a block's K
+ * skipped, the scalar moves in their own kernel (y must be 16-byte aligned).
  * dmrg2d_autotune times a complete H·v (scalar moves included) with every
  * configuration that applies (one warm-up and three timed launches each, on scratch
  * buffers it allocates and frees), keeps the fastest for later apply_H and solver
@@ -390,13 +409,17 @@ void dmrg2d_free_ops(dmrg2d_ops* ops);
  * the whole ladder (on the warm-up's smaller superblocks the same filling per column,
  * rounded half up); blocks carry the creation operators of their boundary column, their
  * parity and (N_up, N_dn) labels; block 4 grows from its own density matrix during the
- * warm-up (a mirrored fermion block would have the reversed mode order); every step
- * records the site densities of its central columns (report->densities).
+ * warm-up (a mirrored fermion block would have the reversed mode order), both blocks from
+ * one ground state; every step records the site densities of its central columns
+ * (report->densities).  Labels of a growing block that the superblock's target leaves
+ * empty (its density matrix is zero there, as on the warm-up's smaller superblocks) keep
+ * their states with weight 0 while m allows, so that larger superblocks find them.
  * Density matrices and their eigenvectors are FP64 on the GPU (cuBLAS DSYRK, cuSOLVER
  * dsyevd); ties in the density-matrix spectrum keep the eigenvectors dsyevd returns last.
- * Ground states: `precision` FP64 runs the plain Lanczos; TF32/BF16 the mixed solver
- * with FP64 refinement where the tensor-core path supports the superblock's shapes
- * (plain FP64 otherwise).  Warm-up steps start from a seeded random vector; every
+ * Ground states: `precision` FP64 runs the plain Lanczos (thick restart keeping
+ * krylov_dim / 4 Ritz vectors, at most 16); TF32/BF16/BF16X3 the mixed solver with FP64
+ * refinement where the tensor-core path supports the superblock's shapes (plain FP64
+ * otherwise).  Warm-up steps start from a seeded random vector; every
  * finite-sweep step starts from the previous ground state carried into its basis (the
  * wavefunction transformation: the new block's U and the stored U of the block that
  * splits into a smaller block and a column).
@@ -452,7 +475,32 @@ typedef struct dmrg2d_sweep_report {
   double obs_seconds;  /*   observables                                              */
 } dmrg2d_sweep_report;
 
-int dmrg2d_sweep(const dmrg2d_model* model, const dmrg2d_sweep_opts* opts,
+/* A DMRG run in progress: the model, the lattice and its filling, every block built so far
+ * (block 1 and block 4 of each length: host operators, device truncation matrices), the
+ * ground state carried to the next step and the sweep count.  dmrg2d_state_create takes
+ * the model and, from opts, the fields that fix the run: n_columns, m_warmup, seed,
+ * use_sectors, n_up, n_dn (validated as for dmrg2d_sweep; EINVAL / EUNSUPPORTED); it does
+ * no device work.  dmrg2d_sweep then runs the warm-up on the first call and, on every
+ * call, opts->n_sweeps more finite sweeps (sweep indices in the report continue from the
+ * earlier calls; each sweep's first step starts from the ground state the previous call
+ * left), with that call's solver options (precision, tol, max_iter, krylov_dim); its
+ * lattice fields must equal the state's (else EINVAL).  Two calls of one sweep each do
+ * exactly what one call of two sweeps does.  After a failed call the state is unusable
+ * (later calls return EINVAL): free it.  A state is used by one host thread at a time. */
+typedef struct dmrg2d_state dmrg2d_state;
+typedef struct dmrg2d_state_info {
+  int n_columns;       /* L                                                              */
+  int warmed_up;       /* 1 once the warm-up has run                                     */
+  int sweeps_done;     /* finite sweeps completed over all calls                         */
+  double last_energy;  /* superblock ground energy of the last step                      */
+  int m_left, m_right; /* states of block 1 and block 4 at the middle (L/2 - 1 columns)   */
+  int failed;          /* 1 after a failed call                                          */
+} dmrg2d_state_info;
+int dmrg2d_state_create(const dmrg2d_model* model, const dmrg2d_sweep_opts* opts,
+                        dmrg2d_state** out);
+void dmrg2d_state_free(dmrg2d_state* state);
+int dmrg2d_state_get_info(const dmrg2d_state* state, dmrg2d_state_info* info);
+int dmrg2d_sweep(dmrg2d_state* state, const dmrg2d_sweep_opts* opts,
                  dmrg2d_sweep_report* report, void* stream);
 
 /* Site densities of the two central columns of a superblock state: the observables of

@@ -76,8 +76,15 @@ int gp_finalise(dmrg2d_ops* ops, GroupPlan* g, cudaStream_t s);
 void gp_release(GroupPlan* g);
 // Y(all V_q) = grouped H_l V + V H_r^T, plus the plan's scalar moves when fuse_moves;
 // cfg = tile layout 0 .. gp_num_configs() - 1
+// lo_ops: the pools' low BF16 parts (BF16X3, precision BF16); accum: add to the stored Y
 int gp_launch(const dmrg2d_ops* ops, const GroupPlan* g, const void* v, float* y, int precision,
-              int cfg, cudaStream_t s, bool fuse_moves = true);
+              int cfg, cudaStream_t s, bool fuse_moves = true, bool lo_ops = false,
+              bool accum = false);
+// Segment kernels (sectors of tens of states): pass 1 = H_l V with M along the columns of
+// V_q, written to Y (added when accum); pass 2 = V H_r^T with M along the rows, added to Y.
+// No scalar moves.  y must be 16-byte aligned.
+int gp_launch_seg(const dmrg2d_ops* ops, const GroupPlan* g, const void* v, float* y,
+                  int precision, cudaStream_t s, bool lo_ops = false, bool accum = false);
 int gp_read_error(const GroupPlan* g, int* code);
 // pool tensor maps and per-block entries (CSR order of the build) for another kernel
 int gp_pool_views(const GroupPlan* g, int precision, int bn, const CUtensorMap** mL,

@@ -349,6 +349,7 @@ extern "C" int dmrg2d_apply_H(const dmrg2d_ops* ops, const void* v, void* y, int
       return launch_hv_simt_ff64(ops, (const double*)v, (double*)y, s);
     case DMRG2D_TF32:
     case DMRG2D_BF16:
+    case DMRG2D_BF16X3:
       if (!ops->tc_ok)
         return set_error(DMRG2D_EUNSUPPORTED, "tensor-core path does not support m1=%d m4=%d",
                          ops->m1, ops->m4);

@@ -576,6 +576,10 @@ struct TcState {
   int pairs = 0;          // CTA pairs resident at once (persistent grid of the pair kernel)
   CUtensorMap mHR2[2];    // H_r blocks in 128-row boxes (half a piece's columns)
   CUtensorMap mHL[2], mHR[2];  // [0] TF32, [1] BF16
+  // BF16X3: the low BF16 parts of the operator blocks, x - bf16(x) rounded to BF16
+  __nv_bfloat16* HLlo = nullptr;
+  __nv_bfloat16* HRlo = nullptr;
+  CUtensorMap mHLlo, mHRlo, mHR2lo;
   int sms = 0;
   int BN = 0;
 };
@@ -609,6 +613,15 @@ int make_map(CUtensorMap* m, const void* base, bool bf16, uint64_t inner, uint64
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return set_error(DMRG2D_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return DMRG2D_OK;
+}
+
+// lo = the BF16 rounding of x - bf16(x): with hi = bf16(x), hi + lo carries ~16 bits of x
+__global__ void k_bf16_lo(const double* __restrict__ x, __nv_bfloat16* __restrict__ o, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double hi = (double)__bfloat162float(__float2bfloat16_rn((float)x[i]));
+    o[i] = __float2bfloat16_rn((float)(x[i] - hi));
+  }
 }
 
 __global__ void k_round_tf32(const double* __restrict__ x, float* __restrict__ o, int64_t n) {
@@ -712,10 +725,16 @@ int tc_prepare(dmrg2d_ops* ops, cudaStream_t s, const std::vector<double>& HL,
   if (dense_ok) {
     alloc((void**)&T->HLt, sizeof(float) * nL * m1 * m1);
     alloc((void**)&T->HRt, sizeof(float) * nR * m4 * m4);
+    alloc((void**)&T->HLlo, sizeof(__nv_bfloat16) * nL * m1 * m1);
+    alloc((void**)&T->HRlo, sizeof(__nv_bfloat16) * nR * m4 * m4);
     if (st == DMRG2D_OK) {
       k_round_tf32<<<1024, 256, 0, s>>>(ops->dev.HL64, T->HLt, nL * m1 * m1);
       k_round_tf32<<<1024, 256, 0, s>>>(ops->dev.HR64, T->HRt, nR * m4 * m4);
+      k_bf16_lo<<<1024, 256, 0, s>>>(ops->dev.HL64, T->HLlo, nL * m1 * m1);
+      k_bf16_lo<<<1024, 256, 0, s>>>(ops->dev.HR64, T->HRlo, nR * m4 * m4);
     }
+    if (st == DMRG2D_OK) st = make_map(&T->mHLlo, T->HLlo, true, m1, nL * m1, 64, BM);
+    if (st == DMRG2D_OK) st = make_map(&T->mHRlo, T->HRlo, true, m4, nR * m4, 64, T->BN);
     for (int b = 0; b < 2 && st == DMRG2D_OK; ++b) {
       const bool bf = b == 1;
       const uint32_t BK = bf ? 64 : 32;
@@ -730,6 +749,8 @@ int tc_prepare(dmrg2d_ops* ops, cudaStream_t s, const std::vector<double>& HL,
       st = make_map(&T->mHR2[b], bf ? (const void*)ops->dev.HR16 : (const void*)T->HRt, bf, m4,
                     nR * m4, bf ? 64 : 32, P_HALF);
     }
+    if (st == DMRG2D_OK && T->pair_ok)
+      st = make_map(&T->mHR2lo, T->HRlo, true, m4, nR * m4, 64, P_HALF);
     auto upload_order = [&](int** dst, int pieces_mt) {
       const std::vector<int> ord = blocked_order(d, pieces_mt, m4 / T->BN, 8);
       alloc((void**)dst, sizeof(int) * ord.size());
@@ -870,6 +891,8 @@ void tc_release(dmrg2d_ops* ops) {
   if (!T) return;
   if (T->HLt) cudaFree(T->HLt);
   if (T->HRt) cudaFree(T->HRt);
+  if (T->HLlo) cudaFree(T->HLlo);
+  if (T->HRlo) cudaFree(T->HRlo);
   if (T->err) cudaFree(T->err);
   if (T->order) cudaFree(T->order);
   if (T->order2) cudaFree(T->order2);
@@ -893,8 +916,10 @@ void tc_release(dmrg2d_ops* ops) {
 // of the same column and H_c in column-slab order, then V H_r^T with the moves of the
 // same row in row-slab order, adding to the stored Y); autotuner index 0 / 7 / 8 / 9 /
 // 10 / 11 / 12 / 13 / 20 / 21 = variant 0 / 1 / 2 / 3 / 4 / 6 / 5 / 7 / 8 / 12
+// lo_ops: the operator blocks' low BF16 parts (BF16X3); accum: add to the stored Y
 static int launch_dense_kernel(const dmrg2d_ops* ops, const TcState* T, const void* v, float* y,
-                               bool bf, bool fuse_moves, int variant, cudaStream_t s) {
+                               bool bf, bool fuse_moves, int variant, cudaStream_t s,
+                               bool lo_ops = false, bool accum = false) {
   const bool pair = (variant & 4) != 0;
   const bool use_pool = (variant & 1) != 0;
   const bool two = (variant & 8) != 0;
@@ -912,7 +937,7 @@ static int launch_dense_kernel(const dmrg2d_ops* ops, const TcState* T, const vo
   p.order = (variant & 2) ? (pair ? T->order2 : T->order) : nullptr;
   p.ph0 = 0;
   p.ph1 = 2;
-  p.accum_y = 0;
+  p.accum_y = accum ? 1 : 0;
   p.BK = (int)BK;
   p.kblk1 = m1 / (int)BK;
   p.kblk2 = m4 / (int)BK;
@@ -929,8 +954,9 @@ static int launch_dense_kernel(const dmrg2d_ops* ops, const TcState* T, const vo
     p.idesc1[n] = make_idesc(fmt, 0, M, T->BN, n, 0);
     p.idesc2[n] = make_idesc(fmt, 1, M, T->BN, 0, n);
   }
-  const CUtensorMap* mA = &T->mHL[b];
-  const CUtensorMap* mB = pair ? &T->mHR2[b] : &T->mHR[b];
+  const CUtensorMap* mA = lo_ops ? &T->mHLlo : &T->mHL[b];
+  const CUtensorMap* mB =
+      lo_ops ? (pair ? &T->mHR2lo : &T->mHRlo) : (pair ? &T->mHR2[b] : &T->mHR[b]);
   p.pooled = 0;
   p.k1 = nullptr;
   p.k2 = nullptr;
@@ -1018,6 +1044,24 @@ int launch_hv_tc(const dmrg2d_ops* ops, const void* v, float* y, int precision, 
   if (ops->sec) return sec_apply(ops, v, y, precision, s);
   if (!ops->tc || !ops->tc_ok)
     return set_error(DMRG2D_EUNSUPPORTED, "tensor-core path not prepared");
+  if (precision == DMRG2D_BF16X3) {
+    // v = [v_hi | v_lo] (BF16); Y = H_hi v_hi + H_hi v_lo + H_lo v_hi in three BF16
+    // launches of the kernel chosen for BF16 (per-position operator blocks, one pass),
+    // the scalar moves (exact coefficients) applied to v_hi and v_lo
+    const TcState* T = (const TcState*)ops->tc;
+    const void* vlo = (const __nv_bfloat16*)v + ops->n_vec;
+    const int cfg = ops->tc_cfg[DMRG2D_BF16];
+    if (cfg < 0) {
+      const int var = (-1 - cfg) & ~9;  // no operator pool, no two-pass form
+      D2_TRY(launch_dense_kernel(ops, T, v, y, true, true, var, s, false, false));
+      D2_TRY(launch_dense_kernel(ops, T, vlo, y, true, true, var, s, false, true));
+      return launch_dense_kernel(ops, T, v, y, true, false, var, s, true, true);
+    }
+    if (!T->plan) return set_error(DMRG2D_EUNSUPPORTED, "grouped kernel unsupported here");
+    D2_TRY(gp_launch(ops, T->plan, v, y, DMRG2D_BF16, cfg, s, true, false, false));
+    D2_TRY(gp_launch(ops, T->plan, vlo, y, DMRG2D_BF16, cfg, s, true, false, true));
+    return gp_launch(ops, T->plan, v, y, DMRG2D_BF16, cfg, s, false, true, true);
+  }
   const bool bf = precision == DMRG2D_BF16;
   if (ops->tc_cfg[precision] < 0) {  // dense kernel: the moves run in its epilogue
     return launch_dense_kernel(ops, (const TcState*)ops->tc, v, y, bf, true,
@@ -1053,12 +1097,14 @@ namespace dmrg2d {
 // blocked piece order (per-position blocks / pool)
 // 14 + c = grouped configuration c with the scalar moves in a separate kernel (sectors)
 // 20 / 21 = two-pass dense kernel (128-row pieces / CTA pairs)
-constexpr int N_CANDIDATES = 22;
+// 22 = segment kernels (sectors: M along the long dimension of each V_q, moves separate)
+constexpr int N_CANDIDATES = 23;
 static int idx_to_cfg(int idx) {
   static const int dense_variant[14] = {0, -1, -1, -1, -1, -1, -1, 1, 2, 3, 4, 6, 5, 7};
   if (idx >= 1 && idx <= 6) return idx - 1;
   if (idx == 20) return -1 - 8;
   if (idx == 21) return -1 - 12;
+  if (idx == 22) return 2 * gp_num_configs();
   if (idx >= 14) return gp_num_configs() + idx - 14;
   return -1 - dense_variant[idx];
 }
@@ -1066,6 +1112,7 @@ static int idx_to_cfg(int idx) {
 static bool tc_candidate_ok(const dmrg2d_ops* ops, int idx) {
   if (idx < 0 || idx >= N_CANDIDATES) return false;
   if (idx >= 14 && idx < 20) return ops->sec && ops->tc_ok;  // grouped, separate moves
+  if (idx == 22) return ops->sec && ops->tc_ok;               // segment kernels
   if (idx == 0 || idx >= 7) {                                // dense-kernel variants
     const TcState* T = (const TcState*)ops->tc;
     if (ops->sec || !T || !T->dense_ok) return false;
@@ -1104,6 +1151,7 @@ extern "C" const char* dmrg2d_tile_config_name(int index) {
   if (index == 13) return "CTA-pair kernel 256x256 (8x8-tile blocked raster), operator pool";
   if (index == 20) return "dense kernel 128x256, two passes (H_l V by column slabs, V H_r^T by row slabs)";
   if (index == 21) return "CTA-pair kernel 256x256, two passes (H_l V by column slabs, V H_r^T by row slabs)";
+  if (index == 22) return "segment kernels (M = 128 along V's long dimension, N = one sector), separate moves";
   static const char* sep[6] = {
       "grouped 128x128 column-slab, separate moves kernel",
       "grouped 128x128 row-slab, separate moves kernel",

@@ -565,6 +565,42 @@ int sec_apply(const dmrg2d_ops* ops, const void* v, void* y, int precision, cuda
                                                        S->d_R32, p);
     if (ev.second) D2_CUDA(cudaEventRecord(ev.second, s));
     if (nm) k_sec_moves<float, float><<<nm, 256, 0, s>>>((const float*)v, (float*)y, p, 0);
+  } else if (precision == DMRG2D_BF16X3 && S->gp_ok && ops->tc_cfg[DMRG2D_BF16] == 2 * gp_num_configs()) {
+    // segment kernels: three products, then the moves on v_hi and v_lo
+    const __nv_bfloat16* vhi = (const __nv_bfloat16*)v;
+    const __nv_bfloat16* vlo = vhi + ops->n_vec;
+    D2_TRY(gp_launch_seg(ops, &S->plan, vhi, (float*)y, DMRG2D_BF16, s, false, false));
+    D2_TRY(gp_launch_seg(ops, &S->plan, vlo, (float*)y, DMRG2D_BF16, s, false, true));
+    D2_TRY(gp_launch_seg(ops, &S->plan, vhi, (float*)y, DMRG2D_BF16, s, true, true));
+    if (nm) {
+      k_sec_moves<__nv_bfloat16, float><<<nm, 256, 0, s>>>(vhi, (float*)y, p, 0);
+      k_sec_moves<__nv_bfloat16, float><<<nm, 256, 0, s>>>(vlo, (float*)y, p, 0);
+    }
+  } else if ((precision == DMRG2D_TF32 || precision == DMRG2D_BF16) && S->gp_ok &&
+             ops->tc_cfg[precision] == 2 * gp_num_configs()) {
+    // segment kernels (M along the long dimension of each V_q), then the scalar moves
+    D2_TRY(gp_launch_seg(ops, &S->plan, v, (float*)y, precision, s));
+    if (nm) {
+      if (precision == DMRG2D_BF16)
+        k_sec_moves<__nv_bfloat16, float><<<nm, 256, 0, s>>>((const __nv_bfloat16*)v, (float*)y,
+                                                            p, 0);
+      else
+        k_sec_moves<float, float><<<nm, 256, 0, s>>>((const float*)v, (float*)y, p, 0);
+    }
+  } else if (precision == DMRG2D_BF16X3 && S->gp_ok) {
+    // v = [v_hi | v_lo]: H_hi v_hi + H_hi v_lo + H_lo v_hi with the layout chosen for BF16,
+    // the scalar moves applied to v_hi and v_lo (in the epilogues, or their own kernel)
+    const int G = gp_num_configs(), cfg = ops->tc_cfg[DMRG2D_BF16];
+    const bool fused = cfg < G;
+    const __nv_bfloat16* vhi = (const __nv_bfloat16*)v;
+    const __nv_bfloat16* vlo = vhi + ops->n_vec;
+    D2_TRY(gp_launch(ops, &S->plan, vhi, (float*)y, DMRG2D_BF16, cfg % G, s, fused, false, false));
+    D2_TRY(gp_launch(ops, &S->plan, vlo, (float*)y, DMRG2D_BF16, cfg % G, s, fused, false, true));
+    D2_TRY(gp_launch(ops, &S->plan, vhi, (float*)y, DMRG2D_BF16, cfg % G, s, false, true, true));
+    if (!fused && nm) {
+      k_sec_moves<__nv_bfloat16, float><<<nm, 256, 0, s>>>(vhi, (float*)y, p, 0);
+      k_sec_moves<__nv_bfloat16, float><<<nm, 256, 0, s>>>(vlo, (float*)y, p, 0);
+    }
   } else if ((precision == DMRG2D_TF32 || precision == DMRG2D_BF16) && S->gp_ok) {
     // tc_cfg < G: one launch, the grouped kernel's epilogue adds the scalar moves;
     // G <= tc_cfg < 2G: the moves run in their own kernel after it (G tile layouts)

@@ -144,6 +144,16 @@ __global__ void k_f64_to_bf16(const double* __restrict__ x, __nv_bfloat16* __res
     o[e] = __float2bfloat16_rn((float)x[e]);
 }
 
+// the BF16X3 input: hi = bf16(x) at e, lo = bf16(x - hi) at n + e
+__global__ void k_f64_to_bf16x3(const double* __restrict__ x, __nv_bfloat16* __restrict__ o,
+                                int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * VT + threadIdx.x; e < n; e += (int64_t)gridDim.x * VT) {
+    const __nv_bfloat16 h = __float2bfloat16_rn((float)x[e]);
+    o[e] = h;
+    o[n + e] = __float2bfloat16_rn((float)(x[e] - (double)__bfloat162float(h)));
+  }
+}
+
 __global__ void k_f64_to_tf32(const double* __restrict__ x, float* __restrict__ o, int64_t n) {
   for (int64_t e = (int64_t)blockIdx.x * VT + threadIdx.x; e < n; e += (int64_t)gridDim.x * VT) {
     uint32_t u;
@@ -192,9 +202,14 @@ __device__ __forceinline__ float to_tf32(float f) {
   return __uint_as_float(u);
 }
 
-// lo[e] = f in the H~ input format (BF16, TF32 rounded to nearest, or FP32)
-__device__ __forceinline__ void put_lo(void* lo, int precision, int64_t e, float f) {
-  if (precision == DMRG2D_BF16)
+// lo[e] = f in the H~ input format (BF16, TF32 rounded to nearest, FP32, or the BF16X3
+// pair: hi at e, lo at n + e)
+__device__ __forceinline__ void put_lo(void* lo, int precision, int64_t e, float f, int64_t n) {
+  if (precision == DMRG2D_BF16X3) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(f);
+    ((__nv_bfloat16*)lo)[e] = h;
+    ((__nv_bfloat16*)lo)[n + e] = __float2bfloat16_rn(f - __bfloat162float(h));
+  } else if (precision == DMRG2D_BF16)
     ((__nv_bfloat16*)lo)[e] = __float2bfloat16_rn(f);
   else if (precision == DMRG2D_TF32)
     ((float*)lo)[e] = to_tf32(f);
@@ -275,7 +290,7 @@ __global__ void k_scale_to32(float* __restrict__ q, const TI* __restrict__ in,
   for (int64_t e = (int64_t)blockIdx.x * VT + threadIdx.x; e < n; e += (int64_t)gridDim.x * VT) {
     const float v = (float)in[e] * f;
     q[e] = v;
-    put_lo(lo, precision, e, v);
+    put_lo(lo, precision, e, v, n);
   }
 }
 
@@ -302,7 +317,7 @@ __global__ void k_cg_start32(const double* __restrict__ r, const double* __restr
     p32[e] = re;
     x32[e] = (float)x[e];
     t32[e] = 0.f;
-    put_lo(lo, precision, e, re);
+    put_lo(lo, precision, e, re, n);
     acc_fma(s, re, re);
   }
   const double v = block_sum(acc_val(s));
@@ -392,7 +407,7 @@ __global__ void k_cg_direction(float* __restrict__ p, const float* __restrict__ 
   for (int64_t e = (int64_t)blockIdx.x * VT + threadIdx.x; e < n; e += (int64_t)gridDim.x * VT) {
     const float pe = fmaf(beta, p[e], r[e]);
     p[e] = pe;
-    put_lo(lo, precision, e, pe);
+    put_lo(lo, precision, e, pe, n);
   }
 }
 
@@ -1394,7 +1409,9 @@ int lanczos_lo(Ctx& C, int prec, double* x, int max_iter, int kdim, double tol, 
 }  // namespace
 
 int convert_f64_to(const double* x, void* out, int precision, int64_t n, cudaStream_t s) {
-  if (precision == DMRG2D_BF16)
+  if (precision == DMRG2D_BF16X3)
+    k_f64_to_bf16x3<<<vgrid(n), VT, 0, s>>>(x, (__nv_bfloat16*)out, n);
+  else if (precision == DMRG2D_BF16)
     k_f64_to_bf16<<<vgrid(n), VT, 0, s>>>(x, (__nv_bfloat16*)out, n);
   else if (precision == DMRG2D_TF32)
     k_f64_to_tf32<<<vgrid(n), VT, 0, s>>>(x, (float*)out, n);
@@ -1606,9 +1623,10 @@ extern "C" int dmrg2d_lanczos_ground(const dmrg2d_ops* ops, const dmrg2d_solver_
   if (o.thick_keep < 0 || o.thick_keep > 32)
     return set_error(DMRG2D_EINVAL, "thick_keep must be in [0, 32]");
   if (o.precision != DMRG2D_FP64 && o.precision != DMRG2D_FP32 && o.precision != DMRG2D_TF32 &&
-      o.precision != DMRG2D_BF16)
+      o.precision != DMRG2D_BF16 && o.precision != DMRG2D_BF16X3)
     return set_error(DMRG2D_EINVAL, "unknown precision %d", o.precision);
-  if ((o.precision == DMRG2D_TF32 || o.precision == DMRG2D_BF16) && !ops->tc_ok)
+  if ((o.precision == DMRG2D_TF32 || o.precision == DMRG2D_BF16 ||
+       o.precision == DMRG2D_BF16X3) && !ops->tc_ok)
     return set_error(DMRG2D_EUNSUPPORTED, "tensor-core path unsupported for these shapes");
   if (o.refine_precision != DMRG2D_FP64 && o.refine_precision != DMRG2D_FP64X)
     return set_error(DMRG2D_EINVAL, "refine_precision must be FP64 or FP64X");
@@ -1662,6 +1680,27 @@ extern "C" int dmrg2d_lanczos_ground(const dmrg2d_ops* ops, const dmrg2d_solver_
   *energy_out = energy;
   if (stats) *stats = local;
   return st;
+}
+
+extern "C" int dmrg2d_convert_input(const double* x, void* out, int precision, int64_t n,
+                                    void* stream) {
+  if (!x || !out) return set_error(DMRG2D_EINVAL, "NULL argument");
+  if (n < 0) return set_error(DMRG2D_EINVAL, "n < 0");
+  const cudaStream_t st = (cudaStream_t)stream;
+  if (n == 0) return DMRG2D_OK;
+  switch (precision) {
+    case DMRG2D_FP64:
+    case DMRG2D_FP64X:
+      D2_CUDA(cudaMemcpyAsync(out, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+      return DMRG2D_OK;
+    case DMRG2D_FP32:
+    case DMRG2D_TF32:
+    case DMRG2D_BF16:
+    case DMRG2D_BF16X3:
+      return convert_f64_to(x, out, precision, n, st);
+    default:
+      return set_error(DMRG2D_EINVAL, "unknown precision %d", precision);
+  }
 }
 
 extern "C" int dmrg2d_tridiag_lowest(const double* alpha, const double* beta, int k, double* s,
@@ -2010,7 +2049,11 @@ extern "C" int dmrg2d_davidson_ground(const dmrg2d_ops* ops, const dmrg2d_davids
   if (o.max_iter < 1) return set_error(DMRG2D_EINVAL, "max_iter < 1");
   if (o.precond < DMRG2D_PRECOND_NONE || o.precond > DMRG2D_PRECOND_MLP)
     return set_error(DMRG2D_EINVAL, "unknown preconditioner %d", o.precond);
-  if ((o.precision == DMRG2D_TF32 || o.precision == DMRG2D_BF16) && !ops->tc_ok)
+  if (o.precision != DMRG2D_FP64 && o.precision != DMRG2D_FP32 && o.precision != DMRG2D_TF32 &&
+      o.precision != DMRG2D_BF16 && o.precision != DMRG2D_BF16X3)
+    return set_error(DMRG2D_EINVAL, "unknown precision %d", o.precision);
+  if ((o.precision == DMRG2D_TF32 || o.precision == DMRG2D_BF16 ||
+       o.precision == DMRG2D_BF16X3) && !ops->tc_ok)
     return set_error(DMRG2D_EUNSUPPORTED, "tensor-core path unsupported for these shapes");
   const auto t0 = std::chrono::steady_clock::now();
   dmrg2d_solver_stats local{};

@@ -189,7 +189,8 @@ class Sweeper {
           cudaStream_t s)
       : M_(*M), o_(*o), rep_(rep), strm_(s), rng_(o->seed) {}
 
-  int run() {
+  // Column operators, their device copies and the library handles (once per run).
+  int init() {
     hub_ = M_.kind == DMRG2D_HUBBARD;
     if (hub_) {  // the spin operators stay empty: every per-leg spin loop below is skipped
       hubbard_column_ops(M_.n_legs, M_.t, M_.U, M_.rung_pbc != 0, &hc_);
@@ -257,51 +258,91 @@ class Sweeper {
         D2_TRY(dcdP_[j].upload(cp, strm_));
       }
     }
+    return DMRG2D_OK;
+  }
+
+  // Infinite-system warm-up: block 1 and block 4 grow together until the superblock spans
+  // the lattice.
+  int warmup() {
     const int L = o_.n_columns, half = (L - 2) / 2;
-    std::map<int, Block> left, right;
-    left[1] = column_block();
-    right[1] = column_block();
+    left_[1] = column_block();
+    right_[1] = column_block();
     for (int l = 1; l < half; ++l) {  // warm-up: block 1 and its mirror image grow together
       if (hub_) {  // electrons: block 4 grows from its own density matrix (a mirrored
                    // block would have the reversed mode order); one ground state serves both
         Block nl, nr;
-        D2_TRY(step(left[l], right[l], true, o_.m_warmup, l, -1, &nl, nullptr, &nr));
-        left[l + 1] = nl;
-        right[l + 1] = nr;
+        D2_TRY(step(left_[l], right_[l], true, o_.m_warmup, l, -1, &nl, nullptr, &nr));
+        left_[l + 1] = nl;
+        right_[l + 1] = nr;
         continue;
       }
       Block nb;
-      D2_TRY(step(left[l], right[l], true, o_.m_warmup, l, -1, &nb, nullptr));
-      left[l + 1] = nb;
-      right[l + 1] = nb;
+      D2_TRY(step(left_[l], right_[l], true, o_.m_warmup, l, -1, &nb, nullptr));
+      left_[l + 1] = nb;
+      right_[l + 1] = nb;
     }
-    std::shared_ptr<DBuf> guess;  // start vector of the next step (null: seeded random)
+    guess_.reset();  // start vector of the next step (null: seeded random)
     if (half == 1) {
-      D2_TRY(step(left[1], right[1], true, o_.m_warmup, 1, -1, nullptr, nullptr));
-      guess = last_x_;  // the sweep's steps use the same superblock
+      D2_TRY(step(left_[1], right_[1], true, o_.m_warmup, 1, -1, nullptr, nullptr));
+      guess_ = last_x_;  // the sweep's steps use the same superblock
     }
-    for (int sw = 0; sw < o_.n_sweeps; ++sw) {
-      const int m = o_.m_sweep[sw];
+    warm_done_ = true;
+    return DMRG2D_OK;
+  }
+
+  // n finite sweeps (to the right end, to the left end, back to the middle), sweep s
+  // keeping m_sweep[s] states; sweep indices continue those of earlier calls.
+  int sweeps(int n, const int* m_sweep) {
+    const int L = o_.n_columns, half = (L - 2) / 2;
+    for (int s = 0; s < n; ++s) {
+      const int m = m_sweep[s], sw = sweeps_done_;
+      std::shared_ptr<DBuf>& guess = guess_;
       for (int l = half; l < L - 3; ++l) {  // to the right end
-        D2_TRY(step(left[l], right[L - 2 - l], true, m, l, sw, &left[l + 1], guess.get()));
+        D2_TRY(step(left_[l], right_[L - 2 - l], true, m, l, sw, &left_[l + 1], guess.get()));
         guess.reset();
-        D2_TRY(move_right(left[l + 1], right[L - 2 - l], &guess));
+        D2_TRY(move_right(left_[l + 1], right_[L - 2 - l], &guess));
       }
       for (int r = 1; r < L - 3; ++r) {  // to the left end
         const int l = L - 2 - r;
-        D2_TRY(step(left[l], right[r], false, m, l, sw, &right[r + 1], guess.get()));
+        D2_TRY(step(left_[l], right_[r], false, m, l, sw, &right_[r + 1], guess.get()));
         guess.reset();
-        D2_TRY(move_left(right[r + 1], left[l], &guess));
+        D2_TRY(move_left(right_[r + 1], left_[l], &guess));
       }
       for (int l = 1; l < half; ++l) {  // back to the middle
-        D2_TRY(step(left[l], right[L - 2 - l], true, m, l, sw, &left[l + 1], guess.get()));
+        D2_TRY(step(left_[l], right_[L - 2 - l], true, m, l, sw, &left_[l + 1], guess.get()));
         guess.reset();
-        D2_TRY(move_right(left[l + 1], right[L - 2 - l], &guess));
+        D2_TRY(move_right(left_[l + 1], right_[L - 2 - l], &guess));
       }
-      D2_TRY(step(left[half], right[half], true, m, half, sw, nullptr, guess.get()));
+      D2_TRY(step(left_[half], right_[half], true, m, half, sw, nullptr, guess.get()));
       guess = last_x_;  // the next sweep starts on this superblock
+      ++sweeps_done_;
     }
     return DMRG2D_OK;
+  }
+
+  // One call of dmrg2d_sweep on this run: its solver options, report and stream.
+  int begin_call(const dmrg2d_sweep_opts* o, dmrg2d_sweep_report* rep, cudaStream_t s) {
+    o_.precision = o->precision;
+    o_.tol = o->tol;
+    o_.max_iter = o->max_iter;
+    o_.krylov_dim = o->krylov_dim;
+    rep_ = rep;
+    strm_ = s;
+    solve_seconds = build_seconds = dm_seconds = renorm_seconds = obs_seconds = 0.0;
+    if (libs_.bl) D2_BLAS(cublasSetStream(libs_.bl, strm_));
+    if (libs_.sv) D2_SOLV(cusolverDnSetStream(libs_.sv, strm_));
+    return DMRG2D_OK;
+  }
+
+  bool warm_done() const { return warm_done_; }
+  int sweeps_done() const { return sweeps_done_; }
+  double last_energy() const { return last_energy_; }
+  const dmrg2d_model& model() const { return M_; }
+  const dmrg2d_sweep_opts& opts() const { return o_; }
+  int block_states(bool left, int cols) const {
+    const auto& mp = left ? left_ : right_;
+    auto it = mp.find(cols);
+    return it == mp.end() ? 0 : it->second.m;
   }
 
   double solve_seconds = 0.0, build_seconds = 0.0, dm_seconds = 0.0, renorm_seconds = 0.0,
@@ -751,6 +792,7 @@ class Sweeper {
     } else {
       so.precision = DMRG2D_FP64;
       so.max_iter = o_.max_iter;
+      so.thick_keep = std::min(16, o_.krylov_dim / 4);
     }
     double energy = 0.0;
     dmrg2d_solver_stats stats{};
@@ -1025,6 +1067,7 @@ class Sweeper {
 
   void record(double e, double trunc, int l, int sweep, int iters, const std::vector<double>& leg,
               const std::vector<double>& rung, double s2, const std::vector<double>& dens) {
+    last_energy_ = e;
     const int i = rep_->n_steps++;
     if (i < rep_->cap) {
       if (rep_->densities && !dens.empty())
@@ -1095,6 +1138,11 @@ class Sweeper {
   dmrg2d_model M_;
   dmrg2d_sweep_opts o_;
   dmrg2d_sweep_report* rep_;
+  std::map<int, Block> left_, right_;  // blocks by lattice columns (block 1 / block 4)
+  std::shared_ptr<DBuf> guess_;        // start vector of the next step (null: seeded random)
+  bool warm_done_ = false;
+  int sweeps_done_ = 0;
+  double last_energy_ = 0.0;
   cudaStream_t strm_;
   Rng rng_;
   SpinColumnOps col_;
@@ -1112,10 +1160,16 @@ class Sweeper {
 
 using namespace dmrg2d;
 
-extern "C" int dmrg2d_sweep(const dmrg2d_model* model, const dmrg2d_sweep_opts* opts,
-                            dmrg2d_sweep_report* report, void* stream) {
-  if (!model || !opts || !report) return set_error(DMRG2D_EINVAL, "sweep: NULL argument");
-  clear_error();
+struct dmrg2d_state {
+  dmrg2d::Sweeper* sw = nullptr;
+  bool ready = false;   // column operators and handles set up (first sweep call)
+  bool failed = false;  // an earlier call failed part-way: the blocks may be inconsistent
+};
+
+namespace {
+
+// The lattice, model and filling fields (fixed for a state).
+int check_lattice(const dmrg2d_model* model, const dmrg2d_sweep_opts* opts) {
   if (model->kind != DMRG2D_HEISENBERG && model->kind != DMRG2D_HUBBARD)
     return set_error(DMRG2D_EUNSUPPORTED, "sweep: Heisenberg or Hubbard ladders only");
   if (model->kind == DMRG2D_HUBBARD) {
@@ -1131,19 +1185,89 @@ extern "C" int dmrg2d_sweep(const dmrg2d_model* model, const dmrg2d_sweep_opts* 
                      model->kind == DMRG2D_HUBBARD ? 4 : 8);
   if (opts->n_columns < 4 || opts->n_columns % 2)
     return set_error(DMRG2D_EINVAL, "sweep: n_columns must be even and >= 4");
-  if (opts->m_warmup < 1 || opts->n_sweeps < 0 || (opts->n_sweeps > 0 && !opts->m_sweep))
-    return set_error(DMRG2D_EINVAL, "sweep: bad m_warmup / n_sweeps / m_sweep");
+  if (opts->m_warmup < 1) return set_error(DMRG2D_EINVAL, "sweep: m_warmup < 1");
+  return DMRG2D_OK;
+}
+
+// The per-call fields: sweeps and solver options.
+int check_call(const dmrg2d_sweep_opts* opts) {
+  if (opts->n_sweeps < 0 || (opts->n_sweeps > 0 && !opts->m_sweep))
+    return set_error(DMRG2D_EINVAL, "sweep: bad n_sweeps / m_sweep");
   for (int i = 0; i < opts->n_sweeps; ++i)
     if (opts->m_sweep[i] < 1) return set_error(DMRG2D_EINVAL, "sweep: m_sweep[%d] < 1", i);
   if (opts->max_iter < 1 || opts->krylov_dim < 2 || !(opts->tol > 0.0))
     return set_error(DMRG2D_EINVAL, "sweep: bad solver options");
+  return DMRG2D_OK;
+}
+
+}  // namespace
+
+extern "C" int dmrg2d_state_create(const dmrg2d_model* model, const dmrg2d_sweep_opts* opts,
+                                   dmrg2d_state** out) {
+  if (!model || !opts || !out) return set_error(DMRG2D_EINVAL, "state_create: NULL argument");
+  *out = nullptr;
+  clear_error();
+  D2_TRY(check_lattice(model, opts));
+  dmrg2d_sweep_opts o = *opts;
+  o.n_sweeps = 0;  // sweeps come with each dmrg2d_sweep call
+  o.m_sweep = nullptr;
+  dmrg2d_state* st = new (std::nothrow) dmrg2d_state();
+  if (!st) return set_error(DMRG2D_ENOMEM, "state_create: out of host memory");
+  st->sw = new (std::nothrow) Sweeper(model, &o, nullptr, nullptr);
+  if (!st->sw) {
+    delete st;
+    return set_error(DMRG2D_ENOMEM, "state_create: out of host memory");
+  }
+  *out = st;
+  return DMRG2D_OK;
+}
+
+extern "C" void dmrg2d_state_free(dmrg2d_state* st) {
+  if (!st) return;
+  delete st->sw;
+  delete st;
+}
+
+extern "C" int dmrg2d_state_get_info(const dmrg2d_state* st, dmrg2d_state_info* info) {
+  if (!st || !info) return set_error(DMRG2D_EINVAL, "state_get_info: NULL argument");
+  const Sweeper& sw = *st->sw;
+  const int L = sw.opts().n_columns, half = (L - 2) / 2;
+  info->n_columns = L;
+  info->warmed_up = sw.warm_done() ? 1 : 0;
+  info->sweeps_done = sw.sweeps_done();
+  info->last_energy = sw.last_energy();
+  info->m_left = sw.block_states(true, half);
+  info->m_right = sw.block_states(false, half);
+  info->failed = st->failed ? 1 : 0;
+  return DMRG2D_OK;
+}
+
+extern "C" int dmrg2d_sweep(dmrg2d_state* state, const dmrg2d_sweep_opts* opts,
+                            dmrg2d_sweep_report* report, void* stream) {
+  if (!state || !opts || !report) return set_error(DMRG2D_EINVAL, "sweep: NULL argument");
+  clear_error();
+  Sweeper& sw = *state->sw;
+  const dmrg2d_sweep_opts& so = sw.opts();
+  if (state->failed)
+    return set_error(DMRG2D_EINVAL, "sweep: an earlier call on this state failed; free it");
+  if (opts->n_columns != so.n_columns || opts->use_sectors != so.use_sectors ||
+      opts->n_up != so.n_up || opts->n_dn != so.n_dn)
+    return set_error(DMRG2D_EINVAL,
+                     "sweep: n_columns, use_sectors, n_up, n_dn differ from the state's");
+  D2_TRY(check_call(opts));
   if (report->cap < 0) return set_error(DMRG2D_EINVAL, "sweep: report cap < 0");
   report->n_steps = 0;
   report->seconds = report->solve_seconds = report->build_seconds = 0.0;
   report->dm_seconds = report->renorm_seconds = report->obs_seconds = 0.0;
   const auto t0 = std::chrono::steady_clock::now();
-  Sweeper sw(model, opts, report, (cudaStream_t)stream);
-  const int st = sw.run();
+  int st = sw.begin_call(opts, report, (cudaStream_t)stream);
+  if (st == DMRG2D_OK && !state->ready) {
+    st = sw.init();
+    state->ready = st == DMRG2D_OK;
+  }
+  if (st == DMRG2D_OK && !sw.warm_done()) st = sw.warmup();
+  if (st == DMRG2D_OK) st = sw.sweeps(opts->n_sweeps, opts->m_sweep);
+  if (st != DMRG2D_OK) state->failed = true;
   report->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   report->solve_seconds = sw.solve_seconds;
   report->build_seconds = sw.build_seconds;

@@ -153,6 +153,22 @@ __device__ __forceinline__ void umma_t(uint32_t dt, uint64_t a, uint64_t b, uint
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
         "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
+// the same, issued only when `go` is nonzero (a guard predicate inside the instruction
+// block: no branch in the issuing thread)
+template <int BF16>
+__device__ __forceinline__ void umma_if_t(uint32_t dt, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t acc, uint32_t go) {
+  if constexpr (BF16)
+    asm volatile(
+        "{\n\t.reg .pred p, g;\n\tsetp.ne.b32 p, %4, 0;\n\tsetp.ne.b32 g, %5, 0;\n\t"
+        "@g tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc), "r"(go));
+  else
+    asm volatile(
+        "{\n\t.reg .pred p, g;\n\tsetp.ne.b32 p, %4, 0;\n\tsetp.ne.b32 g, %5, 0;\n\t"
+        "@g tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc), "r"(go));
+}
 template <int BF16>
 __device__ __forceinline__ void umma_pair_t(uint32_t dt, uint64_t a, uint64_t b, uint32_t idesc,
                                             uint32_t acc) {

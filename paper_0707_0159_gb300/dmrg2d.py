@@ -13,8 +13,9 @@ import os
 import numpy as np
 
 HEISENBERG, HUBBARD = 0, 1
-FP64, TF32, BF16, FP32, FP64X = 0, 1, 2, 3, 4
-PRECISION = {"fp64": FP64, "tf32": TF32, "bf16": BF16, "fp32": FP32, "fp64x": FP64X}
+FP64, TF32, BF16, FP32, FP64X, BF16X3 = 0, 1, 2, 3, 4, 5
+PRECISION = {"fp64": FP64, "tf32": TF32, "bf16": BF16, "fp32": FP32, "fp64x": FP64X,
+             "bf16x3": BF16X3}
 STATUS = {0: "OK", -1: "EINVAL", -2: "ESHAPE", -3: "ENOMEM", -4: "ECUDA", -5: "ENOCONV",
           -6: "ETIMEOUT", -7: "ENAN", -8: "EUNSUPPORTED"}
 
@@ -58,6 +59,12 @@ class SweepReport(C.Structure):
                 ("obs_seconds", C.c_double)]
 
 
+class StateInfo(C.Structure):
+    _fields_ = [("n_columns", C.c_int), ("warmed_up", C.c_int), ("sweeps_done", C.c_int),
+                ("last_energy", C.c_double), ("m_left", C.c_int), ("m_right", C.c_int),
+                ("failed", C.c_int)]
+
+
 class OpsInfo(C.Structure):
     _fields_ = [("n_vec", C.c_int64), ("m1", C.c_int), ("m4", C.c_int), ("d", C.c_int),
                 ("n_legs", C.c_int), ("n_blk_left", C.c_int), ("n_blk_right", C.c_int),
@@ -94,6 +101,7 @@ SIGNATURES = {
     "dmrg2d_ops_get_info": (C.c_int, [C.c_void_p, C.POINTER(OpsInfo)]),
     "dmrg2d_sector_dense_index": (C.c_int, [C.c_void_p, C.c_void_p]),
     "dmrg2d_apply_H": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "dmrg2d_convert_input": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int64, C.c_void_p]),
     "dmrg2d_lanczos_ground": (C.c_int, [C.c_void_p, C.POINTER(SolverOpts), C.c_void_p,
                                         C.POINTER(C.c_double), C.POINTER(SolverStats), C.c_void_p]),
     "dmrg2d_lanczos_ground_noalloc": (C.c_int, [C.c_void_p, C.POINTER(SolverOpts), C.c_void_p,
@@ -103,8 +111,12 @@ SIGNATURES = {
     "dmrg2d_tridiag_lowest": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
                                         C.c_void_p]),
     "dmrg2d_wait_selftest": (C.c_int, [C.c_double, C.c_void_p]),
-    "dmrg2d_sweep": (C.c_int, [C.POINTER(Model), C.POINTER(SweepOpts), C.POINTER(SweepReport),
+    "dmrg2d_sweep": (C.c_int, [C.c_void_p, C.POINTER(SweepOpts), C.POINTER(SweepReport),
                                C.c_void_p]),
+    "dmrg2d_state_create": (C.c_int, [C.POINTER(Model), C.POINTER(SweepOpts),
+                                      C.POINTER(C.c_void_p)]),
+    "dmrg2d_state_free": (None, [C.c_void_p]),
+    "dmrg2d_state_get_info": (C.c_int, [C.c_void_p, C.POINTER(StateInfo)]),
     "dmrg2d_diagonal": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "dmrg2d_default_davidson_opts": (None, [C.POINTER(DavidsonOpts)]),
     "dmrg2d_davidson_ground": (C.c_int, [C.c_void_p, C.POINTER(DavidsonOpts), C.c_void_p,
@@ -251,20 +263,37 @@ def sector_dense_index(ops: Ops) -> np.ndarray:
 
 _DTYPES = {FP64: ("float64", "float64"), FP32: ("float32", "float32"),
            TF32: ("float32", "float32"), BF16: ("bfloat16", "float32"),
-           FP64X: ("float64", "float64")}
+           FP64X: ("float64", "float64"), BF16X3: ("bfloat16", "float32")}
+_IN_PARTS = {BF16X3: 2}   # BF16X3 input: hi part then lo part
 
 
 def apply_H(ops: Ops, v, y, precision=FP64, stream=None):
-    """y = H v on the device (torch CUDA tensors, contiguous, n_vec elements)."""
+    """y = H v on the device (torch CUDA tensors, contiguous, n_vec elements; the BF16X3
+    input holds 2 n_vec elements, see convert_input)."""
     precision = PRECISION.get(precision, precision)
     vin, vout = _DTYPES[precision]
     n = ops.info["n_vec"]
-    for t, dt, name in ((v, vin, "v"), (y, vout, "y")):
-        if not t.is_cuda or not t.is_contiguous() or t.numel() != n or str(t.dtype) != "torch." + dt:
-            raise ValueError(f"{name}: need a contiguous CUDA {dt} tensor of {n} elements, got "
+    for t, dt, name, cnt in ((v, vin, "v", n * _IN_PARTS.get(precision, 1)), (y, vout, "y", n)):
+        if not t.is_cuda or not t.is_contiguous() or t.numel() != cnt or str(t.dtype) != "torch." + dt:
+            raise ValueError(f"{name}: need a contiguous CUDA {dt} tensor of {cnt} elements, got "
                              f"{t.dtype} {tuple(t.shape)} on {t.device}")
     _check(lib().dmrg2d_apply_H(ops.ptr, C.c_void_p(v.data_ptr()), C.c_void_p(y.data_ptr()),
                                 int(precision), _stream(stream)))
+
+
+def convert_input(x, precision, stream=None):
+    """The apply_H input at `precision` from the CUDA float64 tensor x
+    (dmrg2d_convert_input); returns a new tensor (2 x.numel() bf16 values for BF16X3)."""
+    import torch
+    precision = PRECISION.get(precision, precision)
+    if not x.is_cuda or str(x.dtype) != "torch.float64" or not x.is_contiguous():
+        raise ValueError("x must be a contiguous CUDA float64 tensor")
+    # an unknown precision is passed on for the library to reject (EINVAL)
+    dt = getattr(torch, _DTYPES.get(precision, ("float64", "float64"))[0])
+    out = torch.empty(x.numel() * _IN_PARTS.get(precision, 1), dtype=dt, device=x.device)
+    _check(lib().dmrg2d_convert_input(C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()),
+                                      int(precision), int(x.numel()), _stream(stream)))
+    return out
 
 
 def wait_selftest(seconds: float = 0.05, stream=None) -> int:
@@ -288,7 +317,7 @@ def profile_stop(ops: Ops):
     return ms.value, n.value
 
 
-N_TILE_CONFIGS = 22
+N_TILE_CONFIGS = 23
 
 
 def autotune(ops: Ops, precision, stream=None):
@@ -510,40 +539,91 @@ def mlp_make_batch(ops: Ops, x_k, r_k, theta, x_final, D, idx, X, w, T, stream=N
         C.c_void_p(T.data_ptr()), _stream(stream)))
 
 
+class SweepState:
+    """A DMRG run that continues across calls (dmrg2d_state): the warm-up on the first
+    sweep() call, then the requested sweeps on every call, each starting where the last
+    one stopped.  model, n_columns, m_warmup, seed, sectors, n_up, n_dn are fixed here;
+    the solver options may change per call."""
+
+    def __init__(self, model: dict, n_columns: int, m_warmup: int, seed=1, sectors=False,
+                 n_up=0, n_dn=0):
+        self.model = model
+        self._fixed = dict(n_columns=int(n_columns), m_warmup=int(m_warmup), seed=int(seed),
+                           use_sectors=int(bool(sectors)), n_up=int(n_up), n_dn=int(n_dn))
+        opts = self._opts([], FP64, 1e-10, 300, 100)
+        mdl = _model(model)
+        p = C.c_void_p()
+        _check(lib().dmrg2d_state_create(C.byref(mdl), C.byref(opts[0]), C.byref(p)))
+        self._p = p
+
+    def _opts(self, m_sweeps, precision, tol, max_iter, krylov_dim):
+        ms = (C.c_int * max(1, len(m_sweeps)))(*[int(m) for m in m_sweeps])
+        f = self._fixed
+        o = SweepOpts(f["n_columns"], f["m_warmup"], len(m_sweeps), ms, int(precision),
+                      float(tol), int(max_iter), int(krylov_dim), f["seed"], f["use_sectors"],
+                      f["n_up"], f["n_dn"])
+        return o, ms
+
+    def sweep(self, m_sweeps, precision=FP64, tol=1e-10, max_iter=300, krylov_dim=100,
+              cap=4096, stream=None) -> dict:
+        """One finite sweep per entry of m_sweeps (after the warm-up on the first call);
+        the per-step report as dmrg2d.sweep returns it."""
+        precision = PRECISION.get(precision, precision)
+        opts, ms = self._opts(m_sweeps, precision, tol, max_iter, krylov_dim)
+        e, t = (C.c_double * cap)(), (C.c_double * cap)()
+        ll, sw, it = (C.c_int * cap)(), (C.c_int * cap)(), (C.c_int * cap)()
+        nl = int(self.model["n_legs"])
+        nr = max(nl - 1, 1)
+        leg, rung, s2 = (C.c_double * (cap * nl))(), (C.c_double * (cap * nr))(), (C.c_double * cap)()
+        nd = 8 * nl + 2
+        dens = (C.c_double * (cap * nd))()
+        rep = SweepReport(cap, 0, e, t, ll, sw, it, leg, rung, s2, dens, 0.0, 0.0, 0.0, 0.0, 0.0,
+                          0.0)
+        _check(lib().dmrg2d_sweep(self._p, C.byref(opts), C.byref(rep), _stream(stream)))
+        n = min(rep.n_steps, cap)
+        return {"energy": list(e[:n]), "trunc": list(t[:n]), "l": list(ll[:n]),
+                "sweep": list(sw[:n]), "iters": list(it[:n]),
+                "leg_bond": [list(leg[i * nl:(i + 1) * nl]) for i in range(n)],
+                "rung_bond": [list(rung[i * nr:(i + 1) * nr])[:nl - 1] for i in range(n)],
+                "s2": list(s2[:n]), "obs_seconds": rep.obs_seconds,
+                "n_steps": rep.n_steps, "seconds": rep.seconds,
+                "solve_seconds": rep.solve_seconds, "build_seconds": rep.build_seconds,
+                "dm_seconds": rep.dm_seconds, "renorm_seconds": rep.renorm_seconds,
+                **_sweep_densities(dens, n, nl)}
+
+    def info(self) -> dict:
+        inf = StateInfo()
+        _check(lib().dmrg2d_state_get_info(self._p, C.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in StateInfo._fields_}
+
+    def free(self):
+        if self._p:
+            lib().dmrg2d_state_free(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
 def sweep(model: dict, n_columns: int, m_warmup: int, m_sweeps, precision=FP64, tol=1e-10,
           max_iter=300, krylov_dim=100, seed=1, cap=4096, sectors=False, n_up=0, n_dn=0,
           stream=None) -> dict:
-    """dmrg2d_sweep: warm-up plus one finite sweep per entry of m_sweeps on an n-leg
-    Heisenberg ladder (or, with sectors=True and the filling n_up, n_dn, a Hubbard ladder)
-    of n_columns columns.  Returns the per-step energy, truncation error, block-1 length
-    and sweep index (-1 = warm-up), the observables and the timings; for Hubbard ladders
-    "n" (steps x 2 columns x n_legs x [up, down]), "h", "sd" (steps x 2 x n_legs) and "S"
-    (steps x 2) are the central columns' site densities."""
-    precision = PRECISION.get(precision, precision)
-    ms = (C.c_int * max(1, len(m_sweeps)))(*[int(m) for m in m_sweeps])
-    opts = SweepOpts(int(n_columns), int(m_warmup), len(m_sweeps), ms, int(precision), float(tol),
-                     int(max_iter), int(krylov_dim), int(seed), int(bool(sectors)), int(n_up),
-                     int(n_dn))
-    e, t = (C.c_double * cap)(), (C.c_double * cap)()
-    ll, sw, it = (C.c_int * cap)(), (C.c_int * cap)(), (C.c_int * cap)()
-    nl = int(model["n_legs"])
-    nr = max(nl - 1, 1)
-    leg, rung, s2 = (C.c_double * (cap * nl))(), (C.c_double * (cap * nr))(), (C.c_double * cap)()
-    nd = 8 * nl + 2
-    dens = (C.c_double * (cap * nd))()
-    rep = SweepReport(cap, 0, e, t, ll, sw, it, leg, rung, s2, dens, 0.0, 0.0, 0.0, 0.0, 0.0,
-                      0.0)
-    mdl = _model(model)
-    _check(lib().dmrg2d_sweep(C.byref(mdl), C.byref(opts), C.byref(rep), _stream(stream)))
-    n = min(rep.n_steps, cap)
-    return {"energy": list(e[:n]), "trunc": list(t[:n]), "l": list(ll[:n]), "sweep": list(sw[:n]),
-            "iters": list(it[:n]),
-            "leg_bond": [list(leg[i * nl:(i + 1) * nl]) for i in range(n)],
-            "rung_bond": [list(rung[i * nr:(i + 1) * nr])[:nl - 1] for i in range(n)],
-            "s2": list(s2[:n]), "obs_seconds": rep.obs_seconds,
-            "n_steps": rep.n_steps, "seconds": rep.seconds, "solve_seconds": rep.solve_seconds,
-            "build_seconds": rep.build_seconds, "dm_seconds": rep.dm_seconds,
-            "renorm_seconds": rep.renorm_seconds, **_sweep_densities(dens, n, nl)}
+    """dmrg2d_sweep on a fresh state: warm-up plus one finite sweep per entry of m_sweeps
+    on an n-leg Heisenberg ladder (or, with sectors=True and the filling n_up, n_dn, a
+    Hubbard ladder) of n_columns columns.  Returns the per-step energy, truncation error,
+    block-1 length and sweep index (-1 = warm-up), the observables and the timings; for
+    Hubbard ladders "n" (steps x 2 columns x n_legs x [up, down]), "h", "sd" (steps x 2 x
+    n_legs) and "S" (steps x 2) are the central columns' site densities."""
+    st = SweepState(model, n_columns, m_warmup, seed=seed, sectors=sectors, n_up=n_up,
+                    n_dn=n_dn)
+    try:
+        return st.sweep(m_sweeps, precision=precision, tol=tol, max_iter=max_iter,
+                        krylov_dim=krylov_dim, cap=cap, stream=stream)
+    finally:
+        st.free()
 
 
 def _sweep_densities(buf, n: int, nl: int) -> dict:

@@ -98,3 +98,22 @@ def test_site_densities_rejects_null_arguments(lib):
     assert "NULL" in lib.dmrg2d_last_error().decode()
     buf = (ctypes.c_double * 4)()
     assert lib.dmrg2d_site_densities(None, buf, buf, None) == -1
+
+
+def test_sweep_state_is_created_and_validated_on_host(lib):
+    """dmrg2d_state_create checks the lattice and filling before any device work."""
+    from paper_0707_0159_gb300 import dmrg2d, synth
+    st = dmrg2d.SweepState(synth.model("heisenberg", 2), 6, 16)
+    info = st.info()
+    assert info["n_columns"] == 6 and info["warmed_up"] == 0 and info["sweeps_done"] == 0
+    assert info["failed"] == 0
+    st.free()
+    with pytest.raises(dmrg2d.Dmrg2dError) as e:
+        dmrg2d.SweepState(synth.model("heisenberg", 2), 5, 16)        # odd lattice
+    assert e.value.code == -1
+    with pytest.raises(dmrg2d.Dmrg2dError) as e:                       # Hubbard needs sectors
+        dmrg2d.SweepState(synth.model("hubbard", 2), 6, 16, sectors=False)
+    assert e.value.code == -8
+    with pytest.raises(dmrg2d.Dmrg2dError) as e:
+        dmrg2d.SweepState(synth.model("hubbard", 2), 6, 16, sectors=True, n_up=13)
+    assert e.value.code == -1

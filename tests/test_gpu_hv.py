@@ -4,7 +4,9 @@ FP64 must match to a relative Frobenius error <= 1e-12 (the product is exact
 linear algebra; only summation order differs).  FP32 (CUDA cores) <= 1e-5.
 TF32/BF16 tensor-core products are compared with the bound derived from their
 unit roundoff: TF32 <= 1e-3; BF16 <= 6e-3 (its expected error ~2e-3 is above
-1e-3, see the BF16 test).
+1e-3, see the BF16 test); split BF16 (BF16X3: hi and lo parts, three products, the
+lo x lo product dropped) <= 1e-4 (per product at most ~3 u^2 = 4.6e-5 with
+u = 2^-8).
 """
 import numpy as np
 import pytest
@@ -25,6 +27,12 @@ def rel(a, b):
 
 def run(ops, v, prec):
     x = torch.from_numpy(v).to(DEV)
+    if prec == dmrg2d.BF16X3:
+        xs = dmrg2d.convert_input(x, prec)
+        y = torch.full((x.numel(),), float("nan"), dtype=torch.float32, device=DEV)
+        dmrg2d.apply_H(ops, xs, y, prec)
+        torch.cuda.synchronize()
+        return y.double().cpu().numpy(), x.cpu().numpy()
     if prec in (dmrg2d.FP32, dmrg2d.TF32):
         x = x.float()
     elif prec == dmrg2d.BF16:
@@ -164,7 +172,8 @@ TC_CASES = [
 
 
 @pytest.mark.parametrize("case", TC_CASES)
-@pytest.mark.parametrize("prec,tol", [(dmrg2d.TF32, 1e-3), (dmrg2d.BF16, 6e-3)])
+@pytest.mark.parametrize("prec,tol", [(dmrg2d.TF32, 1e-3), (dmrg2d.BF16, 6e-3),
+                                      (dmrg2d.BF16X3, 1e-4)])
 def test_tensor_core_small_shapes(case, prec, tol):
     mdl, left, right = make(*case)
     ops = dmrg2d.build_ops(mdl, left, right)
@@ -243,3 +252,68 @@ def test_ladder3_full_tensor_core_sampled(ladder3_full, prec, tol):
     y, _ = run(ops, v, prec)
     assert np.array_equal(y[idx], outs[best] if best in outs else y[idx])
     assert rel(y[idx], ref) <= tol
+
+
+def test_convert_input_formats():
+    """dmrg2d_convert_input writes the documented formats: TF32 = the nearest TF32 value
+    (10 fraction bits kept), BF16 = bf16(float(x)), BF16X3 = [hi | lo] with hi = bf16(x),
+    lo = bf16(x - hi)."""
+    rng = np.random.default_rng(3)
+    x64 = np.concatenate([rng.standard_normal(4093) * 10.0 ** rng.integers(-6, 6, 4093),
+                          [0.0, -0.0, 1.0]])
+    x = torch.from_numpy(x64).to(DEV)
+    bf = dmrg2d.convert_input(x, dmrg2d.BF16).cpu()
+    assert torch.equal(bf.view(torch.int16), torch.from_numpy(x64).float().bfloat16().view(torch.int16))
+    x3 = dmrg2d.convert_input(x, dmrg2d.BF16X3).cpu()
+    hi = torch.from_numpy(x64).float().bfloat16()
+    lo = (torch.from_numpy(x64) - hi.double()).float().bfloat16()
+    assert torch.equal(x3[:x64.size].view(torch.int16), hi.view(torch.int16))
+    assert torch.equal(x3[x64.size:].view(torch.int16), lo.view(torch.int16))
+    # hi + lo carries ~16 significant bits
+    approx = hi.double().numpy() + lo.double().numpy()
+    assert np.all(np.abs(approx - x64) <= 1.01 * 2.0 ** -16 * np.abs(x64) + 1e-300)
+    tf = dmrg2d.convert_input(x, dmrg2d.TF32).cpu().numpy()
+    assert np.all(tf.view(np.uint32) & 0x1FFF == 0)          # 13 low fraction bits clear
+    assert np.all(np.abs(tf - x64.astype(np.float32)) <= 2.0 ** -11 * np.abs(x64) * 1.0001)
+    with pytest.raises(dmrg2d.Dmrg2dError):
+        dmrg2d.convert_input(x, 9)
+
+
+# ---- every output piece of the full-size superblock -------------------------------------------
+
+@pytest.fixture(scope="module")
+def ladder3_pieces(ladder3_full):
+    """One random output and one corner in each of the 64 x 64 output tiles (i2, i3), each
+    256 x 256 (the CTA-pair kernel's piece): 8192 entries, the oracle's sum per entry."""
+    ops, sb, v, _ = ladder3_full
+    m1, d, m4 = sb.m1, sb.d, sb.m4
+    rng = np.random.default_rng(11)
+    i2, i3 = np.meshgrid(np.arange(d), np.arange(d), indexing="ij")
+    i2, i3 = i2.ravel(), i3.ravel()
+    corners = np.array([(0, 0), (m1 - 1, 0), (0, m4 - 1), (m1 - 1, m4 - 1)])
+    c = corners[np.arange(i2.size) % 4]
+    i1 = np.concatenate([rng.integers(0, m1, i2.size), c[:, 0]])
+    i4 = np.concatenate([rng.integers(0, m4, i2.size), c[:, 1]])
+    i2, i3 = np.concatenate([i2, i2]), np.concatenate([i3, i3])
+    idx = i1 + m1 * i2 + m1 * d * i4 + m1 * d * m4 * i3
+    return idx, sb.apply_at(v, idx)
+
+
+@pytest.mark.parametrize("prec,tol", [(dmrg2d.TF32, 1e-3), (dmrg2d.BF16, 6e-3),
+                                      (dmrg2d.BF16X3, 1e-4)])
+def test_ladder3_full_every_piece(ladder3_full, ladder3_pieces, prec, tol):
+    """The autotuner's choice at full size (what the benchmark times; BF16X3 runs the BF16
+    choice), checked in every output piece: the relative error over all samples, and each
+    sample within a few times the tolerance of the output's RMS, so that a piece left
+    unwritten, written twice or taken from the wrong tile fails."""
+    ops, sb, v, _ = ladder3_full
+    idx, ref = ladder3_pieces
+    if not ops.info["tc_ok"]:
+        pytest.skip("tensor-core path not available for these shapes")
+    best, _ = dmrg2d.autotune(ops, dmrg2d.BF16 if prec == dmrg2d.BF16X3 else prec)
+    y, _ = run(ops, v, prec)
+    got = y[idx]
+    assert np.all(np.isfinite(got))
+    assert rel(got, ref) <= tol, (best, rel(got, ref))
+    rms = np.sqrt(np.mean(ref ** 2))
+    assert np.max(np.abs(got - ref)) <= 30 * tol * rms, (best, np.max(np.abs(got - ref)) / rms)

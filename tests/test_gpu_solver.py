@@ -108,7 +108,8 @@ def test_fp64_lanczos_converges(ladder2_m128):
 
 
 @pytest.mark.parametrize("prec,rprec", [(dmrg2d.FP32, dmrg2d.FP64), (dmrg2d.TF32, dmrg2d.FP64),
-                                        (dmrg2d.BF16, dmrg2d.FP64), (dmrg2d.TF32, dmrg2d.FP64X)])
+                                        (dmrg2d.BF16, dmrg2d.FP64), (dmrg2d.TF32, dmrg2d.FP64X),
+                                        (dmrg2d.BF16X3, dmrg2d.FP64)])
 def test_mixed_precision_reaches_fp64_energy(ladder2_m128, prec, rprec):
     ops, v0, e64, st64, c64 = ladder2_m128
     assert ops.info["tc_ok"]

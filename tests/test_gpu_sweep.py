@@ -186,3 +186,37 @@ def test_truncated_hubbard_ladder_sweep_matches_oracle(n_up, n_dn, m):
             assert abs(out["trunc"][i] - ref["trunc"][k]) <= 1e-9, \
                 (i, out["trunc"][i], ref["trunc"][k])
         assert np.allclose(out["n"][i], np.asarray(ref["n"][k]), atol=1e-7), i
+
+
+@pytest.mark.parametrize("kind", ["heisenberg", "hubbard"])
+def test_sweep_state_continues_across_calls(kind):
+    """dmrg2d_state: one sweep per call on one state, twice, does what one call of two
+    sweeps does (same steps, energies, truncation errors); the second call starts from the
+    ground state the first one left and continues the sweep index; lattice fields that
+    differ from the state's are refused."""
+    if kind == "heisenberg":
+        mdl, kw = model(2), dict(sectors=True)
+    else:
+        mdl, kw = synth.model("hubbard", 2, t=1.0, U=8.0), dict(sectors=True, n_up=3, n_dn=2)
+    solve = dict(tol=1e-12, max_iter=600, krylov_dim=120)
+    once = dmrg2d.sweep(mdl, 6, 8, [8, 12], **kw, **solve)
+    st = dmrg2d.SweepState(mdl, 6, 8, **kw)
+    a = st.sweep([8], **solve)
+    assert st.info()["sweeps_done"] == 1 and st.info()["warmed_up"] == 1
+    b = st.sweep([12], **solve)
+    info = st.info()
+    assert info["sweeps_done"] == 2 and abs(info["last_energy"] - once["energy"][-1]) <= 1e-12
+    both = {k: a[k] + b[k] for k in ("energy", "trunc", "l", "sweep")}
+    assert both["l"] == once["l"] and both["sweep"] == once["sweep"]
+    assert max(s for s in b["sweep"]) == 1 and min(s for s in b["sweep"]) == 1
+    assert np.allclose(both["energy"], once["energy"], rtol=0, atol=1e-11)
+    assert np.allclose(both["trunc"], once["trunc"], rtol=0, atol=1e-11)
+    # b's first step starts from a's last ground state: few solver steps
+    assert b["iters"][0] <= once["iters"][len(a["energy"])] + 2
+    bad = dmrg2d.SweepState(mdl, 6, 8, **kw)
+    bad._fixed["n_columns"] = 8                 # a call whose lattice differs from the state
+    with pytest.raises(dmrg2d.Dmrg2dError) as e:
+        bad.sweep([8], **solve)
+    assert e.value.code == -1
+    st.free()
+    bad.free()
