@@ -87,6 +87,7 @@ struct GDev {
   __nv_bfloat16* pL16lo = nullptr;  // BF16X3: x - bf16(x) rounded to BF16
   __nv_bfloat16* pR16lo = nullptr;
   CUtensorMap mLlo, mRlo[2];
+  CUtensorMap mL32[2], mR32[2], mL32lo, mR32lo;  // the pools in 32-row boxes (segment kernels)
   int KPL = 0, KPR = 0, prL = 0, prR = 0, copies = 1;
   CUtensorMap mL[2], mR[2][2];  // [precision][piece width 128/256]
   int* err = nullptr;
@@ -385,7 +386,7 @@ struct SParams {
   uint32_t idesc[16][2];  // N = 16 (i + 1); [negate the operator block]
   uint32_t a2_lbo, a2_sbo, a2_kstep, a2_layout;  // pass 2: MN-major A (as the grouped kernel)
   int a2_boxes, a2_box_rows;
-  uint32_t tx_bytes;
+  uint32_t a_bytes, b_box_bytes;  // per stage: the A tile; one 32-row box of B
   int BK, KSTEP;  // K per stage; K per instruction
   int accum_y;    // pass 1: add the Y already stored (BF16X3)
 };
@@ -439,6 +440,10 @@ hv_tc_seg_kernel(const __grid_constant__ GMaps maps, const SParams p) {
       const SItem it = p.items[ti];
       const int e0 = PASS == 0 ? p.rows[it.seg].k1b : p.cols[it.seg].k2b;
       const int e1 = PASS == 0 ? p.rows[it.seg].k1e : p.cols[it.seg].k2e;
+      // the operator rows this piece needs, in 32-row boxes (N rounded up to 16 <= 32 nb)
+      const int sdim = PASS == 0 ? p.rows[it.seg].dim : p.cols[it.seg].dim;
+      const int nb = (min(NMAX, sdim - it.n0) + 31) / 32;
+      const uint32_t tx = p.a_bytes + (uint32_t)nb * p.b_box_bytes;
       for (int e = e0; e < e1; ++e) {
         int kdim, pool, voff;
         if (PASS == 0) {
@@ -460,18 +465,21 @@ hv_tc_seg_kernel(const __grid_constant__ GMaps maps, const SParams p) {
           }
           const uint32_t a_s = smem_u32(smem + stage * G_STAGE);
           const uint32_t b_s = a_s + G_STAGE_A;
-          mbar_expect_tx(full(stage), p.tx_bytes);
+          mbar_expect_tx(full(stage), tx);
           if (PASS == 0) {
-            // A: V_q rows voff + kc BK .. (K), columns m0 .. m0 + 127 (M); B: operator rows
+            // A: V_q rows voff + kc BK .. (K), columns m0 .. m0 + 127 (M)
             tma_load_2d(a_s, &maps.vk[it.q], full(stage), voff + kc * BK, it.m0);
-            tma_load_2d(b_s, &maps.L, full(stage), kc * BK, pool + it.n0);
           } else {
             // A: V_q rows m0 .. m0 + 127 (M, MN-major), columns voff + kc BK .. (K)
             for (int b = 0; b < p.a2_boxes; ++b)
               tma_load_2d(a_s + b * p.a2_lbo, &maps.vm[it.q], full(stage),
                           it.m0 + b * p.a2_box_rows, voff + kc * BK);
-            tma_load_2d(b_s, &maps.R, full(stage), kc * BK, pool + it.n0);
           }
+          // B: operator rows pool + n0 .., 32 at a time (the 128B swizzle is a function of
+          // the shared-memory address, so the boxes line up as one tile)
+          for (int b = 0; b < nb; ++b)
+            tma_load_2d(b_s + b * 32 * 128, PASS == 0 ? &maps.L : &maps.R, full(stage), kc * BK,
+                        pool + it.n0 + 32 * b);
           if (++stage == G_STAGES) {
             stage = 0;
             phase ^= 1u;
@@ -920,6 +928,18 @@ int gp_finalise(dmrg2d_ops* ops, GroupPlan* g, cudaStream_t s) {
     if (st == DMRG2D_OK)
       st = map2d(&D->mLlo, D->pL16lo, true, D->KPL, rowsL, 64, G_BM, CU_TENSOR_MAP_SWIZZLE_128B);
     for (int b = 0; b < 2 && st == DMRG2D_OK; ++b) {
+      const bool bf = b == 1;
+      st = map2d(&D->mL32[b], bf ? (const void*)D->pL16 : (const void*)D->pL32, bf, D->KPL,
+                 rowsL, bf ? 64 : 32, 32, CU_TENSOR_MAP_SWIZZLE_128B);
+      if (st == DMRG2D_OK)
+        st = map2d(&D->mR32[b], bf ? (const void*)D->pR16 : (const void*)D->pR32, bf, D->KPR,
+                   rowsR, bf ? 64 : 32, 32, CU_TENSOR_MAP_SWIZZLE_128B);
+    }
+    if (st == DMRG2D_OK)
+      st = map2d(&D->mL32lo, D->pL16lo, true, D->KPL, rowsL, 64, 32, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (st == DMRG2D_OK)
+      st = map2d(&D->mR32lo, D->pR16lo, true, D->KPR, rowsR, 64, 32, CU_TENSOR_MAP_SWIZZLE_128B);
+    for (int b = 0; b < 2 && st == DMRG2D_OK; ++b) {
       const uint32_t rows_box = b ? 256 : 128;
       st = map2d(&D->mR[0][b], D->pR32, false, D->KPR, rowsR, 32, rows_box,
                  CU_TENSOR_MAP_SWIZZLE_128B);
@@ -1041,8 +1061,8 @@ int gp_launch_seg(const dmrg2d_ops* ops, const GroupPlan* g, const void* v, floa
   const int elt = bf ? 2 : 4;
   const int box_rows = bf ? 64 : 32;
   GMaps maps;
-  maps.L = lo_ops ? D->mLlo : D->mL[bf ? 1 : 0];
-  maps.R = lo_ops ? D->mRlo[1] : D->mR[bf ? 1 : 0][1];
+  maps.L = lo_ops ? D->mL32lo : D->mL32[bf ? 1 : 0];  // 32-row boxes of the pools
+  maps.R = lo_ops ? D->mR32lo : D->mR32[bf ? 1 : 0];
   for (int q = 0; q < g->nQ; ++q) {
     const char* base = (const char*)v + (size_t)g->qbase[q] * elt;
     D2_TRY(map2d(&maps.vk[q], base, bf, (uint64_t)g->qld[q], (uint64_t)g->qcols[q], BK, 128,
@@ -1078,9 +1098,9 @@ int gp_launch_seg(const dmrg2d_ops* ops, const GroupPlan* g, const void* v, floa
     p.accum_y = accum ? 1 : 0;
     for (int i = 0; i < 16; ++i)
       for (int n = 0; n < 2; ++n) p.idesc[i][n] = make_idesc(fmt, pass, G_BM, 16 * (i + 1), 0, n);
-    // pass 1: A = V tile (K-major, 16 KB) + B = 128 operator rows; pass 2: A = V tile
-    // (MN-major, 16 KB) + B = 256 operator rows
-    p.tx_bytes = G_STAGE_A + (uint32_t)(pass ? 256 : 128) * 128;
+    // A = the V tile (16 KB); B = 32-row boxes of operator rows (4 KB each)
+    p.a_bytes = G_STAGE_A;
+    p.b_box_bytes = 32 * 128;
     if (p.nitems == 0) continue;
     const int grid = std::min(p.nitems, D->sms);
     if (bf) {

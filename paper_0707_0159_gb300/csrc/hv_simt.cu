@@ -26,40 +26,44 @@ struct SimtParams {
 
 constexpr int BM = 64, BN = 64, BK = 16, TX = 16, TY = 16;  // 256 threads, 4x4 outputs each
 
-template <typename T>
+// BMt x BNt piece per CTA (64 x 64: 4 x 4 outputs per thread; smaller pieces for small
+// superblocks, whose 64 x 64 grid would leave most SMs idle at GB300's FP64 rate)
+template <typename T, int BMt, int BNt>
 __global__ void __launch_bounds__(TX * TY)
 hv_simt_kernel(const T* __restrict__ v, T* __restrict__ y, const T* __restrict__ HL,
                const T* __restrict__ HR, const T* __restrict__ Cval, SimtParams p) {
-  __shared__ T As[BK][BM];
-  __shared__ T Bs[BK][BN];
-  const int nbm = (p.m1 + BM - 1) / BM;
-  const int nbn = (p.m4 + BN - 1) / BN;
+  constexpr int RA = BMt / TX, RB = BNt / TY;  // outputs per thread along rows / columns
+  constexpr int NT = TX * TY;
+  __shared__ T As[BK][BMt];
+  __shared__ T Bs[BK][BNt];
+  const int nbm = (p.m1 + BMt - 1) / BMt;
+  const int nbn = (p.m4 + BNt - 1) / BNt;
   const int bm = blockIdx.x % nbm, i2 = blockIdx.x / nbm;
   const int bn = blockIdx.y % nbn, i3 = blockIdx.y / nbn;
-  const int i0 = bm * BM, j0 = bn * BN;
+  const int i0 = bm * BMt, j0 = bn * BNt;
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
   const int m1 = p.m1, m4 = p.m4;
   const int64_t ld = p.ld;
 
-  T acc[4][4];
+  T acc[RA][RB];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < RA; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+    for (int b = 0; b < RB; ++b) acc[a][b] = T(0);
 
   auto mma_tile = [&]() {
 #pragma unroll
     for (int k = 0; k < BK; ++k) {
-      T av[4], bv[4];
+      T av[RA], bv[RB];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) av[a] = As[k][tx + TX * a];
+      for (int a = 0; a < RA; ++a) av[a] = As[k][tx + TX * a];
 #pragma unroll
-      for (int b = 0; b < 4; ++b) bv[b] = Bs[k][ty + TY * b];
+      for (int b = 0; b < RB; ++b) bv[b] = Bs[k][ty + TY * b];
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+      for (int a = 0; a < RA; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+        for (int b = 0; b < RB; ++b) acc[a][b] += av[a] * bv[b];
     }
   };
 
@@ -68,13 +72,26 @@ hv_simt_kernel(const T* __restrict__ v, T* __restrict__ y, const T* __restrict__
     const T* A = HL + (size_t)e * m1 * m1;                    // A[i][k] = A[i*m1 + k]
     const T* B = v + (int64_t)p.Lcol[e] * m1 + ld * ((int64_t)i3 * m4);  // B[k][j] = B[k + ld*j]
     for (int k0 = 0; k0 < m1; k0 += BK) {
+      if constexpr (BMt == 64 && BNt == 64) {
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int k = tid % BK, i = tid / BK + 16 * r;
-        const int gi = i0 + i, gk = k0 + k;
-        As[k][i] = (gi < m1 && gk < m1) ? A[(size_t)gi * m1 + gk] : T(0);
-        const int gj = j0 + i;  // reuse the same (k, row) mapping for B's 64 columns
-        Bs[k][i] = (gk < m1 && gj < m4) ? B[gk + ld * gj] : T(0);
+        for (int r = 0; r < 4; ++r) {
+          const int k = tid % BK, i = tid / BK + 16 * r;
+          const int gi = i0 + i, gk = k0 + k;
+          As[k][i] = (gi < m1 && gk < m1) ? A[(size_t)gi * m1 + gk] : T(0);
+          const int gj = j0 + i;  // the same (k, row) mapping for B's 64 columns
+          Bs[k][i] = (gk < m1 && gj < m4) ? B[gk + ld * gj] : T(0);
+        }
+      } else {
+        for (int idx = tid; idx < BK * BMt; idx += NT) {
+          const int k = idx % BK, i = idx / BK;
+          const int gi = i0 + i, gk = k0 + k;
+          As[k][i] = (gi < m1 && gk < m1) ? A[(size_t)gi * m1 + gk] : T(0);
+        }
+        for (int idx = tid; idx < BK * BNt; idx += NT) {
+          const int k = idx % BK, j = idx / BK;
+          const int gj = j0 + j, gk = k0 + k;
+          Bs[k][j] = (gk < m1 && gj < m4) ? B[gk + ld * gj] : T(0);
+        }
       }
       __syncthreads();
       mma_tile();
@@ -86,14 +103,27 @@ hv_simt_kernel(const T* __restrict__ v, T* __restrict__ y, const T* __restrict__
     const T* A = v + (int64_t)i2 * m1 + ld * ((int64_t)p.Rcol[e] * m4);  // A[i][k] = A[i + ld*k]
     const T* B = HR + (size_t)e * m4 * m4;                    // B[k][j] = B[j*m4 + k]
     for (int k0 = 0; k0 < m4; k0 += BK) {
+      if constexpr (BMt == 64 && BNt == 64) {
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int i = tid % BM, k = tid / BM + 4 * r;
-        const int gi = i0 + i, gk = k0 + k;
-        As[k][i] = (gi < m1 && gk < m4) ? A[gi + ld * gk] : T(0);
-        const int kb = tid % BK, j = tid / BK + 16 * r;
-        const int gj = j0 + j, gkb = k0 + kb;
-        Bs[kb][j] = (gj < m4 && gkb < m4) ? B[(size_t)gj * m4 + gkb] : T(0);
+        for (int r = 0; r < 4; ++r) {
+          const int i = tid % BM, k = tid / BM + 4 * r;
+          const int gi = i0 + i, gk = k0 + k;
+          As[k][i] = (gi < m1 && gk < m4) ? A[gi + ld * gk] : T(0);
+          const int kb = tid % BK, j = tid / BK + 16 * r;
+          const int gj = j0 + j, gkb = k0 + kb;
+          Bs[kb][j] = (gj < m4 && gkb < m4) ? B[(size_t)gj * m4 + gkb] : T(0);
+        }
+      } else {
+        for (int idx = tid; idx < BK * BMt; idx += NT) {
+          const int i = idx % BMt, k = idx / BMt;
+          const int gi = i0 + i, gk = k0 + k;
+          As[k][i] = (gi < m1 && gk < m4) ? A[gi + ld * gk] : T(0);
+        }
+        for (int idx = tid; idx < BK * BNt; idx += NT) {
+          const int kb = idx % BK, j = idx / BK;
+          const int gj = j0 + j, gkb = k0 + kb;
+          Bs[kb][j] = (gj < m4 && gkb < m4) ? B[(size_t)gj * m4 + gkb] : T(0);
+        }
       }
       __syncthreads();
       mma_tile();
@@ -108,18 +138,18 @@ hv_simt_kernel(const T* __restrict__ v, T* __restrict__ y, const T* __restrict__
     const T c = Cval[e];
     const T* S = v + (int64_t)s2 * m1 + ld * ((int64_t)s3 * m4);
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < RA; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) {
+      for (int b = 0; b < RB; ++b) {
         const int gi = i0 + tx + TX * a, gj = j0 + ty + TY * b;
         if (gi < m1 && gj < m4) acc[a][b] += c * S[gi + ld * gj];
       }
   }
   T* Yt = y + (int64_t)i2 * m1 + ld * ((int64_t)i3 * m4);
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < RA; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
+    for (int b = 0; b < RB; ++b) {
       const int gi = i0 + tx + TX * a, gj = j0 + ty + TY * b;
       if (gi < m1 && gj < m4) Yt[gi + ld * gj] = acc[a][b];
     }
@@ -284,15 +314,31 @@ int launch(const dmrg2d_ops* ops, const T* v, T* y, const T* HL, const T* HR, co
   p.Rcol = ops->dev.Rcol;
   p.Cptr = ops->dev.Cptr;
   p.Csrc = ops->dev.Csrc;
-  const int64_t gx = (int64_t)((ops->m1 + BM - 1) / BM) * ops->d;
-  const int64_t gy = (int64_t)((ops->m4 + BN - 1) / BN) * ops->d;
+  // the largest piece (64, 32 or 16 square) whose grid still gives every SM a CTA
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 1;
+  }
+  auto ctas = [&](int b) {
+    return ((int64_t)(ops->m1 + b - 1) / b) * ops->d * ((int64_t)(ops->m4 + b - 1) / b) * ops->d;
+  };
+  const int tb = ctas(64) >= sms ? 64 : (ctas(32) >= sms ? 32 : 16);
+  const int64_t gx = (int64_t)((ops->m1 + tb - 1) / tb) * ops->d;
+  const int64_t gy = (int64_t)((ops->m4 + tb - 1) / tb) * ops->d;
   if (gx > 0x7fffffff || gy > 65535)
     return set_error(DMRG2D_EUNSUPPORTED, "SIMT grid %lld x %lld too large", (long long)gx,
                      (long long)gy);
   dim3 grid((unsigned)gx, (unsigned)gy);
   auto ev = prof_slot(ops);
   if (ev.first) D2_CUDA(cudaEventRecord(ev.first, s));
-  hv_simt_kernel<T><<<grid, TX * TY, 0, s>>>(v, y, HL, HR, C, p);
+  if (tb == 64)
+    hv_simt_kernel<T, 64, 64><<<grid, TX * TY, 0, s>>>(v, y, HL, HR, C, p);
+  else if (tb == 32)
+    hv_simt_kernel<T, 32, 32><<<grid, TX * TY, 0, s>>>(v, y, HL, HR, C, p);
+  else
+    hv_simt_kernel<T, 16, 16><<<grid, TX * TY, 0, s>>>(v, y, HL, HR, C, p);
   D2_CUDA(cudaGetLastError());
   if (ev.second) D2_CUDA(cudaEventRecord(ev.second, s));
   return DMRG2D_OK;
