@@ -470,8 +470,9 @@ def dmrg_sweep_run(args):
     from paper_0707_0159_gb300 import dmrg2d, synth
     mdl = synth.model("heisenberg", 4, J_leg=1.0, J_rung=1.0)
     ms = [int(m) for m in args.sweep_m.split(",")]
+    prec = args.sweep_precision or args.precision
     out = dmrg2d.sweep(mdl, 12, m_warmup=args.sweep_m_warmup, m_sweeps=ms,
-                       precision=args.precision, tol=1e-9, max_iter=600, krylov_dim=80,
+                       precision=prec, tol=1e-9, max_iter=600, krylov_dim=80,
                        sectors=True)
     e, sw = out["energy"], out["sweep"]
     per = {str(s): min(e[i] for i in range(len(e)) if sw[i] == s) for s in sorted(set(sw))}
@@ -485,8 +486,10 @@ def dmrg_sweep_run(args):
     s2 = {str(sw[i]): out["s2"][i] for i in range(len(e)) if out["s2"][i] == out["s2"][i]}
     return {"lattice": "4x12 open Heisenberg ladder, J=1, S^z_tot = 0 sector",
             "m_warmup": args.sweep_m_warmup, "m_sweeps": ms,
-            "precision": args.precision, "steps": out["n_steps"],
+            "precision": prec, "steps": out["n_steps"],
             "energy_min_per_sweep": per, "energy_last": e[-1], "max_trunc": max(out["trunc"]),
+            "max_trunc_per_sweep": {str(s_): max(out["trunc"][i] for i in range(len(e))
+                                                  if sw[i] == s_) for s_ in sorted(set(sw))},
             "solver_steps": sum(out["iters"]), "seconds": out["seconds"],
             "solve_seconds": out["solve_seconds"], "build_seconds": out["build_seconds"],
             "density_matrix_seconds": out["dm_seconds"], "renorm_seconds": out["renorm_seconds"],
@@ -608,6 +611,8 @@ def main():
     ap.add_argument("--sweep-m", default="128,512,512,1024,1024",
                     help="states kept per finite sweep")
     ap.add_argument("--sweep-m-warmup", type=int, default=128)
+    ap.add_argument("--sweep-precision", default=None, choices=["tf32", "bf16", "fp64"],
+                    help="ground-state H·v precision of the sweep (default: --precision)")
     ap.add_argument("--tile-config", type=int, default=None,
                     help="tensor-core tile configuration index instead of the autotuner")
     ap.add_argument("--ref-seconds", type=float, default=15.0)
