@@ -62,6 +62,9 @@ WORKLOADS = {
     "ladder3_hubbard_d64_m256_dense": (
         lambda synth: synth.workload_ladder3_hubbard_m256(), "tf32",
         {"m": 256, "d": 64, "n_legs": 3, "t": 1.0, "U": 8.0}),
+    "ladder3_hubbard_d64_m128_dense": (   # the same model at m = 128 (V 8192^2, 256 MB)
+        lambda synth: synth.workload_ladder3_hubbard_m256(m=128), "tf32",
+        {"m": 128, "d": 64, "n_legs": 3, "t": 1.0, "U": 8.0}),
     "ladder4_heisenberg_d16_m1024_sectors": (
         lambda synth: synth.workload_ladder4_heisenberg_sectors(), "bf16",
         {"m": 1024, "d": 16, "n_legs": 4, "J": 1.0, "sectors": "S^z_tot = 0, 7 block sectors"}),
@@ -452,6 +455,8 @@ def run_ours(args):
         out["latency"] = {"us_per_hv": ms * 1e3, **lanczos_latency(ops, n, dev)}
     if args.sweep and rank == 0:
         out["dmrg_sweep"] = dmrg_sweep_run(args)
+    if args.precond_study and rank == 0:
+        out["precond_study"] = precond_study(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(seconds=float(args.ref_seconds),
                                            workload=args.workload)
@@ -495,6 +500,84 @@ def dmrg_sweep_run(args):
             "density_matrix_seconds": out["dm_seconds"], "renorm_seconds": out["renorm_seconds"],
             "observables_seconds": out["obs_seconds"], "s2_per_sweep": s2,
             "leg_bond_profile_last_sweep": profile}
+
+
+def precond_study(args):
+    """The learned Davidson preconditioner against Jacobi on the 3-leg Hubbard sector
+    superblock (the structure of the m = 1024 workload: blocks of 12 sites, 25 (N_up, N_dn)
+    sectors, the 3 x 10 lattice at 15 up + 15 down) at m = --precond-m.  The network (2 hidden
+    layers of 256) is trained on logged Jacobi-Davidson steps of seeds 0 .. N-1 (FP64
+    Davidson to 1e-10), then both preconditioners run through the mixed Davidson path (TF32
+    H·v, FP64 outer loop to ||r|| <= 1e-7 |E|) on the unseen seeds 32 .. 39 from the same
+    start vectors (the low-precision Davidson stage to a residual of 1e-3 |E|, above TF32's
+    floor): iterations, H·v counts and time to energy of each."""
+    import numpy as np
+    import torch
+    from paper_0707_0159_gb300 import dmrg2d, synth
+    dev = torch.device("cuda", 0)
+    m = args.precond_m
+    case = lambda seed: synth.workload_ladder3_hubbard_sectors(m=m, seed=seed)
+    net = dmrg2d.MLP(hidden=256, seed=7)
+    rng = np.random.default_rng(11)
+    cap, batch, epochs = 40, 8192, 4
+    t_train = time.perf_counter()
+    losses = []
+    for seed in range(args.precond_train):
+        mdl, left, right, target = case(seed)
+        ops = dmrg2d.build_ops(mdl, left, right, target=target)
+        n = ops.info["n_vec"]
+        pad = dmrg2d.sector_dense_index(ops) < 0
+        v0 = synth.start_vector(n, seed + 100)
+        v0[pad] = 0.0
+        xl = torch.zeros(cap * n, dtype=torch.float64, device=dev)
+        rl = torch.zeros(cap * n, dtype=torch.float64, device=dev)
+        x = torch.from_numpy(v0).to(dev)
+        e, st, code, thetas = dmrg2d.davidson_ground(ops, x, precond="jacobi", tol=1e-10,
+                                                     max_iter=600, log=(cap, xl, rl))
+        D = torch.empty(n, dtype=torch.float64, device=dev)
+        dmrg2d.diagonal(ops, D)
+        steps = min(cap, st["iters"]) - 1
+        X = torch.empty(batch * 4, dtype=torch.float32, device=dev)
+        w = torch.empty(batch, dtype=torch.float32, device=dev)
+        T = torch.empty(batch, dtype=torch.float32, device=dev)
+        valid = torch.from_numpy(np.flatnonzero(~pad)).to(dev)
+        for _ in range(epochs):
+            for k in range(steps):
+                idx = valid[torch.from_numpy(rng.integers(0, valid.numel(), batch)).to(dev)]
+                dmrg2d.mlp_make_batch(ops, xl[k * n:(k + 1) * n], rl[k * n:(k + 1) * n],
+                                      thetas[k], x, D, idx, X, w, T)
+                losses.append(net.train_step(X, w, T, 3e-4))
+        del xl, rl
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t_train
+    rows = []
+    for seed in range(32, 40):
+        mdl, left, right, target = case(seed)
+        ops = dmrg2d.build_ops(mdl, left, right, target=target)
+        n = ops.info["n_vec"]
+        pad = dmrg2d.sector_dense_index(ops) < 0
+        v0 = synth.start_vector(n, seed + 100)
+        v0[pad] = 0.0
+        row = {"seed": seed, "n_vec": n}
+        for pre in ("jacobi", "mlp"):
+            x = torch.from_numpy(v0).to(dev)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e, st, code = dmrg2d.davidson_ground(
+                ops, x, precond=pre, mlp=net if pre == "mlp" else None, precision="tf32",
+                refine=1, tol=1e-3, refine_tol=1e-7, max_iter=400, inner_iter=40, outer_max=40)
+            torch.cuda.synchronize()
+            row[pre] = {"seconds": time.perf_counter() - t0, "energy": e, "status": code,
+                        "iters": st["iters"], "n_hv_low": st["n_hv_low"],
+                        "n_hv_fp64": st["n_hv_fp64"], "resid": st["resid"]}
+        row["energy_rel_diff"] = abs(row["mlp"]["energy"] - row["jacobi"]["energy"]) / abs(
+            row["jacobi"]["energy"])
+        rows.append(row)
+    tot = {pre: {"iters": sum(r[pre]["iters"] for r in rows),
+                 "seconds": sum(r[pre]["seconds"] for r in rows)} for pre in ("jacobi", "mlp")}
+    return {"m": m, "train_seeds": args.precond_train, "eval_seeds": [32, 39],
+            "train_seconds": t_train, "loss_first": losses[0] if losses else None,
+            "loss_last": losses[-1] if losses else None, "per_seed": rows, "total": tot}
 
 
 def kernels_per_hv(tune, prec, sectors):
@@ -613,6 +696,10 @@ def main():
     ap.add_argument("--sweep-m-warmup", type=int, default=128)
     ap.add_argument("--sweep-precision", default=None, choices=["tf32", "bf16", "fp64"],
                     help="ground-state H·v precision of the sweep (default: --precision)")
+    ap.add_argument("--precond-study", action="store_true",
+                    help="also train and evaluate the learned Davidson preconditioner")
+    ap.add_argument("--precond-m", type=int, default=256)
+    ap.add_argument("--precond-train", type=int, default=32)
     ap.add_argument("--tile-config", type=int, default=None,
                     help="tensor-core tile configuration index instead of the autotuner")
     ap.add_argument("--ref-seconds", type=float, default=15.0)

@@ -161,3 +161,28 @@ def test_learned_preconditioner_against_jacobi():
         print("%4d  %12d  %9d  %8.3f  %5.3f" % r)
     # the learned factor must not be catastrophically worse than the formula it replaces
     assert sum(r[2] for r in rows) <= 2 * sum(r[1] for r in rows)
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16x3"])
+def test_mixed_davidson_reaches_fp64_energy(prec):
+    """Davidson with the low-precision H·v (TF32, or split BF16) to a residual above its
+    rounding floor, then the FP64 outer loop: the FP64 Lanczos energy to 1e-9, on a sector
+    superblock, with the Jacobi and with a (fresh: y = 0, i.e. Jacobi) network."""
+    mdl, left, right, target = synth.workload_ladder3_hubbard_sectors(m=64, block_sites=6,
+                                                                      n_up=6, n_dn=6)
+    ops = dmrg2d.build_ops(mdl, left, right, target=target)
+    pad = dmrg2d.sector_dense_index(ops) < 0
+    v0 = np.where(pad, 0.0, synth.start_vector(ops.info["n_vec"], 9))
+    x = torch.from_numpy(v0).to(DEV)
+    e_l, st_l, c_l = dmrg2d.lanczos_ground(ops, x, max_iter=2000, krylov_dim=200, tol=1e-11,
+                                           thick_keep=32)
+    assert c_l == 0
+    net = dmrg2d.MLP(hidden=64, seed=3)
+    for pre in ("jacobi", "mlp"):
+        x = torch.from_numpy(v0).to(DEV)
+        e, st, code = dmrg2d.davidson_ground(ops, x, precond=pre, mlp=net if pre == "mlp" else None,
+                                             precision=prec, refine=1, tol=1e-3, refine_tol=1e-9,
+                                             max_iter=300, inner_iter=40, outer_max=40)
+        assert code == 0, (pre, st)
+        assert abs(e - e_l) <= 1e-9 * abs(e_l), (pre, e, e_l)
+        assert st["resid"] <= 1e-9 * abs(e) and st["n_hv_low"] > 0
