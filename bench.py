@@ -65,6 +65,10 @@ WORKLOADS = {
     "ladder3_hubbard_d64_m128_dense": (   # the same model at m = 128 (V 8192^2, 256 MB)
         lambda synth: synth.workload_ladder3_hubbard_m256(m=128), "tf32",
         {"m": 128, "d": 64, "n_legs": 3, "t": 1.0, "U": 8.0}),
+    "ladder2_hubbard_d16_m512_dense": (   # a reduced superblock for the CTA-pair kernel
+        lambda synth: (synth.model("hubbard", 2, t=1.0, U=8.0), synth.hubbard_block(512, 2, 10),
+                       synth.hubbard_block(512, 2, 11), None), "tf32",
+        {"m": 512, "d": 16, "n_legs": 2, "t": 1.0, "U": 8.0}),
     "ladder4_heisenberg_d16_m1024_sectors": (
         lambda synth: synth.workload_ladder4_heisenberg_sectors(), "bf16",
         {"m": 1024, "d": 16, "n_legs": 4, "J": 1.0, "sectors": "S^z_tot = 0, 7 block sectors"}),
