@@ -40,9 +40,12 @@ METRIC = "superblock H·v TFLOP/s & time to ground energy at 1e-8 rel. vs plain 
 # configuration name and dtype.  They hold only for the kernel source they were taken
 # on: `traffic` is reported as null when csrc/hv_tc.cu no longer has this SHA-256.
 NCU_TRAFFIC = {
-    "hv_tc.cu sha256": "0ad9460508c67df0b6c57c28c05df1b9a4fd96bdd87fcc790e9b8f8fbffdf77e",
+    "hv_tc.cu sha256": "91219050f32fedb6f43c765dd1f019281b6f570488124341b14d92751c68d004",
     "bytes": {
-        "CTA-pair kernel 256x256 (8x8-tile blocked raster)|tf32": 15.157e9 + 1.064e9,
+        "CTA-pair kernel 256x256 (8x8-tile blocked raster), phase-2 V in one 3-D copy|tf32":
+            15.21e9 + 1.07e9,
+        "dense kernel 128x256 (8x8-tile blocked raster), phase-2 V in one 3-D copy|bf16":
+            6.81e9 + 1.06e9,
     },
 }
 

@@ -70,6 +70,9 @@ struct TcParams {
   // phases run by this launch: [ph0, ph1) of {0: H_l V, 1: V H_r^T}; accum_y: the
   // epilogue adds the Y already stored (second pass of the two-pass form)
   int ph0, ph1, accum_y;
+  // the phase-2 V operand in one 3-D box (its a2_boxes row blocks) instead of a2_boxes 2-D
+  // boxes; the shared-memory image is the same
+  int a2_3d;
   // scalar tile moves fused into the epilogue (H_c and off-diagonal column terms)
   int fuse;
   const void* v;
@@ -226,9 +229,12 @@ hv_tc_kernel(const __grid_constant__ CUtensorMap mHL, const __grid_constant__ CU
                               c.mt * BM);
               tma_load_2d(b_s, &mVk, full(stage), nb * p.m1 + kc * p.BK, c0);
             } else {
-              for (int b = 0; b < p.a2_boxes; ++b)
-                tma_load_2d(a_s + b * p.a2_lbo, &mVm, full(stage), r0 + b * p.a2_box_rows,
-                            nb * p.m4 + kc * p.BK);
+              if (p.a2_3d)
+                tma_load_3d(a_s, &mVm, full(stage), 0, nb * p.m4 + kc * p.BK, r0 / p.a2_box_rows);
+              else
+                for (int b = 0; b < p.a2_boxes; ++b)
+                  tma_load_2d(a_s + b * p.a2_lbo, &mVm, full(stage), r0 + b * p.a2_box_rows,
+                              nb * p.m4 + kc * p.BK);
               tma_load_2d(b_s, &mHR, full(stage), kc * p.BK,
                           (p.pooled ? p.k2[e].b_pool + (int)(blockIdx.x % p.copies) * p.poolR_rows
                                     : e * p.m4) +
@@ -431,9 +437,12 @@ hv_tc_pair_kernel(const __grid_constant__ CUtensorMap mHL, const __grid_constant
               tma_load_2d_pair(a_s, &mHL, fb, kc * p.BK, arow + mt * BM);
               tma_load_2d_pair(b_s, &mVk, fb, nb * p.m1 + kc * p.BK, c.i3 * p.m4 + cb);
             } else {
-              for (int b = 0; b < p.a2_boxes; ++b)
-                tma_load_2d_pair(a_s + b * p.a2_lbo, &mVm, fb, r0 + b * p.a2_box_rows,
-                                 nb * p.m4 + kc * p.BK);
+              if (p.a2_3d)
+                tma_load_3d_pair(a_s, &mVm, fb, 0, nb * p.m4 + kc * p.BK, r0 / p.a2_box_rows);
+              else
+                for (int b = 0; b < p.a2_boxes; ++b)
+                  tma_load_2d_pair(a_s + b * p.a2_lbo, &mVm, fb, r0 + b * p.a2_box_rows,
+                                   nb * p.m4 + kc * p.BK);
               const int brow = p.pooled ? p.k2[e].b_pool + (int)(cid % p.copies) * p.poolR_rows
                                         : e * p.m4;
               tma_load_2d_pair(b_s, &mHR, fb, kc * p.BK, brow + cb);
@@ -622,6 +631,26 @@ __global__ void k_bf16_lo(const double* __restrict__ x, __nv_bfloat16* __restric
     const double hi = (double)__bfloat162float(__float2bfloat16_rn((float)x[i]));
     o[i] = __float2bfloat16_rn((float)(x[i] - hi));
   }
+}
+
+// A 3-D view of a column-major matrix with leading dimension ld: dim 0 = a row within a
+// block of d0 rows, dim 1 = the column (stride ld), dim 2 = the row block (stride d0); one
+// box {d0, b1, b2} lands in shared memory as b2 consecutive {d0, b1} tiles.
+int make_map3(CUtensorMap* m, const void* base, bool bf16, uint64_t d0, uint64_t d1, uint64_t d2,
+              uint64_t ld, uint32_t b0, uint32_t b1, uint32_t b2, CUtensorMapSwizzle swz) {
+  auto fn = encode_fn();
+  if (!fn) return set_error(DMRG2D_ECUDA, "cuTensorMapEncodeTiled unavailable");
+  const uint64_t elt = bf16 ? 2 : 4;
+  cuuint64_t dims[3] = {d0, d1, d2};
+  cuuint64_t strides[2] = {ld * elt, d0 * elt};
+  cuuint32_t box[3] = {b0, b1, b2};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                  const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return set_error(DMRG2D_EUNSUPPORTED, "3-D tensor map rejected (%d)", (int)r);
+  return DMRG2D_OK;
 }
 
 __global__ void k_round_tf32(const double* __restrict__ x, float* __restrict__ o, int64_t n) {
@@ -923,6 +952,7 @@ static int launch_dense_kernel(const dmrg2d_ops* ops, const TcState* T, const vo
   const bool pair = (variant & 4) != 0;
   const bool use_pool = (variant & 1) != 0;
   const bool two = (variant & 8) != 0;
+  const bool a3 = (variant & 16) != 0;
   const int b = bf ? 1 : 0;
   const int m1 = ops->m1, m4 = ops->m4, d = ops->d;
   const uint32_t BK = bf ? 64 : 32;
@@ -938,6 +968,7 @@ static int launch_dense_kernel(const dmrg2d_ops* ops, const TcState* T, const vo
   p.ph0 = 0;
   p.ph1 = 2;
   p.accum_y = accum ? 1 : 0;
+  p.a2_3d = a3 ? 1 : 0;
   p.BK = (int)BK;
   p.kblk1 = m1 / (int)BK;
   p.kblk2 = m4 / (int)BK;
@@ -985,8 +1016,14 @@ static int launch_dense_kernel(const dmrg2d_ops* ops, const TcState* T, const vo
   CUtensorMap mVk, mVm;
   const uint64_t rows = (uint64_t)ops->ld, cols = (uint64_t)d * m4;
   D2_TRY(make_map(&mVk, v, bf, rows, cols, BK, pair ? P_HALF : T->BN));
-  D2_TRY(make_map(&mVm, v, bf, rows, cols, (uint32_t)p.a2_box_rows, BK,
-                  bf ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B));
+  if (a3) {  // dims {row in block, column, row block}: the four boxes in one copy
+    D2_TRY(make_map3(&mVm, v, bf, (uint64_t)p.a2_box_rows, cols, rows / (uint64_t)p.a2_box_rows,
+                     (uint64_t)ops->ld, (uint32_t)p.a2_box_rows, BK, (uint32_t)p.a2_boxes,
+                     bf ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B));
+  } else {
+    D2_TRY(make_map(&mVm, v, bf, rows, cols, (uint32_t)p.a2_box_rows, BK,
+                    bf ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B));
+  }
   auto ev = prof_slot(ops);
   if (ev.first) D2_CUDA(cudaEventRecord(ev.first, s));
   auto launch = [&](const TcParams& q) {
@@ -1098,13 +1135,17 @@ namespace dmrg2d {
 // 14 + c = grouped configuration c with the scalar moves in a separate kernel (sectors)
 // 20 / 21 = two-pass dense kernel (128-row pieces / CTA pairs)
 // 22 = segment kernels (sectors: M along the long dimension of each V_q, moves separate)
-constexpr int N_CANDIDATES = 23;
+// 23 / 24 = CTA-pair kernel / dense kernel in blocked order, the phase-2 V operand in one
+// 3-D copy per stage
+constexpr int N_CANDIDATES = 25;
 static int idx_to_cfg(int idx) {
   static const int dense_variant[14] = {0, -1, -1, -1, -1, -1, -1, 1, 2, 3, 4, 6, 5, 7};
   if (idx >= 1 && idx <= 6) return idx - 1;
   if (idx == 20) return -1 - 8;
   if (idx == 21) return -1 - 12;
   if (idx == 22) return 2 * gp_num_configs();
+  if (idx == 23) return -1 - (6 | 16);
+  if (idx == 24) return -1 - (2 | 16);
   if (idx >= 14) return gp_num_configs() + idx - 14;
   return -1 - dense_variant[idx];
 }
@@ -1113,6 +1154,10 @@ static bool tc_candidate_ok(const dmrg2d_ops* ops, int idx) {
   if (idx < 0 || idx >= N_CANDIDATES) return false;
   if (idx >= 14 && idx < 20) return ops->sec && ops->tc_ok;  // grouped, separate moves
   if (idx == 22) return ops->sec && ops->tc_ok;               // segment kernels
+  if (idx == 23 || idx == 24) {                                // dense kernels, 3-D V copies
+    const TcState* T = (const TcState*)ops->tc;
+    return !ops->sec && T && T->dense_ok && (idx == 24 || T->pair_ok);
+  }
   if (idx == 0 || idx >= 7) {                                // dense-kernel variants
     const TcState* T = (const TcState*)ops->tc;
     if (ops->sec || !T || !T->dense_ok) return false;
@@ -1152,6 +1197,8 @@ extern "C" const char* dmrg2d_tile_config_name(int index) {
   if (index == 20) return "dense kernel 128x256, two passes (H_l V by column slabs, V H_r^T by row slabs)";
   if (index == 21) return "CTA-pair kernel 256x256, two passes (H_l V by column slabs, V H_r^T by row slabs)";
   if (index == 22) return "segment kernels (M = 128 along V's long dimension, N = one sector), separate moves";
+  if (index == 23) return "CTA-pair kernel 256x256 (8x8-tile blocked raster), phase-2 V in one 3-D copy";
+  if (index == 24) return "dense kernel 128x256 (8x8-tile blocked raster), phase-2 V in one 3-D copy";
   static const char* sep[6] = {
       "grouped 128x128 column-slab, separate moves kernel",
       "grouped 128x128 row-slab, separate moves kernel",
@@ -1208,6 +1255,12 @@ extern "C" int dmrg2d_autotune(dmrg2d_ops* ops, int precision, int* best, double
     double t = -1.0;
     if (tc_candidate_ok(ops, c)) {
       st = tc_run_candidate(ops, v, y, precision, c, s);  // warm-up
+      if (st == DMRG2D_EUNSUPPORTED) {  // a candidate whose tensor maps the driver refuses
+        st = DMRG2D_OK;
+        clear_error();
+        if (ms && c < n_ms) ms[c] = -1.0;
+        continue;
+      }
       float tmin = 1e30f;
       for (int r = 0; r < 3 && st == DMRG2D_OK; ++r) {
         cudaEventRecord(e0, s);

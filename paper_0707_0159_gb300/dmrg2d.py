@@ -317,7 +317,7 @@ def profile_stop(ops: Ops):
     return ms.value, n.value
 
 
-N_TILE_CONFIGS = 23
+N_TILE_CONFIGS = 25
 
 
 def autotune(ops: Ops, precision, stream=None):

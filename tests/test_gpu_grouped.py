@@ -68,13 +68,13 @@ def test_dense_and_grouped_kernels_agree(prec):
     v = synth.start_vector(sb.n_vec, 4)
     ref = sb.apply(v)
     out = {}
-    for cfg in (0, 1, 4, 7, 8, 9, 20):
+    for cfg in (0, 1, 4, 7, 8, 9, 20, 24):
         dmrg2d.set_tile_config(ops, prec, cfg)
         out[cfg] = run(ops, v, prec)
         assert rel(out[cfg], ref) <= TOL[prec]
     # same operands, same K order within a piece: the kernels agree far below the tolerance
     # (config 20, two passes, rounds the first pass's partial sum to FP32 once more)
-    for cfg in (1, 4, 7, 8, 9, 20):
+    for cfg in (1, 4, 7, 8, 9, 20, 24):
         assert rel(out[cfg], out[0]) <= (2e-5 if cfg == 20 else 1e-6), cfg
 
 
@@ -92,7 +92,7 @@ def test_cta_pair_kernel_matches_oracle_and_dense(case, prec):
     ref = sb.apply(v)
     dmrg2d.set_tile_config(ops, prec, 0)
     y0 = run(ops, v, prec)
-    for cfg in (10, 11, 12, 13, 20, 21):  # per-position blocks / pool / two passes
+    for cfg in (10, 11, 12, 13, 20, 21, 23):  # per-position blocks / pool / two passes / 3-D
         dmrg2d.set_tile_config(ops, prec, cfg)
         y = run(ops, v, prec)
         assert rel(y, ref) <= TOL[prec], (cfg, rel(y, ref))
