@@ -483,9 +483,12 @@ def dmrg_sweep_run(args):
     mdl = synth.model("heisenberg", 4, J_leg=1.0, J_rung=1.0)
     ms = [int(m) for m in args.sweep_m.split(",")]
     prec = args.sweep_precision or args.precision
+    net = dmrg2d.MLP(hidden=256, seed=7) if args.sweep_precond == "mlp" else None
     out = dmrg2d.sweep(mdl, 12, m_warmup=args.sweep_m_warmup, m_sweeps=ms,
                        precision=prec, tol=1e-9, max_iter=600, krylov_dim=80,
-                       sectors=True)
+                       sectors=True, solver=args.sweep_solver, precond=args.sweep_precond,
+                       mlp=net, mlp_train_sweeps=args.sweep_mlp_train_sweeps,
+                       mlp_epochs=args.sweep_mlp_epochs)
     e, sw = out["energy"], out["sweep"]
     per = {str(s): min(e[i] for i in range(len(e)) if sw[i] == s) for s in sorted(set(sw))}
     last = max(sw)
@@ -498,11 +501,17 @@ def dmrg_sweep_run(args):
     s2 = {str(sw[i]): out["s2"][i] for i in range(len(e)) if out["s2"][i] == out["s2"][i]}
     return {"lattice": "4x12 open Heisenberg ladder, J=1, S^z_tot = 0 sector",
             "m_warmup": args.sweep_m_warmup, "m_sweeps": ms,
-            "precision": prec, "steps": out["n_steps"],
+            "precision": prec, "solver": args.sweep_solver,
+            "precond": args.sweep_precond if args.sweep_solver == "davidson" else None,
+            "mlp_train_sweeps": args.sweep_mlp_train_sweeps if net is not None else None,
+            "steps": out["n_steps"],
             "energy_min_per_sweep": per, "energy_last": e[-1], "max_trunc": max(out["trunc"]),
             "max_trunc_per_sweep": {str(s_): max(out["trunc"][i] for i in range(len(e))
                                                   if sw[i] == s_) for s_ in sorted(set(sw))},
-            "solver_steps": sum(out["iters"]), "seconds": out["seconds"],
+            "solver_steps": sum(out["iters"]),
+            "solver_steps_per_sweep": {str(s_): sum(out["iters"][i] for i in range(len(e))
+                                                    if sw[i] == s_) for s_ in sorted(set(sw))},
+            "seconds": out["seconds"], "train_seconds": out["train_seconds"],
             "solve_seconds": out["solve_seconds"], "build_seconds": out["build_seconds"],
             "density_matrix_seconds": out["dm_seconds"], "renorm_seconds": out["renorm_seconds"],
             "observables_seconds": out["obs_seconds"], "s2_per_sweep": s2,
@@ -703,6 +712,12 @@ def main():
     ap.add_argument("--sweep-m-warmup", type=int, default=128)
     ap.add_argument("--sweep-precision", default=None, choices=["tf32", "bf16", "fp64"],
                     help="ground-state H·v precision of the sweep (default: --precision)")
+    ap.add_argument("--sweep-solver", default="lanczos", choices=["lanczos", "davidson"])
+    ap.add_argument("--sweep-precond", default="jacobi", choices=["none", "jacobi", "mlp"],
+                    help="Davidson preconditioner of the sweep (mlp: trained in the sweep)")
+    ap.add_argument("--sweep-mlp-train-sweeps", type=int, default=1,
+                    help="the warm-up and sweeps below this index train the network")
+    ap.add_argument("--sweep-mlp-epochs", type=int, default=2)
     ap.add_argument("--precond-study", action="store_true",
                     help="also train and evaluate the learned Davidson preconditioner")
     ap.add_argument("--precond-m", type=int, default=256)

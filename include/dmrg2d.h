@@ -419,14 +419,27 @@ void dmrg2d_free_ops(dmrg2d_ops* ops);
  * Ground states: `precision` FP64 runs the plain Lanczos (thick restart keeping
  * krylov_dim / 4 Ritz vectors, at most 16); TF32/BF16/BF16X3 the mixed solver with FP64
  * refinement where the tensor-core path supports the superblock's shapes (plain FP64
- * otherwise).  Warm-up steps start from a seeded random vector; every
+ * otherwise).  solver = DMRG2D_SWEEP_DAVIDSON takes dmrg2d_davidson_ground instead (basis
+ * of krylov_dim vectors, clamped to 4..48; max_iter Davidson steps; with TF32/BF16/BF16X3
+ * the low-precision stage stops at a residual of 1e-3 |E| (1e-2 for BF16) and the FP64
+ * outer loop finishes at tol), preconditioned by `precond` (DMRG2D_PRECOND_NONE / JACOBI
+ * / MLP).  With DMRG2D_PRECOND_MLP, `mlp` (caller-owned, not NULL) is the learned
+ * preconditioner, trained inside the sweep when mlp_epochs > 0: every solve of the
+ * warm-up and of the sweeps with index < mlp_train_sweeps runs plain Jacobi Davidson,
+ * records its first 16 steps (Ritz vector, residual, Ritz value) and then takes
+ * mlp_epochs passes over them, one Adam step (learning rate 3e-4) of 8192 samples drawn
+ * by a seeded generator per recorded step, on the pairs dmrg2d_mlp_make_batch forms with
+ * the converged vector; the later solves precondition with the network.  mlp_epochs = 0
+ * uses the network as given.  Training time is reported apart (train_seconds).
+ * Warm-up steps start from a seeded random vector; every
  * finite-sweep step starts from the previous ground state carried into its basis (the
  * wavefunction transformation: the new block's U and the stored U of the block that
  * splits into a smaller block and a column).
  * report: caller-owned arrays of `cap` entries receive, per step in order, the
  * superblock ground energy, the truncation error 1 - (kept weight), the number of
  * columns in block 1, the sweep index (-1 for the warm-up) and the solver's steps
- * (Lanczos steps, or low-precision inner steps of the mixed solver); n_steps counts all
+ * (Lanczos steps, low-precision inner steps of the mixed solver, or Davidson steps plus,
+ * in mixed precision, the outer loop's inner steps); n_steps counts all
  * steps (entries beyond cap are not stored).  Synchronises `stream`.
  * Errors: EINVAL (bad options), EUNSUPPORTED (model), solver and CUDA errors. */
 typedef struct dmrg2d_sweep_opts {
@@ -442,7 +455,13 @@ typedef struct dmrg2d_sweep_opts {
   int use_sectors;     /* 1: S^z_tot = 0 sector-restricted superblocks (blocks carry  */
                        /*    N_up labels, density matrices per sector)               */
   int n_up, n_dn;      /* Hubbard ladders: electrons of each spin on the whole ladder */
+  int solver;          /* DMRG2D_SWEEP_LANCZOS (0) or DMRG2D_SWEEP_DAVIDSON (1)         */
+  int precond;         /* Davidson preconditioner (DMRG2D_PRECOND_*)                    */
+  dmrg2d_mlp* mlp;     /* DMRG2D_PRECOND_MLP: the network (trained in place, see above) */
+  int mlp_train_sweeps;/* the warm-up and sweeps below this index train the network     */
+  int mlp_epochs;      /* passes over each training solve's recorded steps (0: none)    */
 } dmrg2d_sweep_opts;
+enum { DMRG2D_SWEEP_LANCZOS = 0, DMRG2D_SWEEP_DAVIDSON = 1 };
 
 typedef struct dmrg2d_sweep_report {
   int cap;             /* entries the arrays below hold                               */
@@ -473,6 +492,7 @@ typedef struct dmrg2d_sweep_report {
   double dm_seconds;   /*   density matrix and its eigenvectors                      */
   double renorm_seconds;/*  new block operators U^T O U and their copy to the host   */
   double obs_seconds;  /*   observables                                              */
+  double train_seconds;/* training of the learned preconditioner (not in solve_seconds)  */
 } dmrg2d_sweep_report;
 
 /* A DMRG run in progress: the model, the lattice and its filling, every block built so far
@@ -483,7 +503,8 @@ typedef struct dmrg2d_sweep_report {
  * no device work.  dmrg2d_sweep then runs the warm-up on the first call and, on every
  * call, opts->n_sweeps more finite sweeps (sweep indices in the report continue from the
  * earlier calls; each sweep's first step starts from the ground state the previous call
- * left), with that call's solver options (precision, tol, max_iter, krylov_dim); its
+ * left), with that call's solver options (precision, tol, max_iter, krylov_dim, solver,
+ * precond, mlp, mlp_train_sweeps, mlp_epochs); its
  * lattice fields must equal the state's (else EINVAL).  Two calls of one sweep each do
  * exactly what one call of two sweeps does.  After a failed call the state is unusable
  * (later calls return EINVAL): free it.  A state is used by one host thread at a time. */

@@ -181,13 +181,25 @@ struct Rng {
     const uint64_t r = s * 0x2545F4914F6CDD1Dull;
     return ((double)(r >> 11) * (1.0 / 9007199254740992.0)) * 2.0 - 1.0;
   }
+  uint64_t next_u64() {
+    s ^= s >> 12;
+    s ^= s << 25;
+    s ^= s >> 27;
+    return s * 0x2545F4914F6CDD1Dull;
+  }
 };
+
+// the learned preconditioner's training inside a sweep: recorded Davidson steps per
+// solve, samples per Adam step, learning rate
+constexpr int kTrainLog = 16;
+constexpr int kTrainBatch = 8192;
+constexpr float kTrainLr = 3e-4f;
 
 class Sweeper {
  public:
   Sweeper(const dmrg2d_model* M, const dmrg2d_sweep_opts* o, dmrg2d_sweep_report* rep,
           cudaStream_t s)
-      : M_(*M), o_(*o), rep_(rep), strm_(s), rng_(o->seed) {}
+      : M_(*M), o_(*o), rep_(rep), strm_(s), rng_(o->seed), train_rng_(o->seed ^ 0x7A11ull) {}
 
   // Column operators, their device copies and the library handles (once per run).
   int init() {
@@ -326,9 +338,15 @@ class Sweeper {
     o_.tol = o->tol;
     o_.max_iter = o->max_iter;
     o_.krylov_dim = o->krylov_dim;
+    o_.solver = o->solver;
+    o_.precond = o->precond;
+    o_.mlp = o->mlp;
+    o_.mlp_train_sweeps = o->mlp_train_sweeps;
+    o_.mlp_epochs = o->mlp_epochs;
     rep_ = rep;
     strm_ = s;
     solve_seconds = build_seconds = dm_seconds = renorm_seconds = obs_seconds = 0.0;
+    train_seconds = 0.0;
     if (libs_.bl) D2_BLAS(cublasSetStream(libs_.bl, strm_));
     if (libs_.sv) D2_SOLV(cusolverDnSetStream(libs_.sv, strm_));
     return DMRG2D_OK;
@@ -346,11 +364,110 @@ class Sweeper {
   }
 
   double solve_seconds = 0.0, build_seconds = 0.0, dm_seconds = 0.0, renorm_seconds = 0.0,
-         obs_seconds = 0.0;
+         obs_seconds = 0.0, train_seconds = 0.0;
 
  private:
   static double since(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+
+  // HMED: the superblock ground state from the start vector x (overwritten).  Lanczos:
+  // plain FP64 with thick restart, or the mixed solver (low-precision H·v, FP64 outer
+  // loop); Davidson: the same precisions with the chosen preconditioner.  A Davidson solve
+  // that trains the learned preconditioner (warm-up and the first mlp_train_sweeps sweeps)
+  // runs with Jacobi, records its first steps and then trains the network on them.
+  int solve(const dmrg2d_ops* ops, const dmrg2d_ops_info& info, DBuf& x, int sweep,
+            double* energy, dmrg2d_solver_stats* stats) {
+    const bool mixed = o_.precision != DMRG2D_FP64 && info.tc_ok;
+    const auto t0 = std::chrono::steady_clock::now();
+    if (o_.solver == DMRG2D_SWEEP_LANCZOS) {
+      dmrg2d_solver_opts so;
+      dmrg2d_default_solver_opts(&so);
+      so.tol = o_.tol;
+      so.krylov_dim = o_.krylov_dim;
+      if (mixed) {
+        so.precision = o_.precision;
+        so.refine = 1;
+        so.inner_iter = std::min(o_.max_iter, 300);
+        so.outer_max = 40;
+      } else {
+        so.precision = DMRG2D_FP64;
+        so.max_iter = o_.max_iter;
+        so.thick_keep = std::min(16, o_.krylov_dim / 4);
+      }
+      const int st = dmrg2d_lanczos_ground(ops, &so, x.p, energy, stats, strm_);
+      solve_seconds += since(t0);
+      return st;
+    }
+    dmrg2d_davidson_opts dv;
+    dmrg2d_default_davidson_opts(&dv);
+    dv.max_iter = o_.max_iter;
+    dv.max_subspace = std::min(48, std::max(4, o_.krylov_dim));
+    const bool train =
+        o_.precond == DMRG2D_PRECOND_MLP && o_.mlp_epochs > 0 && sweep < o_.mlp_train_sweeps;
+    dv.precond = train ? DMRG2D_PRECOND_JACOBI : o_.precond;
+    dv.mlp = o_.mlp;
+    if (mixed) {
+      dv.precision = o_.precision;
+      dv.refine = 1;
+      dv.tol = std::max(o_.tol, o_.precision == DMRG2D_BF16 ? 1e-2 : 1e-3);
+      dv.refine_tol = o_.tol;
+      dv.inner_iter = 40;
+      dv.outer_max = 40;
+    } else {
+      dv.precision = DMRG2D_FP64;
+      dv.tol = o_.tol;
+    }
+    const int64_t n = info.n_vec;
+    DBuf xl, rl;
+    std::vector<double> theta(kTrainLog, std::nan(""));  // NaN: step not recorded
+    if (train) {
+      D2_TRY(xl.alloc((size_t)kTrainLog * n));
+      D2_TRY(rl.alloc((size_t)kTrainLog * n));
+      dv.log_cap = kTrainLog;
+      dv.log_x = xl.p;
+      dv.log_r = rl.p;
+      dv.log_theta = theta.data();
+    }
+    const int st = dmrg2d_davidson_ground(ops, &dv, x.p, energy, stats, strm_);
+    solve_seconds += since(t0);
+    if (!train || (st != DMRG2D_OK && st != DMRG2D_ENOCONV)) return st;
+    // the recorded steps (the Davidson steps, not the outer loop's), less the last one,
+    // which is the converged vector itself
+    int logged = 0;
+    while (logged < kTrainLog && std::isfinite(theta[logged])) ++logged;
+    const auto tt = std::chrono::steady_clock::now();
+    D2_TRY(train_mlp(ops, n, xl, rl, theta, logged - 1, x.p));
+    train_seconds += since(tt);
+    return st;
+  }
+
+  // mlp_epochs passes over the recorded steps k < steps: per step one batch of samples at
+  // seeded random positions (padding positions of a sector layout carry zero weight and
+  // target) and one Adam step.
+  int train_mlp(const dmrg2d_ops* ops, int64_t n, const DBuf& xl, const DBuf& rl,
+                const std::vector<double>& theta, int steps, const double* xf) {
+    if (steps < 1) return DMRG2D_OK;
+    DBuf D, f;
+    D2_TRY(D.alloc((size_t)n));
+    D2_TRY(dmrg2d_diagonal(ops, D.p, strm_));
+    D2_TRY(f.alloc((size_t)kTrainBatch * 3));  // X (B x 4), w (B), T (B) as floats
+    float* X = (float*)f.p;
+    float* w = X + 4 * (size_t)kTrainBatch;
+    float* T = w + kTrainBatch;
+    std::vector<int64_t> idx(kTrainBatch);
+    IBuf d_idx;
+    for (int e = 0; e < o_.mlp_epochs; ++e)
+      for (int k = 0; k < steps; ++k) {
+        for (auto& i : idx) i = (int64_t)(train_rng_.next_u64() % (uint64_t)n);
+        D2_TRY(d_idx.upload(idx, strm_));
+        D2_TRY(dmrg2d_mlp_make_batch(ops, xl.p + (size_t)k * n, rl.p + (size_t)k * n, theta[k],
+                                     xf, D.p, (const int64_t*)d_idx.p, kTrainBatch, X, w, T,
+                                     strm_));
+        D2_TRY(dmrg2d_mlp_train_step(o_.mlp, X, w, T, kTrainBatch, kTrainLr, nullptr, strm_));
+      }
+    D2_CUDA(cudaStreamSynchronize(strm_));
+    return DMRG2D_OK;
   }
   Block column_block() const {
     Block b;
@@ -779,26 +896,9 @@ class Sweeper {
       }
       D2_TRY(x.upload(x0, strm_));
     }
-    dmrg2d_solver_opts so;
-    dmrg2d_default_solver_opts(&so);
-    so.tol = o_.tol;
-    so.krylov_dim = o_.krylov_dim;
-    const bool mixed = o_.precision != DMRG2D_FP64 && info.tc_ok;
-    if (mixed) {
-      so.precision = o_.precision;
-      so.refine = 1;
-      so.inner_iter = std::min(o_.max_iter, 300);
-      so.outer_max = 40;
-    } else {
-      so.precision = DMRG2D_FP64;
-      so.max_iter = o_.max_iter;
-      so.thick_keep = std::min(16, o_.krylov_dim / 4);
-    }
     double energy = 0.0;
     dmrg2d_solver_stats stats{};
-    const auto t0 = std::chrono::steady_clock::now();
-    const int st = dmrg2d_lanczos_ground(ops, &so, x.p, &energy, &stats, strm_);
-    solve_seconds += since(t0);
+    const int st = solve(ops, info, x, sweep, &energy, &stats);
     if (st != DMRG2D_OK && st != DMRG2D_ENOCONV) return st;
     const auto td = std::chrono::steady_clock::now();
     // the ground state as the dense V ((m1 d) x (d m4)) for the next step's start vector
@@ -1145,6 +1245,7 @@ class Sweeper {
   double last_energy_ = 0.0;
   cudaStream_t strm_;
   Rng rng_;
+  Rng train_rng_;  // sample positions of the learned preconditioner's training batches
   SpinColumnOps col_;
   Libs libs_;
   DBuf dH_col_;
@@ -1197,6 +1298,15 @@ int check_call(const dmrg2d_sweep_opts* opts) {
     if (opts->m_sweep[i] < 1) return set_error(DMRG2D_EINVAL, "sweep: m_sweep[%d] < 1", i);
   if (opts->max_iter < 1 || opts->krylov_dim < 2 || !(opts->tol > 0.0))
     return set_error(DMRG2D_EINVAL, "sweep: bad solver options");
+  if (opts->solver != DMRG2D_SWEEP_LANCZOS && opts->solver != DMRG2D_SWEEP_DAVIDSON)
+    return set_error(DMRG2D_EINVAL, "sweep: unknown solver %d", opts->solver);
+  if (opts->solver == DMRG2D_SWEEP_DAVIDSON) {
+    if (opts->precond < DMRG2D_PRECOND_NONE || opts->precond > DMRG2D_PRECOND_MLP)
+      return set_error(DMRG2D_EINVAL, "sweep: unknown preconditioner %d", opts->precond);
+    if (opts->precond == DMRG2D_PRECOND_MLP && !opts->mlp)
+      return set_error(DMRG2D_EINVAL, "sweep: the MLP preconditioner needs a network");
+    if (opts->mlp_epochs < 0) return set_error(DMRG2D_EINVAL, "sweep: mlp_epochs < 0");
+  }
   return DMRG2D_OK;
 }
 
@@ -1259,6 +1369,7 @@ extern "C" int dmrg2d_sweep(dmrg2d_state* state, const dmrg2d_sweep_opts* opts,
   report->n_steps = 0;
   report->seconds = report->solve_seconds = report->build_seconds = 0.0;
   report->dm_seconds = report->renorm_seconds = report->obs_seconds = 0.0;
+  report->train_seconds = 0.0;
   const auto t0 = std::chrono::steady_clock::now();
   int st = sw.begin_call(opts, report, (cudaStream_t)stream);
   if (st == DMRG2D_OK && !state->ready) {
@@ -1274,5 +1385,6 @@ extern "C" int dmrg2d_sweep(dmrg2d_state* state, const dmrg2d_sweep_opts* opts,
   report->dm_seconds = sw.dm_seconds;
   report->renorm_seconds = sw.renorm_seconds;
   report->obs_seconds = sw.obs_seconds;
+  report->train_seconds = sw.train_seconds;
   return st;
 }

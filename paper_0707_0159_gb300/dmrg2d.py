@@ -44,7 +44,9 @@ class SweepOpts(C.Structure):
     _fields_ = [("n_columns", C.c_int), ("m_warmup", C.c_int), ("n_sweeps", C.c_int),
                 ("m_sweep", C.POINTER(C.c_int)), ("precision", C.c_int), ("tol", C.c_double),
                 ("max_iter", C.c_int), ("krylov_dim", C.c_int), ("seed", C.c_uint64),
-                ("use_sectors", C.c_int), ("n_up", C.c_int), ("n_dn", C.c_int)]
+                ("use_sectors", C.c_int), ("n_up", C.c_int), ("n_dn", C.c_int),
+                ("solver", C.c_int), ("precond", C.c_int), ("mlp", C.c_void_p),
+                ("mlp_train_sweeps", C.c_int), ("mlp_epochs", C.c_int)]
 
 
 class SweepReport(C.Structure):
@@ -56,7 +58,7 @@ class SweepReport(C.Structure):
                 ("seconds", C.c_double),
                 ("solve_seconds", C.c_double), ("build_seconds", C.c_double),
                 ("dm_seconds", C.c_double), ("renorm_seconds", C.c_double),
-                ("obs_seconds", C.c_double)]
+                ("obs_seconds", C.c_double), ("train_seconds", C.c_double)]
 
 
 class StateInfo(C.Structure):
@@ -412,6 +414,7 @@ def tridiag_lowest(alpha, beta, stream=None):
 
 
 PRECOND = {"none": 0, "jacobi": 1, "mlp": 2}
+SWEEP_SOLVER = {"lanczos": 0, "davidson": 1}
 
 
 def site_densities(ops: Ops, x, stream=None) -> dict:
@@ -550,26 +553,36 @@ class SweepState:
         self.model = model
         self._fixed = dict(n_columns=int(n_columns), m_warmup=int(m_warmup), seed=int(seed),
                            use_sectors=int(bool(sectors)), n_up=int(n_up), n_dn=int(n_dn))
-        opts = self._opts([], FP64, 1e-10, 300, 100)
+        opts = self._opts([], FP64, 1e-10, 300, 100, {})
         mdl = _model(model)
         p = C.c_void_p()
         _check(lib().dmrg2d_state_create(C.byref(mdl), C.byref(opts[0]), C.byref(p)))
         self._p = p
 
-    def _opts(self, m_sweeps, precision, tol, max_iter, krylov_dim):
+    def _opts(self, m_sweeps, precision, tol, max_iter, krylov_dim, dav):
         ms = (C.c_int * max(1, len(m_sweeps)))(*[int(m) for m in m_sweeps])
         f = self._fixed
+        mlp = dav.get("mlp")
         o = SweepOpts(f["n_columns"], f["m_warmup"], len(m_sweeps), ms, int(precision),
                       float(tol), int(max_iter), int(krylov_dim), f["seed"], f["use_sectors"],
-                      f["n_up"], f["n_dn"])
+                      f["n_up"], f["n_dn"], SWEEP_SOLVER[dav.get("solver", "lanczos")],
+                      PRECOND.get(dav.get("precond", "jacobi"), dav.get("precond")),
+                      mlp.ptr if mlp is not None else None, int(dav.get("mlp_train_sweeps", 1)),
+                      int(dav.get("mlp_epochs", 1)))
         return o, ms
 
     def sweep(self, m_sweeps, precision=FP64, tol=1e-10, max_iter=300, krylov_dim=100,
-              cap=4096, stream=None) -> dict:
+              cap=4096, stream=None, solver="lanczos", precond="jacobi", mlp=None,
+              mlp_train_sweeps=1, mlp_epochs=1) -> dict:
         """One finite sweep per entry of m_sweeps (after the warm-up on the first call);
-        the per-step report as dmrg2d.sweep returns it."""
+        the per-step report as dmrg2d.sweep returns it.  solver "davidson" takes the
+        Davidson solver with precond "none" / "jacobi" / "mlp"; with "mlp" the network
+        `mlp` is trained in place on the warm-up's solves and those of the sweeps with
+        index < mlp_train_sweeps (mlp_epochs passes; 0: used as given)."""
         precision = PRECISION.get(precision, precision)
-        opts, ms = self._opts(m_sweeps, precision, tol, max_iter, krylov_dim)
+        opts, ms = self._opts(m_sweeps, precision, tol, max_iter, krylov_dim,
+                              dict(solver=solver, precond=precond, mlp=mlp,
+                                   mlp_train_sweeps=mlp_train_sweeps, mlp_epochs=mlp_epochs))
         e, t = (C.c_double * cap)(), (C.c_double * cap)()
         ll, sw, it = (C.c_int * cap)(), (C.c_int * cap)(), (C.c_int * cap)()
         nl = int(self.model["n_legs"])
@@ -578,7 +591,7 @@ class SweepState:
         nd = 8 * nl + 2
         dens = (C.c_double * (cap * nd))()
         rep = SweepReport(cap, 0, e, t, ll, sw, it, leg, rung, s2, dens, 0.0, 0.0, 0.0, 0.0, 0.0,
-                          0.0)
+                          0.0, 0.0)
         _check(lib().dmrg2d_sweep(self._p, C.byref(opts), C.byref(rep), _stream(stream)))
         n = min(rep.n_steps, cap)
         return {"energy": list(e[:n]), "trunc": list(t[:n]), "l": list(ll[:n]),
@@ -589,7 +602,7 @@ class SweepState:
                 "n_steps": rep.n_steps, "seconds": rep.seconds,
                 "solve_seconds": rep.solve_seconds, "build_seconds": rep.build_seconds,
                 "dm_seconds": rep.dm_seconds, "renorm_seconds": rep.renorm_seconds,
-                **_sweep_densities(dens, n, nl)}
+                "train_seconds": rep.train_seconds, **_sweep_densities(dens, n, nl)}
 
     def info(self) -> dict:
         inf = StateInfo()
@@ -610,18 +623,19 @@ class SweepState:
 
 def sweep(model: dict, n_columns: int, m_warmup: int, m_sweeps, precision=FP64, tol=1e-10,
           max_iter=300, krylov_dim=100, seed=1, cap=4096, sectors=False, n_up=0, n_dn=0,
-          stream=None) -> dict:
+          stream=None, **davidson) -> dict:
     """dmrg2d_sweep on a fresh state: warm-up plus one finite sweep per entry of m_sweeps
     on an n-leg Heisenberg ladder (or, with sectors=True and the filling n_up, n_dn, a
     Hubbard ladder) of n_columns columns.  Returns the per-step energy, truncation error,
     block-1 length and sweep index (-1 = warm-up), the observables and the timings; for
     Hubbard ladders "n" (steps x 2 columns x n_legs x [up, down]), "h", "sd" (steps x 2 x
-    n_legs) and "S" (steps x 2) are the central columns' site densities."""
+    n_legs) and "S" (steps x 2) are the central columns' site densities.  The keyword
+    arguments solver, precond, mlp, mlp_train_sweeps, mlp_epochs are SweepState.sweep's."""
     st = SweepState(model, n_columns, m_warmup, seed=seed, sectors=sectors, n_up=n_up,
                     n_dn=n_dn)
     try:
         return st.sweep(m_sweeps, precision=precision, tol=tol, max_iter=max_iter,
-                        krylov_dim=krylov_dim, cap=cap, stream=stream)
+                        krylov_dim=krylov_dim, cap=cap, stream=stream, **davidson)
     finally:
         st.free()
 

@@ -117,3 +117,34 @@ def test_sweep_state_is_created_and_validated_on_host(lib):
     with pytest.raises(dmrg2d.Dmrg2dError) as e:
         dmrg2d.SweepState(synth.model("hubbard", 2), 6, 16, sectors=True, n_up=13)
     assert e.value.code == -1
+
+
+@pytest.mark.parametrize("kw", [dict(solver="davidson", precond=7),
+                                dict(solver="davidson", precond="mlp", mlp=None),
+                                dict(solver="davidson", precond="mlp", mlp_epochs=-1)])
+def test_sweep_solver_options_are_validated_on_host(lib, kw):
+    """The sweep's solver fields (unknown preconditioner, the learned one without a
+    network, negative epochs) are refused before the first device call."""
+    from paper_0707_0159_gb300 import dmrg2d, synth
+    st = dmrg2d.SweepState(synth.model("heisenberg", 2), 6, 8)
+    if kw.get("mlp_epochs") == -1:
+        class _Net:                      # any non-NULL pointer passes the NULL check
+            ptr = 1
+        kw = dict(kw, mlp=_Net())
+    with pytest.raises(dmrg2d.Dmrg2dError) as e:
+        st.sweep([8], **kw)
+    assert e.value.code == -1
+    assert st.info()["failed"] == 0 and st.info()["warmed_up"] == 0
+    st.free()
+
+
+def test_sweep_rejects_an_unknown_solver(lib):
+    from paper_0707_0159_gb300 import dmrg2d, synth
+    st = dmrg2d.SweepState(synth.model("heisenberg", 2), 6, 8)
+    opts, ms = st._opts([8], dmrg2d.FP64, 1e-10, 300, 100, {})
+    opts.solver = 5
+    rep = dmrg2d.SweepReport()
+    rep.cap = 0
+    assert dmrg2d.lib().dmrg2d_sweep(st._p, dmrg2d.C.byref(opts), dmrg2d.C.byref(rep), None) == -1
+    assert st.info()["failed"] == 0
+    st.free()

@@ -220,3 +220,46 @@ def test_sweep_state_continues_across_calls(kind):
     assert e.value.code == -1
     st.free()
     bad.free()
+
+
+@pytest.mark.parametrize("n,m", [(2, 8), (3, 16)])
+def test_davidson_sweep_matches_oracle(n, m):
+    """The sweep with the Davidson solver (Jacobi preconditioner) in place of Lanczos gives
+    the oracle's energies and truncation errors step by step."""
+    mdl = model(n)
+    ref = odmrg.dmrg(mdl, 6, m_warmup=m, m_sweeps=[m, m])
+    assert min(ref["gap"]) > 1e-7
+    out = dmrg2d.sweep(mdl, 6, m_warmup=m, m_sweeps=[m, m], precision="fp64", tol=1e-12,
+                       max_iter=800, krylov_dim=32, solver="davidson", precond="jacobi")
+    assert out["l"] == ref["l"] and out["sweep"] == ref["sweep"]
+    assert np.allclose(out["energy"], ref["energy"], rtol=1e-10, atol=0)
+    assert np.allclose(out["trunc"], ref["trunc"], rtol=1e-5, atol=1e-12)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "tf32"])
+def test_learned_preconditioner_trains_inside_the_sweep(precision):
+    """Davidson with the learned preconditioner in a sector sweep: the network trains on
+    the Jacobi solves of the warm-up and the first sweep (its parameters change, the time
+    is reported apart), the later sweeps precondition with it, and every step's energy is
+    the oracle's (2 x 8 ladder, m = 8 then 16: the density-matrix cuts have gaps, so the
+    kept subspaces are unique), as are those of the Jacobi and Lanczos sweeps."""
+    mdl = model(2)
+    ms = dict(m_warmup=8, m_sweeps=[8, 16, 16])
+    ref = odmrg.dmrg(mdl, 8, **ms)
+    assert min(ref["gap"]) > 1e-7
+    kw = dict(**ms, precision=precision, tol=1e-11, max_iter=800, krylov_dim=32,
+              sectors=True, solver="davidson")
+    jac = dmrg2d.sweep(mdl, 8, precond="jacobi", **kw)
+    net = dmrg2d.MLP(hidden=64, seed=3)
+    p0 = net.get_params()
+    lrn = dmrg2d.sweep(mdl, 8, precond="mlp", mlp=net, mlp_train_sweeps=1, mlp_epochs=2, **kw)
+    assert lrn["train_seconds"] > 0 and jac["train_seconds"] == 0
+    p1 = net.get_params()
+    assert np.all(np.isfinite(p1)) and not np.array_equal(p1, p0)
+    lan = dmrg2d.sweep(mdl, 8, **{k: v for k, v in kw.items() if k != "solver"})
+    # a network used as given (no training) leaves its parameters alone
+    lrn2 = dmrg2d.sweep(mdl, 8, precond="mlp", mlp=net, mlp_epochs=0, **kw)
+    assert np.array_equal(net.get_params(), p1) and lrn2["train_seconds"] == 0
+    for out in (jac, lrn, lan, lrn2):
+        assert out["l"] == ref["l"] and out["sweep"] == ref["sweep"]
+        assert np.allclose(out["energy"], ref["energy"], rtol=1e-9, atol=0)
