@@ -512,6 +512,7 @@ def dmrg_sweep_run(args):
             "solver_steps_per_sweep": {str(s_): sum(out["iters"][i] for i in range(len(e))
                                                     if sw[i] == s_) for s_ in sorted(set(sw))},
             "seconds": out["seconds"], "train_seconds": out["train_seconds"],
+            "transform_seconds": out["transform_seconds"],
             "solve_seconds": out["solve_seconds"], "build_seconds": out["build_seconds"],
             "density_matrix_seconds": out["dm_seconds"], "renorm_seconds": out["renorm_seconds"],
             "observables_seconds": out["obs_seconds"], "s2_per_sweep": s2,
@@ -632,9 +633,7 @@ def time_to_energy(ops, n, prec, args, dev):
     from paper_0707_0159_gb300 import dmrg2d, synth
     v0 = torch.from_numpy(synth.start_vector(n, 3)).to(dev)
     res = {"tol_rel_residual": args.tte_tol}
-    # float-pair FP64 (FP64X) refinement H·v exists for dense superblocks only
-    dense = ops.info["n_sectors"] == 0
-    runs = (("mixed", "fp64x"), ("mixed_fp64_refine", "fp64")) if dense else (("mixed", "fp64"),)
+    runs = (("mixed", "fp64x"), ("mixed_fp64_refine", "fp64"))
     for key, rprec in runs:
         x = v0.clone()
         torch.cuda.synchronize()

@@ -64,7 +64,7 @@ enum {
   DMRG2D_FP32 = 3,   /* v float, y float; FP32 FMA on CUDA cores                      */
   DMRG2D_FP64X = 4,  /* v, y double; float-pair arithmetic (~48-bit significands) on
                         the FP32 CUDA cores: FP64 emulated for the mixed solver's
-                        residuals; dense superblocks only                             */
+                        residuals (sector layouts: the scalar moves in FP64)         */
   DMRG2D_BF16X3 = 5  /* split BF16: v = [v_hi | v_lo], 2 n_vec bf16 values with
                         v_hi = bf16(x), v_lo = bf16(x - v_hi) (dmrg2d_convert_input);
                         y float; three BF16 tensor-core products into FP32,
@@ -184,7 +184,7 @@ typedef struct dmrg2d_solver_opts {
                           start (2 = full reorthogonalisation as in the plain solve,
                           1 = one pass, 0 = the three-term recurrence only)          */
   int refine_precision;/* mixed: H·v of the outer loop's residuals, DMRG2D_FP64 or
-                          DMRG2D_FP64X (float pairs, dense superblocks)              */
+                          DMRG2D_FP64X (float pairs)                                 */
   int thick_keep;      /* plain Lanczos, at a full basis: 0 = explicit restart from the
                           lowest Ritz vector; p in 1..32 = thick restart (Wu and Simon)
                           keeping the p lowest Ritz vectors and the next Lanczos vector,
@@ -418,8 +418,8 @@ void dmrg2d_free_ops(dmrg2d_ops* ops);
  * dsyevd); ties in the density-matrix spectrum keep the eigenvectors dsyevd returns last.
  * Ground states: `precision` FP64 runs the plain Lanczos (thick restart keeping
  * krylov_dim / 4 Ritz vectors, at most 16); TF32/BF16/BF16X3 the mixed solver with FP64
- * refinement where the tensor-core path supports the superblock's shapes (plain FP64
- * otherwise).  solver = DMRG2D_SWEEP_DAVIDSON takes dmrg2d_davidson_ground instead (basis
+ * refinement (its outer-loop H·v in float pairs, DMRG2D_FP64X) where the tensor-core path
+ * supports the superblock's shapes (plain FP64 otherwise).  solver = DMRG2D_SWEEP_DAVIDSON takes dmrg2d_davidson_ground instead (basis
  * of krylov_dim vectors, clamped to 4..48; max_iter Davidson steps; with TF32/BF16/BF16X3
  * the low-precision stage stops at a residual of 1e-3 |E| (1e-2 for BF16) and the FP64
  * outer loop finishes at tol), preconditioned by `precond` (DMRG2D_PRECOND_NONE / JACOBI
@@ -493,6 +493,7 @@ typedef struct dmrg2d_sweep_report {
   double renorm_seconds;/*  new block operators U^T O U and their copy to the host   */
   double obs_seconds;  /*   observables                                              */
   double train_seconds;/* training of the learned preconditioner (not in solve_seconds)  */
+  double transform_seconds; /* wavefunction transformations (the next step's start)   */
 } dmrg2d_sweep_report;
 
 /* A DMRG run in progress: the model, the lattice and its filling, every block built so far

@@ -8,6 +8,7 @@
 //   3. scalar moves (H_c and off-diagonal column terms): acc += c * V_tile(i2', i3')
 // and writes Y once.  V is column-major with leading dimension m1*d.
 #include "common.h"
+#include "ff.cuh"
 
 namespace dmrg2d {
 
@@ -155,36 +156,9 @@ hv_simt_kernel(const T* __restrict__ v, T* __restrict__ y, const T* __restrict__
     }
 }
 
-// ---- FP64 emulated with float pairs (FP64X) ------------------------------------------------
-// A double x is carried as (hi, lo) = (fl(x), fl(x - hi)): about 48 significant bits.
-// Products are exact in two floats (hi*hi by FMA error-free transformation, cross terms
-// added to the error word; lo*lo dropped, 2^-48 relative); sums use the two-sum of Knuth
-// on the high words with all errors collected in the low word, renormalised at the end.
-// Relative error per H·v ~ 2^-48 sqrt(K) (K = terms per output), far below what the
-// mixed solver's residual needs.  Same tiling as hv_simt_kernel; float-pair arithmetic
-// runs on the FP32 pipes (64x the FP64 rate on this part).
-struct ff {
-  float hi, lo;
-};
-__device__ __forceinline__ ff ff_of(double x) {
-  const float h = __double2float_rn(x);
-  return {h, __double2float_rn(x - (double)h)};
-}
-// acc (sum in hi, collected errors in lo) += a * b
-__device__ __forceinline__ void ff_fma(ff& acc, const ff a, const ff b) {
-  // __fmul_rn / __fadd_rn: never contracted into an FMA, which would break the two-sum
-  const float p = __fmul_rn(a.hi, b.hi);
-  float e = fmaf(a.hi, b.hi, -p);        // exact: a.hi b.hi = p + e
-  e = fmaf(a.hi, b.lo, e);
-  e = fmaf(a.lo, b.hi, e);
-  const float s = __fadd_rn(acc.hi, p);  // two-sum of the high words
-  const float bb = __fsub_rn(s, acc.hi);
-  const float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-  acc.hi = s;
-  acc.lo = __fadd_rn(acc.lo, __fadd_rn(err, e));
-}
-__device__ __forceinline__ double ff_to_double(const ff a) { return (double)a.hi + (double)a.lo; }
-
+// ---- FP64 emulated with float pairs (FP64X, ff.cuh) ------------------------------------
+// Same tiling as hv_simt_kernel; float-pair arithmetic runs on the FP32 pipes (64x the
+// FP64 rate on this part).
 __global__ void __launch_bounds__(TX * TY)
 hv_simt_ff_kernel(const double* __restrict__ v, double* __restrict__ y,
                   const double* __restrict__ HL, const double* __restrict__ HR,
@@ -363,8 +337,7 @@ int launch_ff(const dmrg2d_ops* ops, const double* v, double* y, cudaStream_t s)
 }  // namespace
 
 int launch_hv_simt_ff64(const dmrg2d_ops* ops, const double* v, double* y, cudaStream_t s) {
-  if (ops->sec)
-    return set_error(DMRG2D_EUNSUPPORTED, "FP64X H·v: dense superblocks only");
+  if (ops->sec) return sec_apply(ops, v, y, DMRG2D_FP64X, s);
   return launch_ff(ops, v, y, s);
 }
 

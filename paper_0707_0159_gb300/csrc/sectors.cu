@@ -23,6 +23,7 @@
 #include <map>
 
 #include "common.h"
+#include "ff.cuh"
 #include "grouped.h"
 
 namespace dmrg2d {
@@ -126,12 +127,14 @@ struct SecState {
 };
 
 // ---- kernels ------------------------------------------------------------------------------
-template <typename T>
+// T: storage type of v, y and the operators; Tc: compute type (T, or float pairs ff for
+// FP64X with double storage)
+template <typename T, typename Tc>
 __global__ void __launch_bounds__(256)
 hv_simt_sec_kernel(const T* __restrict__ v, T* __restrict__ y, const T* __restrict__ Lsub,
                    const T* __restrict__ Rsub, SecParams p) {
-  __shared__ T As[SBK][SBM];
-  __shared__ T Bs[SBK][SBN];
+  __shared__ Tc As[SBK][SBM];
+  __shared__ Tc Bs[SBK][SBN];
   const TileD t = p.tiles[blockIdx.x];
   const RowSegD rs = p.rseg[t.rs];
   const ColSegD cs = p.cseg[t.cs];
@@ -140,15 +143,16 @@ hv_simt_sec_kernel(const T* __restrict__ v, T* __restrict__ y, const T* __restri
   const int rows = min(SBM, rs.dim - t.r_in), cols = min(SBN, cs.dim - t.c_in);
   const int r0 = rs.off + t.r_in, c0 = cs.off + t.c_in;
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  T acc[4][4];
+  const Tc zero = c_zero<Tc>();
+  Tc acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+    for (int b = 0; b < 4; ++b) acc[a][b] = zero;
   auto mma = [&]() {
 #pragma unroll
     for (int k = 0; k < SBK; ++k) {
-      T av[4], bv[4];
+      Tc av[4], bv[4];
 #pragma unroll
       for (int a = 0; a < 4; ++a) av[a] = As[k][tx + 16 * a];
 #pragma unroll
@@ -156,7 +160,7 @@ hv_simt_sec_kernel(const T* __restrict__ v, T* __restrict__ y, const T* __restri
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+        for (int b = 0; b < 4; ++b) c_mac(acc[a][b], av[a], bv[b]);
     }
   };
   // phase 1: H_l restricted
@@ -169,8 +173,8 @@ hv_simt_sec_kernel(const T* __restrict__ v, T* __restrict__ y, const T* __restri
       for (int r = 0; r < 4; ++r) {
         const int kk = tid % SBK, i = tid / SBK + 16 * r;
         const int gk = k0 + kk;
-        As[kk][i] = (i < rows && gk < k.kdim) ? A[(long long)i * k.kdim + gk] : T(0);
-        Bs[kk][i] = (i < cols && gk < k.kdim) ? B[gk + ld * i] : T(0);
+        As[kk][i] = (i < rows && gk < k.kdim) ? c_in<Tc>(A[(long long)i * k.kdim + gk]) : zero;
+        Bs[kk][i] = (i < cols && gk < k.kdim) ? c_in<Tc>(B[gk + ld * i]) : zero;
       }
       __syncthreads();
       mma();
@@ -187,10 +191,10 @@ hv_simt_sec_kernel(const T* __restrict__ v, T* __restrict__ y, const T* __restri
       for (int r = 0; r < 4; ++r) {
         const int i = tid % SBM, kk = tid / SBM + 4 * r;
         const int gk = k0 + kk;
-        As[kk][i] = (i < rows && gk < k.kdim) ? A[i + ld * gk] : T(0);
+        As[kk][i] = (i < rows && gk < k.kdim) ? c_in<Tc>(A[i + ld * gk]) : zero;
         const int kb = tid % SBK, j = tid / SBK + 16 * r;
         const int gkb = k0 + kb;
-        Bs[kb][j] = (j < cols && gkb < k.kdim) ? B[(long long)j * k.kdim + gkb] : T(0);
+        Bs[kb][j] = (j < cols && gkb < k.kdim) ? c_in<Tc>(B[(long long)j * k.kdim + gkb]) : zero;
       }
       __syncthreads();
       mma();
@@ -203,7 +207,7 @@ hv_simt_sec_kernel(const T* __restrict__ v, T* __restrict__ y, const T* __restri
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int i = tx + 16 * a, j = ty + 16 * b;
-      if (i < rows && j < cols) Y[i + ld * j] = acc[a][b];
+      if (i < rows && j < cols) Y[i + ld * j] = c_out(acc[a][b]);
     }
   // zero padding rows of the segment (last row tile of the segment only)
   if (t.r_in + SBM >= rs.dim) {
@@ -552,17 +556,23 @@ int sec_apply(const dmrg2d_ops* ops, const void* v, void* y, int precision, cuda
   const SecParams p = S->params();
   const int nt = (int)S->tiles.size(), nm = (int)S->mitems.size();
   // timed kernel: the CUDA-core kernel here; the grouped tensor-core launch times itself
-  const bool simt = precision == DMRG2D_FP64 || precision == DMRG2D_FP32;
+  const bool simt =
+      precision == DMRG2D_FP64 || precision == DMRG2D_FP32 || precision == DMRG2D_FP64X;
   auto ev = simt ? prof_slot(ops) : std::pair<cudaEvent_t, cudaEvent_t>(nullptr, nullptr);
   if (ev.first) D2_CUDA(cudaEventRecord(ev.first, s));
-  if (precision == DMRG2D_FP64) {
-    if (nt) hv_simt_sec_kernel<double><<<nt, 256, 0, s>>>((const double*)v, (double*)y, S->d_L64,
+  if (precision == DMRG2D_FP64 || precision == DMRG2D_FP64X) {
+    // FP64X: the sub-block products in float pairs, the scalar moves in FP64
+    if (nt && precision == DMRG2D_FP64)
+      hv_simt_sec_kernel<double, double><<<nt, 256, 0, s>>>((const double*)v, (double*)y,
+                                                            S->d_L64, S->d_R64, p);
+    else if (nt)
+      hv_simt_sec_kernel<double, ff><<<nt, 256, 0, s>>>((const double*)v, (double*)y, S->d_L64,
                                                         S->d_R64, p);
     if (ev.second) D2_CUDA(cudaEventRecord(ev.second, s));
     if (nm) k_sec_moves<double, double><<<nm, 256, 0, s>>>((const double*)v, (double*)y, p, 1);
   } else if (precision == DMRG2D_FP32) {
-    if (nt) hv_simt_sec_kernel<float><<<nt, 256, 0, s>>>((const float*)v, (float*)y, S->d_L32,
-                                                       S->d_R32, p);
+    if (nt) hv_simt_sec_kernel<float, float><<<nt, 256, 0, s>>>((const float*)v, (float*)y,
+                                                              S->d_L32, S->d_R32, p);
     if (ev.second) D2_CUDA(cudaEventRecord(ev.second, s));
     if (nm) k_sec_moves<float, float><<<nm, 256, 0, s>>>((const float*)v, (float*)y, p, 0);
   } else if (precision == DMRG2D_BF16X3 && S->gp_ok && ops->tc_cfg[DMRG2D_BF16] == 2 * gp_num_configs()) {

@@ -1630,8 +1630,6 @@ extern "C" int dmrg2d_lanczos_ground(const dmrg2d_ops* ops, const dmrg2d_solver_
     return set_error(DMRG2D_EUNSUPPORTED, "tensor-core path unsupported for these shapes");
   if (o.refine_precision != DMRG2D_FP64 && o.refine_precision != DMRG2D_FP64X)
     return set_error(DMRG2D_EINVAL, "refine_precision must be FP64 or FP64X");
-  if (o.refine_precision == DMRG2D_FP64X && ops->sec)
-    return set_error(DMRG2D_EUNSUPPORTED, "FP64X refinement: dense superblocks only");
   const auto t0 = std::chrono::steady_clock::now();
   dmrg2d_solver_stats local{};
   Ctx C;

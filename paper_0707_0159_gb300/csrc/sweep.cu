@@ -170,6 +170,36 @@ __global__ void k_set_ones(double* __restrict__ U, const int64_t* __restrict__ p
     U[pos[i]] = 1.0;
 }
 
+// G[r + nr c] = X[idx[r] + ldx c] (0 where idx[r] < 0): rows of X picked by an index list
+__global__ void k_gather_idx(const double* __restrict__ X, int64_t ldx,
+                             const int64_t* __restrict__ idx, int nr, int nc,
+                             double* __restrict__ G) {
+  const int64_t total = (int64_t)nr * nc;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(i % nr), c = (int)(i / nr);
+    const int64_t row = idx[r];
+    G[i] = row >= 0 ? X[row + ldx * c] : 0.0;
+  }
+}
+
+// by_rows: Y[idx[r] + ldy c] = G[r + nr c]; else Y[r + ldy idx[c]] = G[r + nr c]
+// (entries whose index is negative are skipped)
+__global__ void k_scatter_idx(const double* __restrict__ G, int nr, int nc,
+                              const int64_t* __restrict__ idx, int by_rows,
+                              double* __restrict__ Y, int64_t ldy) {
+  const int64_t total = (int64_t)nr * nc;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(i % nr), c = (int)(i / nr);
+    if (by_rows) {
+      if (idx[r] >= 0) Y[idx[r] + ldy * c] = G[i];
+    } else if (idx[c] >= 0) {
+      Y[r + ldy * idx[c]] = G[i];
+    }
+  }
+}
+
 // xorshift64* stream for the start vectors (values in (-1, 1))
 struct Rng {
   uint64_t s;
@@ -312,18 +342,18 @@ class Sweeper {
       for (int l = half; l < L - 3; ++l) {  // to the right end
         D2_TRY(step(left_[l], right_[L - 2 - l], true, m, l, sw, &left_[l + 1], guess.get()));
         guess.reset();
-        D2_TRY(move_right(left_[l + 1], right_[L - 2 - l], &guess));
+        D2_TRY(timed_move(true, left_[l + 1], right_[L - 2 - l], &guess));
       }
       for (int r = 1; r < L - 3; ++r) {  // to the left end
         const int l = L - 2 - r;
         D2_TRY(step(left_[l], right_[r], false, m, l, sw, &right_[r + 1], guess.get()));
         guess.reset();
-        D2_TRY(move_left(right_[r + 1], left_[l], &guess));
+        D2_TRY(timed_move(false, right_[r + 1], left_[l], &guess));
       }
       for (int l = 1; l < half; ++l) {  // back to the middle
         D2_TRY(step(left_[l], right_[L - 2 - l], true, m, l, sw, &left_[l + 1], guess.get()));
         guess.reset();
-        D2_TRY(move_right(left_[l + 1], right_[L - 2 - l], &guess));
+        D2_TRY(timed_move(true, left_[l + 1], right_[L - 2 - l], &guess));
       }
       D2_TRY(step(left_[half], right_[half], true, m, half, sw, nullptr, guess.get()));
       guess = last_x_;  // the next sweep starts on this superblock
@@ -346,7 +376,7 @@ class Sweeper {
     rep_ = rep;
     strm_ = s;
     solve_seconds = build_seconds = dm_seconds = renorm_seconds = obs_seconds = 0.0;
-    train_seconds = 0.0;
+    train_seconds = transform_seconds = 0.0;
     if (libs_.bl) D2_BLAS(cublasSetStream(libs_.bl, strm_));
     if (libs_.sv) D2_SOLV(cusolverDnSetStream(libs_.sv, strm_));
     return DMRG2D_OK;
@@ -364,11 +394,21 @@ class Sweeper {
   }
 
   double solve_seconds = 0.0, build_seconds = 0.0, dm_seconds = 0.0, renorm_seconds = 0.0,
-         obs_seconds = 0.0, train_seconds = 0.0;
+         obs_seconds = 0.0, train_seconds = 0.0, transform_seconds = 0.0;
 
  private:
   static double since(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+
+  // The wavefunction transformation after a step (the next step's start vector), timed.
+  int timed_move(bool right, const Block& grown, const Block& other, std::shared_ptr<DBuf>* g) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const int st = right ? move_right(grown, other, g) : move_left(grown, other, g);
+    if (st == DMRG2D_OK && cudaStreamSynchronize(strm_) != cudaSuccess)
+      return set_error(DMRG2D_ECUDA, "sweep: wavefunction transformation");
+    transform_seconds += since(t0);
+    return st;
   }
 
   // HMED: the superblock ground state from the start vector x (overwritten).  Lanczos:
@@ -388,6 +428,7 @@ class Sweeper {
       if (mixed) {
         so.precision = o_.precision;
         so.refine = 1;
+        so.refine_precision = DMRG2D_FP64X;  // outer-loop residuals in float pairs
         so.inner_iter = std::min(o_.max_iter, 300);
         so.outer_max = 40;
       } else {
@@ -537,25 +578,41 @@ class Sweeper {
     return DMRG2D_OK;
   }
 
-  // Full eigendecomposition (ascending) of the symmetric n x n matrix A (lower) in place;
-  // eigenvalues to the host.
-  int eigh_all(double* A, int n, Mat* w_host) {
+  // The `top` largest eigenpairs (ascending) of the symmetric n x n matrix A (lower), in
+  // place: eigenvectors in A's first `top` columns, eigenvalues to the host.  dsyevd for
+  // the whole spectrum, dsyevdx selected by index otherwise.
+  int eigh_top(double* A, int n, int top, Mat* w_host) {
     DBuf w, work;
     D2_TRY(w.alloc((size_t)n));
-    int lwork = 0;
-    D2_SOLV(cusolverDnDsyevd_bufferSize(libs_.sv, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
-                                        n, A, n, w.p, &lwork));
+    int lwork = 0, meig = top;
+    const bool all = top >= n;
+    if (all)
+      D2_SOLV(cusolverDnDsyevd_bufferSize(libs_.sv, CUSOLVER_EIG_MODE_VECTOR,
+                                          CUBLAS_FILL_MODE_LOWER, n, A, n, w.p, &lwork));
+    else
+      D2_SOLV(cusolverDnDsyevdx_bufferSize(libs_.sv, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I,
+                                           CUBLAS_FILL_MODE_LOWER, n, A, n, 0.0, 0.0, n - top + 1,
+                                           n, &meig, w.p, &lwork));
     D2_TRY(work.alloc((size_t)std::max(lwork, 1)));
     IBuf info;
     D2_TRY(info.upload(std::vector<int>{0}, strm_));
-    D2_SOLV(cusolverDnDsyevd(libs_.sv, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, A, n,
-                             w.p, work.p, lwork, (int*)info.p));
+    if (all)
+      D2_SOLV(cusolverDnDsyevd(libs_.sv, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, A, n,
+                               w.p, work.p, lwork, (int*)info.p));
+    else
+      D2_SOLV(cusolverDnDsyevdx(libs_.sv, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I,
+                                CUBLAS_FILL_MODE_LOWER, n, A, n, 0.0, 0.0, n - top + 1, n, &meig,
+                                w.p, work.p, lwork, (int*)info.p));
     int hinfo = 0;
-    w_host->resize((size_t)n);
+    const int got = all ? n : top;
+    w_host->resize((size_t)got);
     D2_CUDA(cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, strm_));
-    D2_CUDA(cudaMemcpyAsync(w_host->data(), w.p, n * sizeof(double), cudaMemcpyDeviceToHost, strm_));
+    D2_CUDA(cudaMemcpyAsync(w_host->data(), w.p, got * sizeof(double), cudaMemcpyDeviceToHost,
+                            strm_));
     D2_CUDA(cudaStreamSynchronize(strm_));
-    if (hinfo != 0) return set_error(DMRG2D_ECUDA, "sweep: dsyevd info %d", hinfo);
+    if (hinfo != 0 || (!all && meig != top))
+      return set_error(DMRG2D_ECUDA, "sweep: dsyevd(x) info %d, %d of %d eigenpairs", hinfo, meig,
+                       top);
     return DMRG2D_OK;
   }
 
@@ -594,6 +651,29 @@ class Sweeper {
     for (int j = 0; j < k; ++j) *kept += hw[(size_t)j];
     k_take_leading<<<1024, 256, 0, strm_>>>(rho.p, n, k, U.p);
     D2_CUDA(cudaGetLastError());
+    return DMRG2D_OK;
+  }
+
+  // Labels as one integer ordered like the label, N_up (spins) or N_up * 4096 + N_dn
+  // (electrons): of block state i, of column state c, of a target
+  int blk_label(const std::vector<int32_t>& qn, int i) const {
+    return hub_ ? qn[2 * (size_t)i] * 4096 + qn[2 * (size_t)i + 1] : qn[(size_t)i];
+  }
+  int col_label(int c) const {
+    return hub_ ? hc_.nup[(size_t)c] * 4096 + hc_.ndn[(size_t)c] : __builtin_popcount((unsigned)c);
+  }
+  // [start, end) of every label among n states labelled qn (equal labels contiguous)
+  using Ranges = std::map<int, std::pair<int, int>>;
+  int label_ranges(const std::vector<int32_t>& qn, int n, Ranges* out) const {
+    out->clear();
+    for (int i = 0; i < n;) {
+      const int lab = blk_label(qn, i);
+      int j = i + 1;
+      while (j < n && blk_label(qn, j) == lab) ++j;
+      if (out->count(lab)) return set_error(DMRG2D_EINVAL, "sweep: block labels not grouped");
+      (*out)[lab] = {i, j};
+      i = j;
+    }
     return DMRG2D_OK;
   }
 
@@ -661,9 +741,10 @@ class Sweeper {
       }
       idx[q] = std::make_shared<IBuf>();
       D2_TRY(idx[q]->upload(dense, strm_));
+      // at most *kio states are kept from any one sector: its *kio largest eigenpairs
       Mat w;
-      D2_TRY(eigh_all(vecs[q]->p, dim[q], &w));
-      for (int j = 0; j < dim[q]; ++j) cand.push_back({w[(size_t)j], q, j});
+      D2_TRY(eigh_top(vecs[q]->p, dim[q], std::min(dim[q], *kio), &w));
+      for (int j = 0; j < (int)w.size(); ++j) cand.push_back({w[(size_t)j], q, j});
       r0 += qld[q];
       c0 += qcols[q];
     }
@@ -766,9 +847,10 @@ class Sweeper {
                   std::vector<double>* leg, std::vector<double>* rung, double* s2) {
     const int m1 = Lb.m, m4 = Rb.m, d = col_.d, nl = (int)col_.sz.size();
     const int64_t nL = (int64_t)m1 * d, nR = (int64_t)d * m4, nd = nL * nR;
-    DBuf T, T2;
-    D2_TRY(T.alloc((size_t)nd));
-    D2_TRY(T2.alloc((size_t)nd));
+    // two work vectors of the dense V's size, kept across steps (the largest so far)
+    if (obs_T_.n < (size_t)nd) D2_TRY(obs_T_.alloc((size_t)nd));
+    if (obs_T2_.n < (size_t)nd) D2_TRY(obs_T2_.alloc((size_t)nd));
+    DBuf &T = obs_T_, &T2 = obs_T2_;
     leg->assign(nl, 0.0);
     rung->assign(std::max(nl - 1, 0), 0.0);
     for (int y = 0; y < nl; ++y) {
@@ -856,25 +938,26 @@ class Sweeper {
     std::vector<long long> qbase;
     std::vector<int> qld, qcols;
     std::vector<int64_t> rowL, colR;
-    IBuf d_rowL, d_colR;
+    auto d_rowL = std::make_shared<IBuf>(), d_colR = std::make_shared<IBuf>();
     if (sec) {
       D2_TRY(sec_layout(ops, qbase, qld, qcols, rowL, colR));
-      D2_TRY(d_rowL.upload(rowL, strm_));
-      D2_TRY(d_colR.upload(colR, strm_));
+      D2_TRY(d_rowL->upload(rowL, strm_));
+      D2_TRY(d_colR->upload(colR, strm_));
     }
     auto pack = [&](double* Vd, double* xpk, int to_packed) -> int {
       int64_t r0 = 0, c0 = 0;
       for (size_t q = 0; q < qld.size(); ++q) {
         k_pack<<<512, 256, 0, strm_>>>(Vd, nL, xpk + qbase[q], qld[q], qcols[q],
-                                       (const int64_t*)d_rowL.p + r0, (const int64_t*)d_colR.p + c0,
-                                       to_packed);
+                                       (const int64_t*)d_rowL->p + r0,
+                                       (const int64_t*)d_colR->p + c0, to_packed);
         r0 += qld[q];
         c0 += qcols[q];
       }
       D2_CUDA(cudaGetLastError());
       return DMRG2D_OK;
     };
-    DBuf x;
+    auto xs = std::make_shared<DBuf>();
+    DBuf& x = *xs;
     if (guess && guess->n == (size_t)nd) {  // the previous ground state, in this basis
       D2_TRY(x.alloc((size_t)nv));
       if (sec)
@@ -912,6 +995,27 @@ class Sweeper {
     }
     last_x_ = xd;
     last_nv_ = nd;
+    last_sec_.valid = sec;
+    if (sec) {
+      last_sec_.m1 = Lb.m;
+      last_sec_.m4 = Rb.m;
+      last_sec_.target = hub_ ? target[0] * 4096 + target[1] : target[0];
+      last_sec_.x = xs;
+      last_sec_.qbase = qbase;
+      last_sec_.qld = qld;
+      last_sec_.qcols = qcols;
+      last_sec_.qlab.assign(qld.size(), 0);
+      int64_t r0 = 0;
+      for (size_t q = 0; q < qld.size(); ++q) {
+        int r = 0;
+        while (r < qld[q] && rowL[r0 + r] < 0) ++r;
+        if (r == qld[q]) return set_error(DMRG2D_EINVAL, "sweep: empty sector matrix");
+        last_sec_.qlab[q] = enlarged_label(Lb, rowL[r0 + r]);
+        r0 += qld[q];
+      }
+      last_sec_.d_rowL = d_rowL;
+      last_sec_.d_colR = d_colR;
+    }
     double norm2 = 0.0;  // trace of rho = |x|^2
     D2_BLAS(cublasDdot(libs_.bl, (int)nv, x.p, 1, x.p, 1, &norm2));
     // ---- DMF + DMD: k leading eigenvectors of the growing half's density matrix ----------
@@ -1011,6 +1115,14 @@ class Sweeper {
       renorm_seconds += since(tr);
       return DMRG2D_OK;
     }
+    if (o_.use_sectors) {
+      D2_TRY(renorm_sectors(grow_left ? Lb : Rb, U, dHB, g, out));
+      out->m_prev = mb;
+      out->U = Up;
+      out->cols = (grow_left ? Lb.cols : Rb.cols) + 1;
+      renorm_seconds += since(tr);
+      return DMRG2D_OK;
+    }
     const double one = 1.0, zero = 0.0;
     DBuf HU, T;
     D2_TRY(HU.alloc((size_t)(n * k)));
@@ -1072,6 +1184,105 @@ class Sweeper {
       D2_TRY(project(T.p, pass ? &out->Sp_tot : &out->Sz_tot, pass == 0));
     }
     renorm_seconds += since(tr);
+    return DMRG2D_OK;
+  }
+
+  // Renormalisation of a spin block in sectors.  U (n x k) is zero outside each kept
+  // state's sector: column j (label q) lives on the rows i + m c with label(i) = q - q(c),
+  // a contiguous range of the block's states for every column state c.  A block operator
+  // that shifts block labels by dY then maps those rows onto the range of q - q(c) + dY:
+  // (1 (x) Y) U is one GEMM per column state and kept label (out zero elsewhere).  A
+  // projection U^T (X U) with X shifting labels by dX has only the blocks (q + dX, q),
+  // one GEMM each over the n rows.  Same operators and order as the dense renormalisation.
+  int kron_blk_sec(const double* Y, bool tY, int dY, const double* W, double* out, int m, int k,
+                   const Ranges& rb, const Ranges& rk) {
+    const int d = col_.d;
+    const int64_t n = (int64_t)m * d;
+    const double one = 1.0, zero = 0.0;
+    D2_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * n * k, strm_));
+    for (int c = 0; c < d; ++c)
+      for (const auto& kq : rk) {
+        const int a = kq.first - col_label(c);
+        auto ia = rb.find(a), ib = rb.find(a + dY);
+        if (ia == rb.end() || ib == rb.end()) continue;
+        const int s0 = ia->second.first, ms = ia->second.second - s0;
+        const int r0 = ib->second.first, mr = ib->second.second - r0;
+        const int j0 = kq.second.first, nk = kq.second.second - j0;
+        // Y row-major: Y[r][s] is the column-major (s, r) entry
+        const double* A = tY ? Y + r0 + (int64_t)m * s0 : Y + s0 + (int64_t)m * r0;
+        D2_BLAS(cublasDgemm(libs_.bl, tY ? CUBLAS_OP_N : CUBLAS_OP_T, CUBLAS_OP_N, mr, nk, ms,
+                            &one, A, m, W + s0 + (int64_t)m * c + n * j0, (int)n, &zero,
+                            out + r0 + (int64_t)m * c + n * j0, (int)n));
+      }
+    return DMRG2D_OK;
+  }
+  int project_sec(const double* U, const double* XU, int dX, int64_t n, int k, const Ranges& rk,
+                  Mat* dst, bool symmetrise) {
+    const double one = 1.0, zero = 0.0;
+    DBuf small;
+    D2_TRY(small.alloc((size_t)k * k));
+    D2_CUDA(cudaMemsetAsync(small.p, 0, sizeof(double) * k * k, strm_));
+    for (const auto& kq : rk) {
+      auto it = rk.find(kq.first + dX);
+      if (it == rk.end()) continue;
+      const int j0 = kq.second.first, nj = kq.second.second - j0;
+      const int i0 = it->second.first, ni = it->second.second - i0;
+      D2_BLAS(cublasDgemm(libs_.bl, CUBLAS_OP_T, CUBLAS_OP_N, ni, nj, (int)n, &one, U + n * i0,
+                          (int)n, XU + n * j0, (int)n, &zero, small.p + i0 + (int64_t)k * j0, k));
+    }
+    Mat hs((size_t)k * k);
+    D2_CUDA(cudaMemcpyAsync(hs.data(), small.p, (size_t)k * k * sizeof(double),
+                            cudaMemcpyDeviceToHost, strm_));
+    D2_CUDA(cudaStreamSynchronize(strm_));
+    dst->assign((size_t)k * k, 0.0);
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) {
+        const double a = hs[(size_t)i + (size_t)j * k];
+        (*dst)[(size_t)i * k + j] = symmetrise ? 0.5 * (a + hs[(size_t)j + (size_t)i * k]) : a;
+      }
+    return DMRG2D_OK;
+  }
+  int renorm_sectors(const Block& B, DBuf& U, DBuf& dHB, const Grown& g, Block* out) {
+    const int mb = g.mb, k = g.k;
+    const int64_t n = g.n;
+    Ranges rb, rk;
+    D2_TRY(label_ranges(B.qn, mb, &rb));
+    D2_TRY(label_ranges(g.labels, k, &rk));
+    DBuf HU, T;
+    D2_TRY(HU.alloc((size_t)(n * k)));
+    D2_TRY(T.alloc((size_t)(n * k)));
+    // H_enl U as in the dense renormalisation: S+ raises N_up by one, S- lowers it
+    D2_TRY(kron_blk_sec(dHB.p, false, 0, U.p, HU.p, mb, k, rb, rk));
+    D2_TRY(kron_col(dH_col_.p, false, U.p, HU.p, mb, k, 1.0, 1.0));
+    const double J = M_.J_leg;
+    for (size_t y = 0; y < col_.sz.size(); ++y) {
+      DBuf dz, dp;
+      D2_TRY(dz.upload(B.edge[2 * y], strm_));
+      D2_TRY(dp.upload(B.edge[2 * y + 1], strm_));
+      D2_TRY(kron_blk_sec(dz.p, false, 0, U.p, T.p, mb, k, rb, rk));
+      D2_TRY(kron_col(dsz_[y].p, false, T.p, HU.p, mb, k, J, 1.0));
+      D2_TRY(kron_blk_sec(dp.p, false, 1, U.p, T.p, mb, k, rb, rk));
+      D2_TRY(kron_col(dsp_[y].p, true, T.p, HU.p, mb, k, 0.5 * J, 1.0));
+      D2_TRY(kron_blk_sec(dp.p, true, -1, U.p, T.p, mb, k, rb, rk));
+      D2_TRY(kron_col(dsp_[y].p, false, T.p, HU.p, mb, k, 0.5 * J, 1.0));
+    }
+    out->m = k;
+    out->qn = g.labels;
+    D2_TRY(project_sec(U.p, HU.p, 0, n, k, rk, &out->H, true));
+    out->edge.assign(2 * col_.sz.size(), Mat());
+    for (size_t y = 0; y < col_.sz.size(); ++y) {
+      D2_TRY(kron_col(dsz_[y].p, false, U.p, T.p, mb, k, 1.0, 0.0));
+      D2_TRY(project_sec(U.p, T.p, 0, n, k, rk, &out->edge[2 * y], false));
+      D2_TRY(kron_col(dsp_[y].p, false, U.p, T.p, mb, k, 1.0, 0.0));
+      D2_TRY(project_sec(U.p, T.p, 1, n, k, rk, &out->edge[2 * y + 1], false));
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+      DBuf dB;
+      D2_TRY(dB.upload(pass ? B.Sp_tot : B.Sz_tot, strm_));
+      D2_TRY(kron_blk_sec(dB.p, false, pass, U.p, T.p, mb, k, rb, rk));
+      D2_TRY(kron_col(pass ? dSp_tot_.p : dSz_tot_.p, false, U.p, T.p, mb, k, 1.0, 1.0));
+      D2_TRY(project_sec(U.p, T.p, pass, n, k, rk, pass ? &out->Sp_tot : &out->Sz_tot, pass == 0));
+    }
     return DMRG2D_OK;
   }
 
@@ -1192,6 +1403,17 @@ class Sweeper {
   std::vector<DBuf> drung_;
   std::shared_ptr<DBuf> last_x_;  // ground state of the last step's superblock
   int64_t last_nv_ = 0;
+  // the last step's sector-restricted ground state: packed vector, its layout (the rows
+  // and columns of each V_q in the dense V), the enlarged-left label of each V_q, the
+  // target label and the block sizes
+  struct LastSectors {
+    bool valid = false;
+    int m1 = 0, m4 = 0, target = 0;
+    std::shared_ptr<DBuf> x;
+    std::vector<long long> qbase;
+    std::vector<int> qld, qcols, qlab;
+    std::shared_ptr<IBuf> d_rowL, d_colR;
+  } last_sec_;
 
   // Guess for the superblock after moving right: block 1 grew into nl (its U: (m_l d) x k),
   // block 4 = Rs of m_r states (made from a block of m' states plus a column, Rs.U:
@@ -1201,6 +1423,8 @@ class Sweeper {
     const int d = col_.d, k = nl.m, ml = nl.m_prev, mr = Rs.m, mp = Rs.m_prev;
     const int64_t nL = (int64_t)ml * d, nR = (int64_t)d * mr;
     if (!nl.U || !Rs.U || last_nv_ != nL * nR) return DMRG2D_OK;  // no guess
+    if (last_sec_.valid && last_sec_.m1 == ml && last_sec_.m4 == mr)
+      return move_right_sectors(nl, Rs, out);
     DBuf W;
     D2_TRY(W.alloc((size_t)k * nR));
     auto v = std::make_shared<DBuf>();
@@ -1221,6 +1445,8 @@ class Sweeper {
     const int d = col_.d, k = nr.m, mr = nr.m_prev, ml = Ls.m, mp = Ls.m_prev;
     const int64_t nL = (int64_t)ml * d, nR = (int64_t)d * mr;
     if (!nr.U || !Ls.U || last_nv_ != nL * nR) return DMRG2D_OK;
+    if (last_sec_.valid && last_sec_.m1 == ml && last_sec_.m4 == mr)
+      return move_left_sectors(nr, Ls, out);
     DBuf W;
     D2_TRY(W.alloc((size_t)nL * k));
     auto v = std::make_shared<DBuf>();
@@ -1231,6 +1457,129 @@ class Sweeper {
     D2_BLAS(cublasDgemmStridedBatched(libs_.bl, CUBLAS_OP_N, CUBLAS_OP_N, mp * d, k, ml, &one,
                                       Ls.U->p, mp * d, 0, W.p, (int)nL, (long long)ml, &zero, v->p,
                                       mp * d, (long long)mp * d * k, d));
+    *out = v;
+    return DMRG2D_OK;
+  }
+
+  // The same two transformations on a sector-restricted ground state, label by label.
+  // W = U^T V from the packed matrices V_q: the kept states of label qL (a contiguous range
+  // of U's columns) see only V_q of that enlarged-left label, W_q = U_q^T V_q with U_q the
+  // rows of U at V_q's rows (0 on padding).  Then, per split-off column i3 and label p of
+  // block 4 (a contiguous range of its states), the kept states of label
+  // target - q(i3) - p take the product with the range's columns of Rs.U.  Everything
+  // else of W and of the new V is zero.
+  int move_right_sectors(const Block& nl, const Block& Rs, std::shared_ptr<DBuf>* out) {
+    const int d = col_.d, k = nl.m, ml = nl.m_prev, mr = Rs.m, mp = Rs.m_prev;
+    const int64_t nL = (int64_t)ml * d, nR = (int64_t)d * mr;
+    const LastSectors& ls = last_sec_;
+    Ranges rk, r4;
+    D2_TRY(label_ranges(nl.qn, k, &rk));
+    D2_TRY(label_ranges(Rs.qn, mr, &r4));
+    const double one = 1.0, zero = 0.0;
+    DBuf W, G, Wq;
+    D2_TRY(W.alloc((size_t)k * nR));
+    D2_CUDA(cudaMemsetAsync(W.p, 0, sizeof(double) * k * nR, strm_));
+    size_t gmax = 0, wmax = 0;
+    for (size_t q = 0; q < ls.qld.size(); ++q) {
+      auto it = rk.find(ls.qlab[q]);
+      if (it == rk.end()) continue;
+      const size_t kq = it->second.second - it->second.first;
+      gmax = std::max(gmax, (size_t)ls.qld[q] * kq);
+      wmax = std::max(wmax, kq * ls.qcols[q]);
+    }
+    D2_TRY(G.alloc(std::max<size_t>(gmax, 1)));
+    D2_TRY(Wq.alloc(std::max<size_t>(wmax, 1)));
+    int64_t r0 = 0, c0 = 0;
+    for (size_t q = 0; q < ls.qld.size(); ++q) {
+      const int ld = ls.qld[q], nc = ls.qcols[q];
+      auto it = rk.find(ls.qlab[q]);
+      if (it != rk.end()) {
+        const int j0 = it->second.first, kq = it->second.second - j0;
+        k_gather_idx<<<512, 256, 0, strm_>>>(nl.U->p + nL * j0, nL,
+                                             (const int64_t*)ls.d_rowL->p + r0, ld, kq, G.p);
+        D2_BLAS(cublasDgemm(libs_.bl, CUBLAS_OP_T, CUBLAS_OP_N, kq, nc, ld, &one, G.p, ld,
+                            ls.x->p + ls.qbase[q], ld, &zero, Wq.p, kq));
+        k_scatter_idx<<<512, 256, 0, strm_>>>(Wq.p, kq, nc, (const int64_t*)ls.d_colR->p + c0, 0,
+                                              W.p + j0, k);
+        D2_CUDA(cudaGetLastError());
+      }
+      r0 += ld;
+      c0 += nc;
+    }
+    auto v = std::make_shared<DBuf>();
+    const int64_t nv = (int64_t)k * d * d * mp;
+    D2_TRY(v->alloc((size_t)nv));
+    D2_CUDA(cudaMemsetAsync(v->p, 0, sizeof(double) * nv, strm_));
+    for (int i3 = 0; i3 < d; ++i3)
+      for (const auto& pr : r4) {
+        auto it = rk.find(ls.target - col_label(i3) - pr.first);
+        if (it == rk.end()) continue;
+        const int b0 = it->second.first, kq = it->second.second - b0;
+        const int a0 = pr.second.first, np = pr.second.second - a0;
+        D2_BLAS(cublasDgemm(libs_.bl, CUBLAS_OP_N, CUBLAS_OP_T, kq, mp * d, np, &one,
+                            W.p + b0 + (int64_t)k * (a0 + (int64_t)mr * i3), k,
+                            Rs.U->p + (int64_t)mp * d * a0, mp * d, &zero,
+                            v->p + b0 + (int64_t)k * i3, k * d));
+      }
+    *out = v;
+    return DMRG2D_OK;
+  }
+  // W = V U from the packed matrices: the kept states of label target - qL see only V_q,
+  // W_q = V_q U_q with U_q the rows of U at V_q's columns; per split-off column s2 and
+  // label p of block 1, the kept states of label target - p - q(s2) take Ls.U's range.
+  int move_left_sectors(const Block& nr, const Block& Ls, std::shared_ptr<DBuf>* out) {
+    const int d = col_.d, k = nr.m, mr = nr.m_prev, ml = Ls.m, mp = Ls.m_prev;
+    const int64_t nL = (int64_t)ml * d, nR = (int64_t)d * mr;
+    const LastSectors& ls = last_sec_;
+    Ranges rk, r1;
+    D2_TRY(label_ranges(nr.qn, k, &rk));
+    D2_TRY(label_ranges(Ls.qn, ml, &r1));
+    const double one = 1.0, zero = 0.0;
+    DBuf W, G, Wq;
+    D2_TRY(W.alloc((size_t)nL * k));
+    D2_CUDA(cudaMemsetAsync(W.p, 0, sizeof(double) * nL * k, strm_));
+    size_t gmax = 0, wmax = 0;
+    for (size_t q = 0; q < ls.qld.size(); ++q) {
+      auto it = rk.find(ls.target - ls.qlab[q]);
+      if (it == rk.end()) continue;
+      const size_t kq = it->second.second - it->second.first;
+      gmax = std::max(gmax, (size_t)ls.qcols[q] * kq);
+      wmax = std::max(wmax, (size_t)ls.qld[q] * kq);
+    }
+    D2_TRY(G.alloc(std::max<size_t>(gmax, 1)));
+    D2_TRY(Wq.alloc(std::max<size_t>(wmax, 1)));
+    int64_t r0 = 0, c0 = 0;
+    for (size_t q = 0; q < ls.qld.size(); ++q) {
+      const int ld = ls.qld[q], nc = ls.qcols[q];
+      auto it = rk.find(ls.target - ls.qlab[q]);
+      if (it != rk.end()) {
+        const int j0 = it->second.first, kq = it->second.second - j0;
+        k_gather_idx<<<512, 256, 0, strm_>>>(nr.U->p + nR * j0, nR,
+                                             (const int64_t*)ls.d_colR->p + c0, nc, kq, G.p);
+        D2_BLAS(cublasDgemm(libs_.bl, CUBLAS_OP_N, CUBLAS_OP_N, ld, kq, nc, &one,
+                            ls.x->p + ls.qbase[q], ld, G.p, nc, &zero, Wq.p, ld));
+        k_scatter_idx<<<512, 256, 0, strm_>>>(Wq.p, ld, kq, (const int64_t*)ls.d_rowL->p + r0, 1,
+                                              W.p + nL * j0, nL);
+        D2_CUDA(cudaGetLastError());
+      }
+      r0 += ld;
+      c0 += nc;
+    }
+    auto v = std::make_shared<DBuf>();
+    const int64_t nv = (int64_t)mp * d * d * k;
+    D2_TRY(v->alloc((size_t)nv));
+    D2_CUDA(cudaMemsetAsync(v->p, 0, sizeof(double) * nv, strm_));
+    for (int s2 = 0; s2 < d; ++s2)
+      for (const auto& pr : r1) {
+        auto it = rk.find(ls.target - pr.first - col_label(s2));
+        if (it == rk.end()) continue;
+        const int b0 = it->second.first, kq = it->second.second - b0;
+        const int a0 = pr.second.first, np = pr.second.second - a0;
+        D2_BLAS(cublasDgemm(libs_.bl, CUBLAS_OP_N, CUBLAS_OP_N, mp * d, kq, np, &one,
+                            Ls.U->p + (int64_t)mp * d * a0, mp * d,
+                            W.p + a0 + (int64_t)ml * s2 + nL * b0, (int)nL, &zero,
+                            v->p + (int64_t)mp * d * (b0 + (int64_t)k * s2), mp * d));
+      }
     *out = v;
     return DMRG2D_OK;
   }
@@ -1246,6 +1595,7 @@ class Sweeper {
   cudaStream_t strm_;
   Rng rng_;
   Rng train_rng_;  // sample positions of the learned preconditioner's training batches
+  DBuf obs_T_, obs_T2_;  // work vectors of the observables
   SpinColumnOps col_;
   Libs libs_;
   DBuf dH_col_;
@@ -1369,7 +1719,7 @@ extern "C" int dmrg2d_sweep(dmrg2d_state* state, const dmrg2d_sweep_opts* opts,
   report->n_steps = 0;
   report->seconds = report->solve_seconds = report->build_seconds = 0.0;
   report->dm_seconds = report->renorm_seconds = report->obs_seconds = 0.0;
-  report->train_seconds = 0.0;
+  report->train_seconds = report->transform_seconds = 0.0;
   const auto t0 = std::chrono::steady_clock::now();
   int st = sw.begin_call(opts, report, (cudaStream_t)stream);
   if (st == DMRG2D_OK && !state->ready) {
@@ -1386,5 +1736,6 @@ extern "C" int dmrg2d_sweep(dmrg2d_state* state, const dmrg2d_sweep_opts* opts,
   report->renorm_seconds = sw.renorm_seconds;
   report->obs_seconds = sw.obs_seconds;
   report->train_seconds = sw.train_seconds;
+  report->transform_seconds = sw.transform_seconds;
   return st;
 }

@@ -58,7 +58,8 @@ class SweepReport(C.Structure):
                 ("seconds", C.c_double),
                 ("solve_seconds", C.c_double), ("build_seconds", C.c_double),
                 ("dm_seconds", C.c_double), ("renorm_seconds", C.c_double),
-                ("obs_seconds", C.c_double), ("train_seconds", C.c_double)]
+                ("obs_seconds", C.c_double), ("train_seconds", C.c_double),
+                ("transform_seconds", C.c_double)]
 
 
 class StateInfo(C.Structure):
@@ -591,7 +592,7 @@ class SweepState:
         nd = 8 * nl + 2
         dens = (C.c_double * (cap * nd))()
         rep = SweepReport(cap, 0, e, t, ll, sw, it, leg, rung, s2, dens, 0.0, 0.0, 0.0, 0.0, 0.0,
-                          0.0, 0.0)
+                          0.0, 0.0, 0.0)
         _check(lib().dmrg2d_sweep(self._p, C.byref(opts), C.byref(rep), _stream(stream)))
         n = min(rep.n_steps, cap)
         return {"energy": list(e[:n]), "trunc": list(t[:n]), "l": list(ll[:n]),
@@ -602,7 +603,8 @@ class SweepState:
                 "n_steps": rep.n_steps, "seconds": rep.seconds,
                 "solve_seconds": rep.solve_seconds, "build_seconds": rep.build_seconds,
                 "dm_seconds": rep.dm_seconds, "renorm_seconds": rep.renorm_seconds,
-                "train_seconds": rep.train_seconds, **_sweep_densities(dens, n, nl)}
+                "train_seconds": rep.train_seconds, "transform_seconds": rep.transform_seconds,
+                **_sweep_densities(dens, n, nl)}
 
     def info(self) -> dict:
         inf = StateInfo()

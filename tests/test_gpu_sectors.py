@@ -94,7 +94,8 @@ def test_layout_matches_documented_rule(sector_case):
     assert np.array_equal(lib_map, pmap)
 
 
-@pytest.mark.parametrize("prec,tol", [(dmrg2d.FP64, 1e-12), (dmrg2d.FP32, 1e-5)])
+@pytest.mark.parametrize("prec,tol", [(dmrg2d.FP64, 1e-12), (dmrg2d.FP64X, 1e-12),
+                                      (dmrg2d.FP32, 1e-5)])
 def test_sector_hv_matches_oracle(sector_case, prec, tol):
     name, mdl, left, right, target, sb, ops, pmap = sector_case
     valid = pmap >= 0
@@ -104,7 +105,7 @@ def test_sector_hv_matches_oracle(sector_case, prec, tol):
     yd = sb.apply(vd)
     ref = np.zeros(len(pmap))
     ref[valid] = yd[pmap[valid]]
-    dt = torch.float64 if prec == dmrg2d.FP64 else torch.float32
+    dt = torch.float64 if prec in (dmrg2d.FP64, dmrg2d.FP64X) else torch.float32
     x = torch.from_numpy(vp).to("cuda", dt)
     y = torch.full((len(pmap),), 7.0, dtype=dt, device="cuda")   # padding must be overwritten
     dmrg2d.apply_H(ops, x, y, prec)
@@ -170,3 +171,23 @@ def test_tiny_sector_lanczos_matches_oracle():
     vd[pmap[valid]] = vp[valid]
     e_ref, _, info = oracle_lanczos(sb.apply, vd, max_iter=300, tol=1e-11)
     assert abs(e - e_ref) <= 1e-9 * abs(e_ref), (e, e_ref)
+
+
+def test_sector_mixed_solver_with_float_pair_refinement(sector_case):
+    """The mixed solver on a sector superblock with its outer-loop H·v in float pairs
+    (FP64X) reaches the plain FP64 Lanczos energy from the same start vector."""
+    name, mdl, left, right, target, sb, ops, pmap = sector_case
+    valid = pmap >= 0
+    vp = np.where(valid, synth.start_vector(len(pmap), 8), 0.0)
+    x64 = torch.from_numpy(vp).cuda()
+    e64, st64, c64 = dmrg2d.lanczos_ground(ops, x64, max_iter=800, krylov_dim=300, tol=1e-11)
+    assert c64 == 0, st64
+    low = dmrg2d.TF32 if ops.info["tc_ok"] else dmrg2d.FP32
+    x = torch.from_numpy(vp).cuda()
+    e, st, code = dmrg2d.lanczos_ground(ops, x, precision=low, refine=1, tol=1e-9,
+                                        inner_iter=60, outer_max=40,
+                                        refine_precision=dmrg2d.FP64X)
+    assert code == 0, st
+    assert st["n_hv_fp64"] > 0
+    assert abs(e - e64) <= 1e-9 * abs(e64), (e, e64)
+    assert np.all(x.cpu().numpy()[~valid] == 0.0)

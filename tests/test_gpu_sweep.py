@@ -37,13 +37,21 @@ def test_untruncated_sweep_equals_ed():
     assert max(out["trunc"]) <= 1e-12
 
 
-def test_wavefunction_transformation_gives_the_next_ground_state():
+@pytest.mark.parametrize("kind", ["dense", "sectors", "hubbard"])
+def test_wavefunction_transformation_gives_the_next_ground_state(kind):
     """Without truncation the previous ground state, carried into the next superblock's
     basis, is that superblock's ground state: every finite step after the first (which
-    starts from a random vector) converges at the first convergence check."""
-    mdl = model(2)
-    out = dmrg2d.sweep(mdl, 6, m_warmup=64, m_sweeps=[64, 64], precision="fp64", tol=1e-10,
-                       max_iter=600)
+    starts from a random vector) converges at the first convergence check.  Dense
+    superblocks, the S^z_tot = 0 sector (the label-by-label transformation of the packed
+    state) and a Hubbard chain in its (N_up, N_dn) sector."""
+    kw = dict(precision="fp64", tol=1e-10, max_iter=600)
+    if kind == "hubbard":
+        mdl = synth.model("hubbard", 1, t=1.0, U=4.0)
+        kw.update(sectors=True, n_up=2, n_dn=2)
+    else:
+        mdl = model(2)
+        kw.update(sectors=kind == "sectors")
+    out = dmrg2d.sweep(mdl, 6, m_warmup=64, m_sweeps=[64, 64], **kw)
     sw = np.array(out["sweep"])
     it = np.array(out["iters"])[sw >= 0]
     assert it[0] > 10                      # seeded random start
