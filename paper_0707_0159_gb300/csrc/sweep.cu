@@ -19,6 +19,9 @@
 #include <cusolverDn.h>
 
 #include <algorithm>
+#include <array>
+#include <cstring>
+#include <tuple>
 #include <chrono>
 #include <cmath>
 #include <map>
@@ -200,6 +203,38 @@ __global__ void k_scatter_idx(const double* __restrict__ G, int nr, int nc,
   }
 }
 
+// One term of an expectation value on a packed vector: coef * <sub-block 1, sub-block 2>,
+// both rows x cols column-major (leading dimensions ld1, ld2) at offsets off1, off2
+struct DotItem {
+  long long off1, off2;
+  int ld1, ld2, rows, cols;
+  double coef;
+};
+// out[i] = value of item i (one CTA per item at a time, block reduction)
+__global__ void __launch_bounds__(256) k_item_dots(const double* __restrict__ x,
+                                                   const DotItem* __restrict__ items, int n,
+                                                   double* __restrict__ out) {
+  __shared__ double red[8];
+  for (int it = blockIdx.x; it < n; it += gridDim.x) {
+    const DotItem t = items[it];
+    const long long total = (long long)t.rows * t.cols;
+    double acc = 0.0;
+    for (long long i = threadIdx.x; i < total; i += 256) {
+      const long long r = i % t.rows, c = i / t.rows;
+      acc += x[t.off1 + r + t.ld1 * c] * x[t.off2 + r + t.ld2 * c];
+    }
+    for (int o = 16; o; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      double v = threadIdx.x < 8 ? red[threadIdx.x] : 0.0;
+      for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (threadIdx.x == 0) out[it] = t.coef * v;
+    }
+    __syncthreads();
+  }
+}
+
 // xorshift64* stream for the start vectors (values in (-1, 1))
 struct Rng {
   uint64_t s;
@@ -277,11 +312,13 @@ class Sweeper {
       return t;
     };
     drung_.resize(std::max(nl - 1, 0));
+    rung_h_.clear();
     for (int y = 0; y + 1 < nl; ++y) {
       Mat b = mm(col_.sz[y], col_.sz[y + 1]);
       const Mat pm = mm(col_.sp[y], tr(col_.sp[y + 1])), mp = mm(tr(col_.sp[y]), col_.sp[y + 1]);
       for (size_t e = 0; e < b.size(); ++e) b[e] += 0.5 * (pm[e] + mp[e]);
       D2_TRY(drung_[y].upload(b, strm_));
+      rung_h_.push_back(b);
     }
     dsz_.resize(col_.sz.size());
     dsp_.resize(col_.sp.size());
@@ -844,16 +881,19 @@ class Sweeper {
   // <S_(2,y) . S_(3,y)> (leg bonds between the central columns), <S_(2,y) . S_(2,y+1)>
   // (rung bonds of column 2) and, when with_s2, <S_tot^2> = |S+ x|^2 + |Sz x|^2 + <Sz>.
   int observables(const double* V, const Block& Lb, const Block& Rb, bool with_s2,
-                  std::vector<double>* leg, std::vector<double>* rung, double* s2) {
+                  std::vector<double>* leg, std::vector<double>* rung, double* s2,
+                  bool bonds = true) {
     const int m1 = Lb.m, m4 = Rb.m, d = col_.d, nl = (int)col_.sz.size();
     const int64_t nL = (int64_t)m1 * d, nR = (int64_t)d * m4, nd = nL * nR;
     // two work vectors of the dense V's size, kept across steps (the largest so far)
     if (obs_T_.n < (size_t)nd) D2_TRY(obs_T_.alloc((size_t)nd));
     if (obs_T2_.n < (size_t)nd) D2_TRY(obs_T2_.alloc((size_t)nd));
     DBuf &T = obs_T_, &T2 = obs_T2_;
-    leg->assign(nl, 0.0);
-    rung->assign(std::max(nl - 1, 0), 0.0);
-    for (int y = 0; y < nl; ++y) {
+    if (bonds) {
+      leg->assign(nl, 0.0);
+      rung->assign(std::max(nl - 1, 0), 0.0);
+    }
+    for (int y = 0; bonds && y < nl; ++y) {
       // (A (x) 1) V (B (x) 1)^T for (A, B) = (Sz, Sz), (S+, S-), (S-, S+) with weights 1, 1/2, 1/2
       const double* sz = dsz_[y].p;
       const double* sp = dsp_[y].p;
@@ -868,7 +908,7 @@ class Sweeper {
         (*leg)[y] += t.c * r;
       }
     }
-    for (int y = 0; y + 1 < nl; ++y) {
+    for (int y = 0; bonds && y + 1 < nl; ++y) {
       D2_TRY(kron_col(drung_[y].p, false, V, T.p, m1, (int)nR, 1.0, 0.0));
       D2_TRY(dotv(V, T.p, nd, &(*rung)[y]));
     }
@@ -896,6 +936,126 @@ class Sweeper {
         }
       }
       *s2 = a + b + c;
+    }
+    return DMRG2D_OK;
+  }
+
+  // The bond energies of observables() on the packed ground state of the last step.  A
+  // column operator A on i2 (and B on i3) moves the row segment (i2, block-1 sector a) of
+  // V_qL to (i2', a) of V_qL' and the column segment (i3, block-4 sector b) to (i3', b):
+  // <x|(A (x) B)|x> is a sum of coef * <sub-block, sub-block> over those segment pairs,
+  // coef = A[i2'][i2] B[i3'][i3] (B = 1 for the rung bonds of column 2).
+  int bonds_sectors(int m1, int m4, std::vector<double>* leg, std::vector<double>* rung) {
+    const LastSectors& ls = last_sec_;
+    const int d = col_.d, nl = (int)col_.sz.size(), nQ = (int)ls.qld.size();
+    struct Seg {
+      int q, off, len;
+    };
+    std::map<std::pair<int, int>, Seg> rseg;                 // (i2, first i1) -> row segment
+    std::map<std::tuple<int, int, int>, std::pair<int, int>> cseg;  // (q, i3, first i4)
+    std::vector<std::vector<std::array<int, 4>>> qcols(nQ);  // per q: (i3, i4, off, len)
+    std::vector<std::vector<std::array<int, 4>>> qrows(nQ);  // per q: (i2, i1, off, len)
+    int64_t r0 = 0, c0 = 0;
+    for (int q = 0; q < nQ; ++q) {
+      for (int r = 0; r < ls.qld[q];) {
+        const int64_t e = ls.rowL[r0 + r];
+        if (e < 0) {
+          ++r;
+          continue;
+        }
+        const int i2 = (int)(e / m1), i1 = (int)(e % m1);
+        int len = 1;
+        while (r + len < ls.qld[q] && ls.rowL[r0 + r + len] == e + len &&
+               (e + len) / m1 == i2)
+          ++len;
+        rseg[{i2, i1}] = {q, r, len};
+        qrows[q].push_back({i2, i1, r, len});
+        r += len;
+      }
+      for (int c = 0; c < ls.qcols[q];) {
+        const int64_t e = ls.colR[c0 + c];
+        const int i3 = (int)(e / m4), i4 = (int)(e % m4);
+        int len = 1;
+        while (c + len < ls.qcols[q] && ls.colR[c0 + c + len] == e + len &&
+               (e + len) / m4 == i3)
+          ++len;
+        cseg[std::make_tuple(q, i3, i4)] = {c, len};
+        qcols[q].push_back({i3, i4, c, len});
+        c += len;
+      }
+      r0 += ls.qld[q];
+      c0 += ls.qcols[q];
+    }
+    std::vector<DotItem> items;
+    std::vector<size_t> first;  // item range of each output: legs, then rungs
+    // A[i2'][i2] of a row-major d x d operator, transposed when t
+    auto el = [d](const Mat& X, bool t, int r, int c) {
+      return t ? X[(size_t)c * d + r] : X[(size_t)r * d + c];
+    };
+    auto add = [&](const Mat& A, bool ta, const Mat* B, bool tb, double coef) {
+      for (int q = 0; q < nQ; ++q)
+        for (const auto& rs : qrows[q])
+          for (int i2p = 0; i2p < d; ++i2p) {
+            const double a = el(A, ta, i2p, rs[0]);
+            if (a == 0.0) continue;
+            auto pr = rseg.find({i2p, rs[1]});
+            if (pr == rseg.end() || pr->second.len != rs[3]) continue;
+            const int qp = pr->second.q;
+            for (const auto& cs : qcols[q])
+              for (int i3p = 0; i3p < d; ++i3p) {
+                const double b = B ? el(*B, tb, i3p, cs[0]) : (i3p == cs[0] ? 1.0 : 0.0);
+                if (b == 0.0) continue;
+                auto pc = cseg.find(std::make_tuple(qp, i3p, cs[1]));
+                if (pc == cseg.end() || pc->second.second != cs[3]) continue;
+                DotItem t;
+                t.off1 = ls.qbase[qp] + pr->second.off + (long long)ls.qld[qp] * pc->second.first;
+                t.ld1 = ls.qld[qp];
+                t.off2 = ls.qbase[q] + rs[2] + (long long)ls.qld[q] * cs[2];
+                t.ld2 = ls.qld[q];
+                t.rows = rs[3];
+                t.cols = cs[3];
+                t.coef = coef * a * b;
+                items.push_back(t);
+              }
+          }
+    };
+    for (int y = 0; y < nl; ++y) {
+      first.push_back(items.size());
+      add(col_.sz[y], false, &col_.sz[y], false, 1.0);
+      add(col_.sp[y], false, &col_.sp[y], true, 0.5);
+      add(col_.sp[y], true, &col_.sp[y], false, 0.5);
+    }
+    for (int y = 0; y + 1 < nl; ++y) {
+      first.push_back(items.size());
+      add(rung_h_[(size_t)y], false, nullptr, false, 1.0);
+    }
+    first.push_back(items.size());
+    leg->assign(nl, 0.0);
+    rung->assign(std::max(nl - 1, 0), 0.0);
+    if (items.empty()) return DMRG2D_OK;
+    IBuf d_items;
+    DBuf d_out;
+    {
+      std::vector<int64_t> raw(items.size() * sizeof(DotItem) / sizeof(int64_t));
+      std::memcpy(raw.data(), items.data(), items.size() * sizeof(DotItem));
+      D2_TRY(d_items.upload(raw, strm_));
+    }
+    D2_TRY(d_out.alloc(items.size()));
+    const int grid = (int)std::min<size_t>(items.size(), 152 * 8);
+    k_item_dots<<<grid, 256, 0, strm_>>>(ls.x->p, (const DotItem*)d_items.p, (int)items.size(),
+                                         d_out.p);
+    D2_CUDA(cudaGetLastError());
+    Mat vals(items.size());
+    D2_CUDA(cudaMemcpyAsync(vals.data(), d_out.p, items.size() * sizeof(double),
+                            cudaMemcpyDeviceToHost, strm_));
+    D2_CUDA(cudaStreamSynchronize(strm_));
+    for (size_t o = 0; o + 1 < first.size(); ++o) {
+      double v = 0.0;
+      for (size_t i = first[o]; i < first[o + 1]; ++i) v += vals[i];
+      if ((int)o < nl)
+        (*leg)[o] = v;
+      else
+        (*rung)[o - nl] = v;
     }
     return DMRG2D_OK;
   }
@@ -1015,6 +1175,8 @@ class Sweeper {
       }
       last_sec_.d_rowL = d_rowL;
       last_sec_.d_colR = d_colR;
+      last_sec_.rowL = rowL;
+      last_sec_.colR = colR;
     }
     double norm2 = 0.0;  // trace of rho = |x|^2
     D2_BLAS(cublasDdot(libs_.bl, (int)nv, x.p, 1, x.p, 1, &norm2));
@@ -1037,7 +1199,12 @@ class Sweeper {
                               strm_));
       D2_CUDA(cudaStreamSynchronize(strm_));
     } else {
-      D2_TRY(observables(xd->p, Lb, Rb, out == nullptr, &leg, &rung, &s2));
+      if (sec) {  // bond energies on the packed state; <S_tot^2> on the dense V
+        D2_TRY(bonds_sectors(Lb.m, Rb.m, &leg, &rung));
+        if (out == nullptr) D2_TRY(observables(xd->p, Lb, Rb, true, &leg, &rung, &s2, false));
+      } else {
+        D2_TRY(observables(xd->p, Lb, Rb, out == nullptr, &leg, &rung, &s2));
+      }
       for (double& v : leg) v /= norm2;
       for (double& v : rung) v /= norm2;
       s2 /= norm2;
@@ -1401,6 +1568,7 @@ class Sweeper {
   Mat col_Sz_tot_, col_Sp_tot_;
   DBuf dSz_tot_, dSp_tot_;
   std::vector<DBuf> drung_;
+  std::vector<Mat> rung_h_;  // the same rung-bond operators on the host (row-major)
   std::shared_ptr<DBuf> last_x_;  // ground state of the last step's superblock
   int64_t last_nv_ = 0;
   // the last step's sector-restricted ground state: packed vector, its layout (the rows
@@ -1412,6 +1580,7 @@ class Sweeper {
     std::shared_ptr<DBuf> x;
     std::vector<long long> qbase;
     std::vector<int> qld, qcols, qlab;
+    std::vector<int64_t> rowL, colR;
     std::shared_ptr<IBuf> d_rowL, d_colR;
   } last_sec_;
 
