@@ -9,10 +9,12 @@
 // and uploads them.  Column operators are built here from bit arithmetic on
 // the column basis (layout in include/dmrg2d.h).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
 #include <map>
+#include <thread>
 
 #include "common.h"
 
@@ -212,6 +214,24 @@ void hubbard_column_ops(int n, double t, double U, bool pbc, HubbardColumnOps* o
 }
 
 // Assemble the packed operators on the host.
+// f(0 .. n-1) on the host's cores (the operator blocks of a superblock are independent)
+template <typename F>
+static void parallel_for(int n, F f) {
+  const int nt = (int)std::min<unsigned>((unsigned)std::max(n, 1),
+                                         std::max(1u, std::thread::hardware_concurrency()));
+  if (nt <= 1 || n < 2) {
+    for (int i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::atomic<int> next{0};
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nt; ++t)
+    pool.emplace_back([&] {
+      for (int i = next++; i < n; i = next++) f(i);
+    });
+  for (auto& th : pool) th.join();
+}
+
 static int assemble(const dmrg2d_model* M, const dmrg2d_block* L, const dmrg2d_block* R,
                     dmrg2d_ops* ops, std::vector<double>& HL, std::vector<double>& HR) {
   const bool heis = M->kind == DMRG2D_HEISENBERG;
@@ -297,22 +317,26 @@ static int assemble(const dmrg2d_model* M, const dmrg2d_block* L, const dmrg2d_b
       ptr[i + 1] = (int)cidx.size();
     }
     const size_t mm = (size_t)m * m;
-    blocks.assign(cidx.size() * mm, 0.0);
+    std::vector<int> row_of(cidx.size());
     for (int i = 0; i < d; ++i)
-      for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
-        const int k = cidx[e];
-        double* B = blocks.data() + (size_t)e * mm;
-        if (i == k)
-          for (size_t q = 0; q < mm; ++q) B[q] += HB[q];
-        const double hc = col.H[(size_t)i * d + k];
-        if (hc != 0.0)
-          for (int q = 0; q < m; ++q) B[(size_t)q * m + q] += hc;
-        for (const Term& tm : terms) {
-          const double x = tm.coef * tm.X[(size_t)i * d + k];
-          if (x == 0.0) continue;
-          for (size_t q = 0; q < mm; ++q) B[q] += x * tm.Y[q];
-        }
+      for (int e = ptr[i]; e < ptr[i + 1]; ++e) row_of[(size_t)e] = i;
+    blocks.resize(cidx.size() * mm);
+    parallel_for((int)cidx.size(), [&](int e) {  // one block position per task
+      const int i = row_of[(size_t)e], k = cidx[(size_t)e];
+      double* B = blocks.data() + (size_t)e * mm;
+      if (i == k)
+        std::copy(HB, HB + mm, B);
+      else
+        std::fill(B, B + mm, 0.0);
+      const double hc = col.H[(size_t)i * d + k];
+      if (hc != 0.0)
+        for (int q = 0; q < m; ++q) B[(size_t)q * m + q] += hc;
+      for (const Term& tm : terms) {
+        const double x = tm.coef * tm.X[(size_t)i * d + k];
+        if (x == 0.0) continue;
+        for (size_t q = 0; q < mm; ++q) B[q] += x * tm.Y[q];
       }
+    });
   };
   std::vector<std::vector<char>> posL, posR;
   build_side(tl, L->H, m1, ops->hLptr, ops->hLcol, HL, posL);
