@@ -277,7 +277,11 @@ int dmrg2d_lanczos_ground_noalloc(const dmrg2d_ops* ops, const dmrg2d_solver_opt
  * states: H_l V with the MMA's M = 128 along the columns of each V_q and N = one row
  * segment (the grouped kernel's operands with their roles swapped), then V H_r^T with M
  * along the rows and N = one column segment, N rounded up to 16, K steps past a block's K
- * skipped, the scalar moves in their own kernel (y must be 16-byte aligned).
+ * skipped, the scalar moves in their own kernel (y must be 16-byte aligned); 23 and 24
+ * are configurations 11 (CTA pair, blocked order) and 8 (dense kernel, blocked order)
+ * with the MN-major V operand of V H_r^T fetched per pipeline stage by one 3-D tensor
+ * copy (a row within a block of rows, the column, the row block) instead of one 2-D box
+ * per block of rows (same shared-memory image, same results).
  * dmrg2d_autotune times a complete H·v (scalar moves included) with every
  * configuration that applies (one warm-up and three timed launches each, on scratch
  * buffers it allocates and frees), keeps the fastest for later apply_H and solver
