@@ -14,7 +14,10 @@ the same call with the vector staged from/to pinned host memory (pipelined over
 three streams), SM clocks sampled during the timed region, the CPU oracle timed
 on a bounded sample, the time to the ground energy (residual 1e-7 |E|) of the
 mixed-precision solver (--no-tte to skip; --tte-fp64 adds the plain FP64 Lanczos,
-which takes over 25 minutes), and with --sweep the DMRG sweep on a 4 x 12 ladder.
+which takes over 25 minutes), the H·v of the other workloads (the two m = 1024 sector
+superblocks and the small FP64 one with its Lanczos step latency; --no-other-workloads
+to skip), and with --sweep the DMRG sweep on a 4 x 12 ladder (--sweep-profile: its
+kernel shares under the CUDA profiler).
 
   python bench.py [--gpus N --steps K --warmup W] [--precision tf32|bf16|fp32|fp64]
   python bench.py --impl reference     # the CPU oracle on the same workload
@@ -460,8 +463,12 @@ def run_ours(args):
         out["time_to_energy"] = time_to_energy(ops, n, prec, args, dev)
     if prec == dmrg2d.FP64 and rank == 0:   # the small superblock: latency per H·v and step
         out["latency"] = {"us_per_hv": ms * 1e3, **lanczos_latency(ops, n, dev)}
+    if args.other_workloads and rank == 0 and world == 1 and args.workload == WORKLOAD:
+        out["other_workloads"] = other_workloads(args, dev)
     if args.sweep and rank == 0:
         out["dmrg_sweep"] = dmrg_sweep_run(args)
+    if args.sweep_profile and rank == 0:
+        out["dmrg_sweep_kernel_profile"] = sweep_kernel_profile(args)
     if args.precond_study and rank == 0:
         out["precond_study"] = precond_study(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -517,6 +524,115 @@ def dmrg_sweep_run(args):
             "density_matrix_seconds": out["dm_seconds"], "renorm_seconds": out["renorm_seconds"],
             "observables_seconds": out["obs_seconds"], "s2_per_sweep": s2,
             "leg_bond_profile_last_sweep": profile}
+
+
+def other_workloads(args, dev):
+    """H·v of the other workloads on the same GPU (outside the headline's timed region):
+    the two sector-restricted m = 1024 superblocks in their precisions (tile configuration
+    by the autotuner) and the small FP64 superblock with its Lanczos step latency.  Each
+    H·v timed alone by CUDA events; the small one with an L2 flush (512 MB write) before
+    each H·v, the large ones with inputs larger than L2."""
+    import torch
+    from paper_0707_0159_gb300 import dmrg2d, synth
+    pk = peaks()
+    res = {}
+    for name in ("ladder4_heisenberg_d16_m1024_sectors", "ladder3_hubbard_d64_m1024_sectors",
+                 "ladder2_heisenberg_d4_m64"):
+        build, pname, _ = WORKLOADS[name]
+        prec = dmrg2d.PRECISION[pname]
+        mdl, left, right, target = build(synth)
+        ops = dmrg2d.build_ops(mdl, left, right, target=target)
+        n, flops = ops.info["n_vec"], ops.info["flops_per_apply"]
+        v_np = synth.start_vector(n, 12)
+        if target is not None:
+            v_np[dmrg2d.sector_dense_index(ops) < 0] = 0.0
+        in_dt = {dmrg2d.FP64: torch.float64, dmrg2d.TF32: torch.float32,
+                 dmrg2d.BF16: torch.bfloat16}[prec]
+        v = torch.from_numpy(v_np).to(in_dt).to(dev)
+        y = torch.empty(n, dtype=torch.float64 if prec == dmrg2d.FP64 else torch.float32,
+                        device=dev)
+        tune = None
+        if prec != dmrg2d.FP64:
+            best, _ = dmrg2d.autotune(ops, prec)
+            tune = {"chosen": best, "name": dmrg2d.tile_config_name(best)}
+        small = prec == dmrg2d.FP64
+        scratch = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev) if small else None
+        for _ in range(3):
+            dmrg2d.apply_H(ops, v, y, prec)
+        torch.cuda.synchronize()
+        evs = []
+        for _ in range(10):
+            if small:
+                scratch.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            dmrg2d.apply_H(ops, v, y, prec)
+            b.record()
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in evs) / len(evs)
+        tf = flops / (ms * 1e-3) / 1e12
+        if prec == dmrg2d.BF16:
+            peak = pk.get("bf16_tflops", 1900.0)
+        elif prec == dmrg2d.TF32:
+            peak = pk.get("bf16_tflops", 1900.0) * 1.1 / 2.25
+        else:
+            peak = 1.25
+        res[name] = {"precision": pname, "n_vec": n, "flops_per_hv": flops, "ms_per_hv": ms,
+                     "tflops": tf, "frac_of_peak": tf / peak, "tile_config": tune}
+        if small:
+            res[name]["latency"] = {"us_per_hv": ms * 1e3, **lanczos_latency(ops, n, dev)}
+        del ops, v, y, scratch
+    return res
+
+
+def sweep_kernel_profile(args):
+    """Where the sweep's device time goes: the 4 x 12 sweep with the --sweep-profile-m
+    schedule run once under the CUDA profiler (CUPTI, through torch.profiler), kernels
+    grouped by name.  Times under the profiler are not benchmark values: only the shares
+    are reported as evidence."""
+    from torch.profiler import ProfilerActivity, profile
+    from paper_0707_0159_gb300 import dmrg2d, synth
+    mdl = synth.model("heisenberg", 4, J_leg=1.0, J_rung=1.0)
+    ms = [int(m) for m in args.sweep_profile_m.split(",")]
+    prec = args.sweep_precision or args.precision
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        out = dmrg2d.sweep(mdl, 12, m_warmup=args.sweep_m_warmup, m_sweeps=ms,
+                           precision=prec, tol=1e-9, max_iter=600, krylov_dim=80, sectors=True)
+    rows = []
+    for e in prof.key_averages():
+        t = getattr(e, "device_time_total", None)
+        if t is None:
+            t = getattr(e, "cuda_time_total", 0.0)
+        if t > 0 and not e.key.startswith("Memcpy") and not e.key.startswith("Memset"):
+            rows.append((t, e.count, e.key))
+    rows.sort(reverse=True)
+    tot = sum(r[0] for r in rows) or 1.0
+
+    def group(name):
+        if "sytrd" in name:
+            return "cuSOLVER tridiagonalisation (sytrd)"
+        if "stedc" in name or "laed" in name or "steqr" in name or "larft" in name \
+                or "ormtr" in name or "transpose<sytrd" in name:
+            return "cuSOLVER other (eigenvectors, back-transformation)"
+        if "d884gemm" in name or "d884syrk" in name or "syherk" in name or "gemm" in name.lower():
+            return "cuBLAS FP64 GEMM / SYRK"
+        if "hv_" in name:
+            return "H·v kernels (this library)"
+        if "dmrg2d" in name:
+            return "other kernels of this library"
+        return "other"
+    groups = {}
+    for t, c, k in rows:
+        g = groups.setdefault(group(k), [0.0, 0])
+        g[0] += t
+        g[1] += c
+    return {"schedule": {"m_warmup": args.sweep_m_warmup, "m_sweeps": ms}, "precision": prec,
+            "steps": out["n_steps"], "note": "device time under the CUDA profiler; shares only",
+            "groups": {k: {"share": v[0] / tot, "launches": v[1]}
+                       for k, v in sorted(groups.items(), key=lambda kv: -kv[1][0])},
+            "top_kernels": [{"name": k[:120], "launches": c, "share": t / tot}
+                            for t, c, k in rows[:15]]}
 
 
 def precond_study(args):
@@ -711,6 +827,14 @@ def main():
     ap.add_argument("--sweep-m-warmup", type=int, default=128)
     ap.add_argument("--sweep-precision", default=None, choices=["tf32", "bf16", "fp64"],
                     help="ground-state H·v precision of the sweep (default: --precision)")
+    ap.add_argument("--other-workloads", action="store_true", default=True,
+                    help="also time the sector-restricted and small workloads' H·v (default "
+                         "on, with the default workload at N = 1)")
+    ap.add_argument("--no-other-workloads", dest="other_workloads", action="store_false")
+    ap.add_argument("--sweep-profile", action="store_true",
+                    help="also run the sweep once under the CUDA profiler: kernel shares")
+    ap.add_argument("--sweep-profile-m", default="128,1024",
+                    help="states kept per finite sweep in the profiled run")
     ap.add_argument("--sweep-solver", default="lanczos", choices=["lanczos", "davidson"])
     ap.add_argument("--sweep-precond", default="jacobi", choices=["none", "jacobi", "mlp"],
                     help="Davidson preconditioner of the sweep (mlp: trained in the sweep)")
