@@ -110,12 +110,26 @@ struct DBuf {
   }
 };
 
+// library handles on the sweep's stream, and kSide side streams with their own handles
+// (the density matrices of different sectors are formed and diagonalised concurrently)
+constexpr int kSide = 4;
 struct Libs {
   cublasHandle_t bl = nullptr;
   cusolverDnHandle_t sv = nullptr;
+  cudaStream_t side[kSide] = {};
+  cublasHandle_t sbl[kSide] = {};
+  cusolverDnHandle_t ssv[kSide] = {};
+  cudaEvent_t ev_main = nullptr, ev_side[kSide] = {};
   ~Libs() {
     if (bl) cublasDestroy(bl);
     if (sv) cusolverDnDestroy(sv);
+    for (int k = 0; k < kSide; ++k) {
+      if (sbl[k]) cublasDestroy(sbl[k]);
+      if (ssv[k]) cusolverDnDestroy(ssv[k]);
+      if (ev_side[k]) cudaEventDestroy(ev_side[k]);
+      if (side[k]) cudaStreamDestroy(side[k]);
+    }
+    if (ev_main) cudaEventDestroy(ev_main);
   }
 };
 
@@ -282,6 +296,15 @@ class Sweeper {
     D2_BLAS(cublasSetStream(libs_.bl, strm_));
     D2_SOLV(cusolverDnCreate(&libs_.sv));
     D2_SOLV(cusolverDnSetStream(libs_.sv, strm_));
+    D2_CUDA(cudaEventCreateWithFlags(&libs_.ev_main, cudaEventDisableTiming));
+    for (int k = 0; k < kSide; ++k) {
+      D2_CUDA(cudaStreamCreateWithFlags(&libs_.side[k], cudaStreamNonBlocking));
+      D2_CUDA(cudaEventCreateWithFlags(&libs_.ev_side[k], cudaEventDisableTiming));
+      D2_BLAS(cublasCreate(&libs_.sbl[k]));
+      D2_BLAS(cublasSetStream(libs_.sbl[k], libs_.side[k]));
+      D2_SOLV(cusolverDnCreate(&libs_.ssv[k]));
+      D2_SOLV(cusolverDnSetStream(libs_.ssv[k], libs_.side[k]));
+    }
     // column operators on the device (row-major buffers)
     D2_TRY(dH_col_.upload(col_.H, strm_));
     const int dd = col_.d, nl = (int)col_.sz.size();
@@ -615,44 +638,6 @@ class Sweeper {
     return DMRG2D_OK;
   }
 
-  // The `top` largest eigenpairs (ascending) of the symmetric n x n matrix A (lower), in
-  // place: eigenvectors in A's first `top` columns, eigenvalues to the host.  dsyevd for
-  // the whole spectrum, dsyevdx selected by index otherwise.
-  int eigh_top(double* A, int n, int top, Mat* w_host) {
-    DBuf w, work;
-    D2_TRY(w.alloc((size_t)n));
-    int lwork = 0, meig = top;
-    const bool all = top >= n;
-    if (all)
-      D2_SOLV(cusolverDnDsyevd_bufferSize(libs_.sv, CUSOLVER_EIG_MODE_VECTOR,
-                                          CUBLAS_FILL_MODE_LOWER, n, A, n, w.p, &lwork));
-    else
-      D2_SOLV(cusolverDnDsyevdx_bufferSize(libs_.sv, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I,
-                                           CUBLAS_FILL_MODE_LOWER, n, A, n, 0.0, 0.0, n - top + 1,
-                                           n, &meig, w.p, &lwork));
-    D2_TRY(work.alloc((size_t)std::max(lwork, 1)));
-    IBuf info;
-    D2_TRY(info.upload(std::vector<int>{0}, strm_));
-    if (all)
-      D2_SOLV(cusolverDnDsyevd(libs_.sv, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, A, n,
-                               w.p, work.p, lwork, (int*)info.p));
-    else
-      D2_SOLV(cusolverDnDsyevdx(libs_.sv, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I,
-                                CUBLAS_FILL_MODE_LOWER, n, A, n, 0.0, 0.0, n - top + 1, n, &meig,
-                                w.p, work.p, lwork, (int*)info.p));
-    int hinfo = 0;
-    const int got = all ? n : top;
-    w_host->resize((size_t)got);
-    D2_CUDA(cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, strm_));
-    D2_CUDA(cudaMemcpyAsync(w_host->data(), w.p, got * sizeof(double), cudaMemcpyDeviceToHost,
-                            strm_));
-    D2_CUDA(cudaStreamSynchronize(strm_));
-    if (hinfo != 0 || (!all && meig != top))
-      return set_error(DMRG2D_ECUDA, "sweep: dsyevd(x) info %d, %d of %d eigenpairs", hinfo, meig,
-                       top);
-    return DMRG2D_OK;
-  }
-
   // Dense superblock: rho = V V^T (grow_left) or V^T V of the dense V = x ((n x other) or
   // (other x n)), its k leading eigenvectors (dsyevdx, selected by index) into U, largest
   // first; *kept = their eigenvalue sum.
@@ -744,10 +729,15 @@ class Sweeper {
       int q, j;
     };
     std::vector<Cand> cand;
+    // host side first (index lists, uploads on the sweep's stream, every buffer), so that
+    // no allocation or free falls between the launches of the side streams
+    std::vector<std::shared_ptr<IBuf>> d_rows(nQ);
+    std::vector<std::shared_ptr<DBuf>> G(nQ), work(nQ);
+    std::vector<int> top(nQ), lwork(nQ), meig(nQ), all(nQ);
+    std::vector<int64_t> woff(nQ + 1, 0);
     int64_t r0 = 0, c0 = 0;
     for (int q = 0; q < nQ; ++q) {
       std::vector<int64_t> dense;
-      const double* xq = xpk + qbase[q];
       vecs[q] = std::make_shared<DBuf>();
       if (grow_left) {
         std::vector<int> rows;
@@ -756,34 +746,87 @@ class Sweeper {
             rows.push_back(r);
             dense.push_back(rowL[r0 + r]);
           }
-        const int nr = (int)rows.size();
-        IBuf d_rows;
-        D2_TRY(d_rows.upload(rows, strm_));
-        DBuf G;
-        D2_TRY(G.alloc((size_t)nr * qcols[q]));
-        k_gather_rows<<<512, 256, 0, strm_>>>(xq, qld[q], qcols[q], (const int*)d_rows.p, nr, G.p);
-        D2_CUDA(cudaGetLastError());
-        D2_TRY(vecs[q]->alloc((size_t)nr * nr));
-        D2_BLAS(cublasDsyrk(libs_.bl, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, nr, qcols[q], &one, G.p,
-                            nr, &zero, vecs[q]->p, nr));
-        dim[q] = nr;
+        dim[q] = (int)rows.size();
+        d_rows[q] = std::make_shared<IBuf>();
+        D2_TRY(d_rows[q]->upload(rows, strm_));
+        G[q] = std::make_shared<DBuf>();
+        D2_TRY(G[q]->alloc((size_t)dim[q] * qcols[q]));
         lab[q] = enlarged_label(Lb, dense[0]);  // of the enlarged-left state i1 + m1 i2
       } else {
         for (int c = 0; c < qcols[q]; ++c) dense.push_back(colR[c0 + c]);
-        D2_TRY(vecs[q]->alloc((size_t)qcols[q] * qcols[q]));
-        D2_BLAS(cublasDsyrk(libs_.bl, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, qcols[q], qld[q], &one,
-                            xq, qld[q], &zero, vecs[q]->p, qcols[q]));
         dim[q] = qcols[q];
         lab[q] = enlarged_label(Rb, dense[0]);  // of the enlarged-right state i4 + m4 i3
       }
+      D2_TRY(vecs[q]->alloc((size_t)dim[q] * dim[q]));
       idx[q] = std::make_shared<IBuf>();
       D2_TRY(idx[q]->upload(dense, strm_));
       // at most *kio states are kept from any one sector: its *kio largest eigenpairs
-      Mat w;
-      D2_TRY(eigh_top(vecs[q]->p, dim[q], std::min(dim[q], *kio), &w));
-      for (int j = 0; j < (int)w.size(); ++j) cand.push_back({w[(size_t)j], q, j});
+      // (dsyevd for the whole spectrum, dsyevdx selected by index otherwise)
+      const int n = dim[q], k = q % kSide;
+      top[q] = std::min(n, *kio);
+      all[q] = top[q] >= n;
+      meig[q] = top[q];
+      if (all[q])
+        D2_SOLV(cusolverDnDsyevd_bufferSize(libs_.ssv[k], CUSOLVER_EIG_MODE_VECTOR,
+                                            CUBLAS_FILL_MODE_LOWER, n, vecs[q]->p, n,
+                                            vecs[q]->p, &lwork[q]));
+      else
+        D2_SOLV(cusolverDnDsyevdx_bufferSize(
+            libs_.ssv[k], CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I, CUBLAS_FILL_MODE_LOWER, n,
+            vecs[q]->p, n, 0.0, 0.0, n - top[q] + 1, n, &meig[q], vecs[q]->p, &lwork[q]));
+      work[q] = std::make_shared<DBuf>();
+      D2_TRY(work[q]->alloc((size_t)std::max(lwork[q], 1)));
+      woff[q + 1] = woff[q] + n;
       r0 += qld[q];
       c0 += qcols[q];
+    }
+    DBuf w_all;
+    IBuf info_all;
+    D2_TRY(w_all.alloc((size_t)std::max<int64_t>(woff[nQ], 1)));
+    D2_TRY(info_all.upload(std::vector<int>((size_t)nQ, 0), strm_));
+    // the sectors' density matrices and eigenpairs on the side streams, after the sweep's
+    // stream has produced the ground state and the uploads above
+    D2_CUDA(cudaEventRecord(libs_.ev_main, strm_));
+    for (int k = 0; k < kSide; ++k) D2_CUDA(cudaStreamWaitEvent(libs_.side[k], libs_.ev_main, 0));
+    r0 = 0;
+    for (int q = 0; q < nQ; ++q) {
+      const int k = q % kSide, n = dim[q];
+      const double* xq = xpk + qbase[q];
+      if (grow_left) {
+        k_gather_rows<<<512, 256, 0, libs_.side[k]>>>(xq, qld[q], qcols[q],
+                                                      (const int*)d_rows[q]->p, n, G[q]->p);
+        D2_CUDA(cudaGetLastError());
+        D2_BLAS(cublasDsyrk(libs_.sbl[k], CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, n, qcols[q], &one,
+                            G[q]->p, n, &zero, vecs[q]->p, n));
+      } else {
+        D2_BLAS(cublasDsyrk(libs_.sbl[k], CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, n, qld[q], &one,
+                            xq, qld[q], &zero, vecs[q]->p, n));
+      }
+      int* info = (int*)info_all.p + q;
+      if (all[q])
+        D2_SOLV(cusolverDnDsyevd(libs_.ssv[k], CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n,
+                                 vecs[q]->p, n, w_all.p + woff[q], work[q]->p, lwork[q], info));
+      else
+        D2_SOLV(cusolverDnDsyevdx(libs_.ssv[k], CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I,
+                                  CUBLAS_FILL_MODE_LOWER, n, vecs[q]->p, n, 0.0, 0.0,
+                                  n - top[q] + 1, n, &meig[q], w_all.p + woff[q], work[q]->p,
+                                  lwork[q], info));
+    }
+    for (int k = 0; k < kSide; ++k) {
+      D2_CUDA(cudaEventRecord(libs_.ev_side[k], libs_.side[k]));
+      D2_CUDA(cudaStreamWaitEvent(strm_, libs_.ev_side[k], 0));
+    }
+    Mat w_host((size_t)std::max<int64_t>(woff[nQ], 1));
+    std::vector<int> info_host((size_t)nQ, 0);
+    D2_CUDA(cudaStreamSynchronize(strm_));
+    D2_CUDA(cudaMemcpy(w_host.data(), w_all.p, sizeof(double) * woff[nQ], cudaMemcpyDeviceToHost));
+    D2_CUDA(cudaMemcpy(info_host.data(), info_all.p, sizeof(int) * nQ, cudaMemcpyDeviceToHost));
+    for (int q = 0; q < nQ; ++q) {
+      if (info_host[(size_t)q] != 0 || (!all[q] && meig[q] != top[q]))
+        return set_error(DMRG2D_ECUDA, "sweep: dsyevd(x) info %d, %d of %d eigenpairs",
+                         info_host[(size_t)q], meig[q], top[q]);
+      const int got = all[q] ? dim[q] : top[q];
+      for (int j = 0; j < got; ++j) cand.push_back({w_host[(size_t)(woff[q] + j)], q, j});
     }
     // Labels of the enlarged block that no V_q holds (the superblock's target leaves them
     // empty, as the smaller superblocks of the warm-up do for labels only the full filling
