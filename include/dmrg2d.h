@@ -281,7 +281,8 @@ int dmrg2d_lanczos_ground_noalloc(const dmrg2d_ops* ops, const dmrg2d_solver_opt
  * are configurations 11 (CTA pair, blocked order) and 8 (dense kernel, blocked order)
  * with the MN-major V operand of V H_r^T fetched per pipeline stage by one 3-D tensor
  * copy (a row within a block of rows, the column, the row block) instead of one 2-D box
- * per block of rows (same shared-memory image, same results).
+ * per block of rows (same shared-memory image, same results); 25 and 26 are configuration
+ * 23 with the output tiles visited in 4 x 4 / 16 x 16 patches instead of 8 x 8.
  * dmrg2d_autotune times a complete H·v (scalar moves included) with every
  * configuration that applies (one warm-up and three timed launches each, on scratch
  * buffers it allocates and frees), keeps the fastest for later apply_H and solver

@@ -574,6 +574,7 @@ struct TcState {
   int* err = nullptr;
   int* order = nullptr;   // blocked piece order of the dense kernel
   int* order2 = nullptr;  // the same for the CTA-pair kernel (256-row pieces)
+  int* order2p[2] = {nullptr, nullptr};  // the CTA-pair kernel in 4 x 4 / 16 x 16 patches
   // two-pass form: pass A (H_l V, column-slab order) and pass B (V H_r^T, row-slab
   // order), for 128-row pieces [0] and CTA-pair pieces [1]; the scalar moves split so
   // that each pass reads the sources its order keeps in L2
@@ -780,8 +781,8 @@ int tc_prepare(dmrg2d_ops* ops, cudaStream_t s, const std::vector<double>& HL,
     }
     if (st == DMRG2D_OK && T->pair_ok)
       st = make_map(&T->mHR2lo, T->HRlo, true, m4, nR * m4, 64, P_HALF);
-    auto upload_order = [&](int** dst, int pieces_mt) {
-      const std::vector<int> ord = blocked_order(d, pieces_mt, m4 / T->BN, 8);
+    auto upload_order = [&](int** dst, int pieces_mt, int patch = 8) {
+      const std::vector<int> ord = blocked_order(d, pieces_mt, m4 / T->BN, patch);
       alloc((void**)dst, sizeof(int) * ord.size());
       if (st == DMRG2D_OK &&
           cudaMemcpy(*dst, ord.data(), sizeof(int) * ord.size(), cudaMemcpyHostToDevice) !=
@@ -789,7 +790,11 @@ int tc_prepare(dmrg2d_ops* ops, cudaStream_t s, const std::vector<double>& HL,
         st = set_error(DMRG2D_ECUDA, "order upload failed");
     };
     upload_order(&T->order, m1 / BM);
-    if (T->pair_ok) upload_order(&T->order2, m1 / 256);
+    if (T->pair_ok) {
+      upload_order(&T->order2, m1 / 256);
+      upload_order(&T->order2p[0], m1 / 256, 4);
+      upload_order(&T->order2p[1], m1 / 256, 16);
+    }
     // two-pass form: slab orders and the moves split by pass (same column: pass A,
     // same row: pass B, the rest (H_c between the two columns): pass A)
     auto upload_ints = [&](int** dst, const std::vector<int>& h) {
@@ -925,6 +930,8 @@ void tc_release(dmrg2d_ops* ops) {
   if (T->err) cudaFree(T->err);
   if (T->order) cudaFree(T->order);
   if (T->order2) cudaFree(T->order2);
+  for (int k = 0; k < 2; ++k)
+    if (T->order2p[k]) cudaFree(T->order2p[k]);
   for (int k = 0; k < 2; ++k) {
     if (T->orderA[k]) cudaFree(T->orderA[k]);
     if (T->orderB[k]) cudaFree(T->orderB[k]);
@@ -964,7 +971,10 @@ static int launch_dense_kernel(const dmrg2d_ops* ops, const TcState* T, const vo
   p.n_mt = pair ? m1 / 256 : m1 / BM;  // pieces (pairs of pieces) per block row
   p.n_nt = m4 / T->BN;
   p.tiles = d * p.n_mt * d * p.n_nt;
-  p.order = (variant & 2) ? (pair ? T->order2 : T->order) : nullptr;
+  // blocked order: 8 x 8 tile patches, or (CTA pairs, bits 5 / 6) 4 x 4 / 16 x 16
+  const int* pair_order = (variant & 32) ? T->order2p[0] : (variant & 64) ? T->order2p[1]
+                                                                          : T->order2;
+  p.order = (variant & 2) ? (pair ? pair_order : T->order) : nullptr;
   p.ph0 = 0;
   p.ph1 = 2;
   p.accum_y = accum ? 1 : 0;
@@ -1137,7 +1147,8 @@ namespace dmrg2d {
 // 22 = segment kernels (sectors: M along the long dimension of each V_q, moves separate)
 // 23 / 24 = CTA-pair kernel / dense kernel in blocked order, the phase-2 V operand in one
 // 3-D copy per stage
-constexpr int N_CANDIDATES = 25;
+// 25 / 26 = candidate 23 with the output tiles in 4 x 4 / 16 x 16 patches
+constexpr int N_CANDIDATES = 27;
 static int idx_to_cfg(int idx) {
   static const int dense_variant[14] = {0, -1, -1, -1, -1, -1, -1, 1, 2, 3, 4, 6, 5, 7};
   if (idx >= 1 && idx <= 6) return idx - 1;
@@ -1146,6 +1157,8 @@ static int idx_to_cfg(int idx) {
   if (idx == 22) return 2 * gp_num_configs();
   if (idx == 23) return -1 - (6 | 16);
   if (idx == 24) return -1 - (2 | 16);
+  if (idx == 25) return -1 - (6 | 16 | 32);
+  if (idx == 26) return -1 - (6 | 16 | 64);
   if (idx >= 14) return gp_num_configs() + idx - 14;
   return -1 - dense_variant[idx];
 }
@@ -1154,7 +1167,7 @@ static bool tc_candidate_ok(const dmrg2d_ops* ops, int idx) {
   if (idx < 0 || idx >= N_CANDIDATES) return false;
   if (idx >= 14 && idx < 20) return ops->sec && ops->tc_ok;  // grouped, separate moves
   if (idx == 22) return ops->sec && ops->tc_ok;               // segment kernels
-  if (idx == 23 || idx == 24) {                                // dense kernels, 3-D V copies
+  if (idx >= 23) {                                             // dense kernels, 3-D V copies
     const TcState* T = (const TcState*)ops->tc;
     return !ops->sec && T && T->dense_ok && (idx == 24 || T->pair_ok);
   }
@@ -1199,6 +1212,8 @@ extern "C" const char* dmrg2d_tile_config_name(int index) {
   if (index == 22) return "segment kernels (M = 128 along V's long dimension, N = one sector), separate moves";
   if (index == 23) return "CTA-pair kernel 256x256 (8x8-tile blocked raster), phase-2 V in one 3-D copy";
   if (index == 24) return "dense kernel 128x256 (8x8-tile blocked raster), phase-2 V in one 3-D copy";
+  if (index == 25) return "CTA-pair kernel 256x256 (4x4-tile blocked raster), phase-2 V in one 3-D copy";
+  if (index == 26) return "CTA-pair kernel 256x256 (16x16-tile blocked raster), phase-2 V in one 3-D copy";
   static const char* sep[6] = {
       "grouped 128x128 column-slab, separate moves kernel",
       "grouped 128x128 row-slab, separate moves kernel",
@@ -1206,7 +1221,7 @@ extern "C" const char* dmrg2d_tile_config_name(int index) {
       "grouped 128x256 column-slab, separate moves kernel",
       "grouped 128x256 row-slab, separate moves kernel",
       "grouped 128x256 longest-first, separate moves kernel"};
-  if (index >= 14 && index < N_CANDIDATES) return sep[index - 14];
+  if (index >= 14 && index < 20) return sep[index - 14];
   return gp_config_name(index - 1);
 }
 

@@ -320,7 +320,7 @@ def profile_stop(ops: Ops):
     return ms.value, n.value
 
 
-N_TILE_CONFIGS = 25
+N_TILE_CONFIGS = 27
 
 
 def autotune(ops: Ops, precision, stream=None):

@@ -92,7 +92,7 @@ def test_cta_pair_kernel_matches_oracle_and_dense(case, prec):
     ref = sb.apply(v)
     dmrg2d.set_tile_config(ops, prec, 0)
     y0 = run(ops, v, prec)
-    for cfg in (10, 11, 12, 13, 20, 21, 23):  # per-position blocks / pool / two passes / 3-D
+    for cfg in (10, 11, 12, 13, 20, 21, 23, 25, 26):  # blocks / pool / two passes / 3-D
         dmrg2d.set_tile_config(ops, prec, cfg)
         y = run(ops, v, prec)
         assert rel(y, ref) <= TOL[prec], (cfg, rel(y, ref))

@@ -234,7 +234,7 @@ def test_ladder3_full_tensor_core_sampled(ladder3_full, prec, tol):
         pytest.skip("tensor-core path not available for these shapes")
     ref = sb.apply_at(v, idx)
     outs = {}
-    for cfg in (0, 7, 8, 9, 10, 11, 12, 13, 20, 21, 23, 24):
+    for cfg in (0, 7, 8, 9, 10, 11, 12, 13, 20, 21, 23, 24, 25, 26):
         dmrg2d.set_tile_config(ops, prec, cfg)
         y, _ = run(ops, v, prec)
         outs[cfg] = y[idx]
@@ -245,6 +245,8 @@ def test_ladder3_full_tensor_core_sampled(ladder3_full, prec, tol):
     for cfg in (10, 11, 12, 13, 23):  # M = 256 instructions over a CTA pair
         assert rel(outs[cfg], outs[0]) <= 1e-6, cfg
     assert np.array_equal(outs[23], outs[11])   # one 3-D copy = the four 2-D copies
+    for cfg in (25, 26):                          # patch size: the same pieces in another order
+        assert np.array_equal(outs[cfg], outs[23]), cfg
     # two passes: the first pass's partial sum (H_l V and its moves, entries up to |H_l||V|,
     # far above |Y|) is rounded to FP32 once more before V H_r^T is added
     for cfg in (20, 21):
