@@ -781,7 +781,7 @@ def time_to_energy(ops, n, prec, args, dev):
         res["speedup"] = res["fp64"]["seconds"] / res["mixed"]["seconds"]
         if args.tte_ref_tol > 0:
             # the same FP64 solve continued from its own vector to a tighter residual: the
-            # reference energy both solvers are judged against (not part of either time)
+            # reference energy both solvers are compared with (not part of either time)
             t0 = time.perf_counter()
             e_ref, st_ref, c_ref = dmrg2d.lanczos_ground(
                 ops, x, precision=dmrg2d.FP64, tol=args.tte_ref_tol,
