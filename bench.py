@@ -463,6 +463,8 @@ def run_ours(args):
         out["time_to_energy"] = time_to_energy(ops, n, prec, args, dev)
     if prec == dmrg2d.FP64 and rank == 0:   # the small superblock: latency per H·v and step
         out["latency"] = {"us_per_hv": ms * 1e3, **lanczos_latency(ops, n, dev)}
+    if args.link_probe and rank == 0:
+        out["host_link_probe"] = link_probe(dev)
     if args.other_workloads and rank == 0 and world == 1 and args.workload == WORKLOAD:
         out["other_workloads"] = other_workloads(args, dev)
     if args.sweep and rank == 0:
@@ -524,6 +526,38 @@ def dmrg_sweep_run(args):
             "density_matrix_seconds": out["dm_seconds"], "renorm_seconds": out["renorm_seconds"],
             "observables_seconds": out["obs_seconds"], "s2_per_sweep": s2,
             "leg_bond_profile_last_sweep": profile}
+
+
+def link_probe(dev):
+    """Host-link bandwidth with 1 GiB pinned buffers: host to device, device to host, and
+    both at once, each copy split into 1, 2, 4 or 8 chunks on separate streams."""
+    import torch
+    n = 2 ** 28
+    h_in = torch.empty(n, dtype=torch.float32).pin_memory()
+    h_out = torch.empty(n, dtype=torch.float32).pin_memory()
+    d_in = torch.empty(n, dtype=torch.float32, device=dev)
+    d_out = torch.empty(n, dtype=torch.float32, device=dev)
+    streams = [torch.cuda.Stream() for _ in range(8)]
+
+    def run(k, up, down, reps=5):
+        ch = n // k
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            for i in range(k):
+                if up:
+                    with torch.cuda.stream(streams[i % 4]):
+                        d_in[i * ch:(i + 1) * ch].copy_(h_in[i * ch:(i + 1) * ch],
+                                                        non_blocking=True)
+                if down:
+                    with torch.cuda.stream(streams[4 + i % 4]):
+                        h_out[i * ch:(i + 1) * ch].copy_(d_out[i * ch:(i + 1) * ch],
+                                                         non_blocking=True)
+        torch.cuda.synchronize()
+        return 4 * n / ((time.perf_counter() - t0) / reps) / 1e9
+
+    return {str(k): {"h2d_gbs": run(k, True, False), "d2h_gbs": run(k, False, True),
+                     "both_each_gbs": run(k, True, True)} for k in (1, 2, 4, 8)}
 
 
 def other_workloads(args, dev):
@@ -831,6 +865,8 @@ def main():
                     help="also time the sector-restricted and small workloads' H·v (default "
                          "on, with the default workload at N = 1)")
     ap.add_argument("--no-other-workloads", dest="other_workloads", action="store_false")
+    ap.add_argument("--link-probe", action="store_true",
+                    help="also measure the host link (one way and both ways, chunked copies)")
     ap.add_argument("--sweep-profile", action="store_true",
                     help="also run the sweep once under the CUDA profiler: kernel shares")
     ap.add_argument("--sweep-profile-m", default="128,1024",
