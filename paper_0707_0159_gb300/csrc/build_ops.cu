@@ -14,6 +14,7 @@
 #include <cstdarg>
 #include <cstring>
 #include <map>
+#include <new>
 #include <thread>
 
 #include "common.h"
@@ -224,11 +225,18 @@ static void parallel_for(int n, F f) {
     return;
   }
   std::atomic<int> next{0};
+  auto worker = [&] {
+    for (int i = next++; i < n; i = next++) f(i);
+  };
   std::vector<std::thread> pool;
-  for (int t = 0; t < nt; ++t)
-    pool.emplace_back([&] {
-      for (int i = next++; i < n; i = next++) f(i);
-    });
+  for (int t = 1; t < nt; ++t) {
+    try {
+      pool.emplace_back(worker);
+    } catch (...) {  // no more threads: the ones started and this one finish the work
+      break;
+    }
+  }
+  worker();
   for (auto& th : pool) th.join();
 }
 
@@ -423,7 +431,12 @@ extern "C" int dmrg2d_build_ops(const dmrg2d_model* model, const dmrg2d_block* l
   ops->n_legs = model->n_legs;
   cudaGetDevice(&ops->device);
   std::vector<double> HL, HR;
-  int st = assemble(model, left, right, ops, HL, HR);
+  int st;
+  try {
+    st = assemble(model, left, right, ops, HL, HR);
+  } catch (const std::bad_alloc&) {
+    st = set_error(DMRG2D_ENOMEM, "build_ops: out of host memory for the operator blocks");
+  }
   if (st != DMRG2D_OK) {
     delete ops;
     return st;
