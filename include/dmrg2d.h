@@ -408,8 +408,10 @@ void dmrg2d_free_ops(dmrg2d_ops* ops);
  * along the legs, n_columns even and >= 4; dense superblocks, or (use_sectors) the
  * S^z_tot = 0 sector: blocks carry their states' N_up (grouped by label), the superblock
  * H·v runs on the sector-restricted layout, and the density matrix, block diagonal in
- * the growing half's label, is diagonalised sector by sector (dsyevd), keeping the m
- * largest eigenvalues over all sectors.  Hubbard ladders (DMRG2D_HUBBARD, n_legs <= 4,
+ * the growing half's label, is diagonalised sector by sector (dsyevd; dsyevdx for the m
+ * largest eigenpairs of a sector with more than m states; sectors on concurrent streams),
+ * keeping the m largest eigenvalues over all sectors; the renormalisation of spin blocks
+ * and the wavefunction transformation run label by label on the sector structure.  Hubbard ladders (DMRG2D_HUBBARD, n_legs <= 4,
  * use_sectors = 1, else EUNSUPPORTED): the target sector is (n_up, n_dn) electrons on
  * the whole ladder (on the warm-up's smaller superblocks the same filling per column,
  * rounded half up); blocks carry the creation operators of their boundary column, their
@@ -420,12 +422,14 @@ void dmrg2d_free_ops(dmrg2d_ops* ops);
  * empty (its density matrix is zero there, as on the warm-up's smaller superblocks) keep
  * their states with weight 0 while m allows, so that larger superblocks find them.
  * Density matrices and their eigenvectors are FP64 on the GPU (cuBLAS DSYRK, cuSOLVER
- * dsyevd); ties in the density-matrix spectrum keep the eigenvectors dsyevd returns last.
+ * dsyevd / dsyevdx); ties in the density-matrix spectrum keep the eigenvectors the solver
+ * returns last.
  * Ground states: `precision` FP64 runs the plain Lanczos (thick restart keeping
  * krylov_dim / 4 Ritz vectors, at most 16); TF32/BF16/BF16X3 the mixed solver with FP64
  * refinement (its outer-loop H·v in float pairs, DMRG2D_FP64X) where the tensor-core path
- * supports the superblock's shapes (plain FP64 otherwise).  solver = DMRG2D_SWEEP_DAVIDSON takes dmrg2d_davidson_ground instead (basis
- * of krylov_dim vectors, clamped to 4..48; max_iter Davidson steps; with TF32/BF16/BF16X3
+ * supports the superblock's shapes (plain FP64 otherwise).  solver =
+ * DMRG2D_SWEEP_DAVIDSON takes dmrg2d_davidson_ground instead (basis of krylov_dim
+ * vectors, clamped to 4..48; max_iter Davidson steps; with TF32/BF16/BF16X3
  * the low-precision stage stops at a residual of 1e-3 |E| (1e-2 for BF16) and the FP64
  * outer loop finishes at tol), preconditioned by `precond` (DMRG2D_PRECOND_NONE / JACOBI
  * / MLP).  With DMRG2D_PRECOND_MLP, `mlp` (caller-owned, not NULL) is the learned
