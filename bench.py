@@ -483,21 +483,35 @@ def run_ours(args):
     return 0
 
 
+SWEEP_LATTICES = {
+    # name: (model, columns, sector filling, default --sweep-m, description)
+    "heisenberg4x12": (lambda synth: synth.model("heisenberg", 4, J_leg=1.0, J_rung=1.0), 12,
+                       {}, "128,512,512,1024,1024",
+                       "4x12 open Heisenberg ladder, J=1, S^z_tot = 0 sector"),
+    # the paper's Fig. 3b system: 3 x 10 Hubbard ladder, U/t = 10, 14 up + 14 down
+    "hubbard3x10": (lambda synth: synth.model("hubbard", 3, t=1.0, U=10.0), 10,
+                    {"n_up": 14, "n_dn": 14}, "128,256,256",
+                    "3x10 open Hubbard ladder, t=1, U=10, (N_up, N_dn) = (14, 14)"),
+}
+
+
 def dmrg_sweep_run(args):
-    """The DMRG sweep around the path: 4 x 12 open Heisenberg ladder (J = 1) in the
-    S^z_tot = 0 sector, warm-up with --sweep-m-warmup states, then finite sweeps with the
-    --sweep-m schedule, superblock ground states in --precision with FP64 refinement;
-    energies per sweep and the time split."""
+    """The DMRG sweep around the path on --sweep-lattice (default: the 4 x 12 open
+    Heisenberg ladder, J = 1, in the S^z_tot = 0 sector; or the 3 x 10 Hubbard ladder at
+    U = 10 with 14 + 14 electrons), warm-up with --sweep-m-warmup states, then finite
+    sweeps with the --sweep-m schedule, superblock ground states in --precision with FP64
+    refinement; energies per sweep, the time split and the observables of the last sweep."""
     from paper_0707_0159_gb300 import dmrg2d, synth
-    mdl = synth.model("heisenberg", 4, J_leg=1.0, J_rung=1.0)
-    ms = [int(m) for m in args.sweep_m.split(",")]
+    build, L, filling, m_default, desc = SWEEP_LATTICES[args.sweep_lattice]
+    mdl = build(synth)
+    ms = [int(m) for m in (args.sweep_m or m_default).split(",")]
     prec = args.sweep_precision or args.precision
     net = dmrg2d.MLP(hidden=256, seed=7) if args.sweep_precond == "mlp" else None
-    out = dmrg2d.sweep(mdl, 12, m_warmup=args.sweep_m_warmup, m_sweeps=ms,
+    out = dmrg2d.sweep(mdl, L, m_warmup=args.sweep_m_warmup, m_sweeps=ms,
                        precision=prec, tol=1e-9, max_iter=600, krylov_dim=80,
                        sectors=True, solver=args.sweep_solver, precond=args.sweep_precond,
                        mlp=net, mlp_train_sweeps=args.sweep_mlp_train_sweeps,
-                       mlp_epochs=args.sweep_mlp_epochs)
+                       mlp_epochs=args.sweep_mlp_epochs, **filling)
     e, sw = out["energy"], out["sweep"]
     per = {str(s): min(e[i] for i in range(len(e)) if sw[i] == s) for s in sorted(set(sw))}
     last = max(sw)
@@ -508,7 +522,19 @@ def dmrg_sweep_run(args):
         if sw[i] == last:
             profile[str(out["l"][i])] = out["leg_bond"][i]
     s2 = {str(sw[i]): out["s2"][i] for i in range(len(e)) if out["s2"][i] == out["s2"][i]}
-    return {"lattice": "4x12 open Heisenberg ladder, J=1, S^z_tot = 0 sector",
+    extra = {}
+    if filling:
+        # hole density h(x, y) and S(x) of the central columns x = l, l + 1 of each step of
+        # the last sweep (the paper's Hubbard observables; the end columns are never central)
+        hole, smax = {}, {}
+        for i in range(len(e)):
+            if sw[i] == last:
+                for c in range(2):
+                    x = str(out["l"][i] + c)
+                    hole[x] = [float(v) for v in out["h"][i][c]]
+                    smax[x] = float(out["S"][i][c])
+        extra = {"hole_density_last_sweep": hole, "S_last_sweep": smax}
+    return {"lattice": desc, **extra,
             "m_warmup": args.sweep_m_warmup, "m_sweeps": ms,
             "precision": prec, "solver": args.sweep_solver,
             "precond": args.sweep_precond if args.sweep_solver == "davidson" else None,
@@ -525,7 +551,7 @@ def dmrg_sweep_run(args):
             "solve_seconds": out["solve_seconds"], "build_seconds": out["build_seconds"],
             "density_matrix_seconds": out["dm_seconds"], "renorm_seconds": out["renorm_seconds"],
             "observables_seconds": out["obs_seconds"], "s2_per_sweep": s2,
-            "leg_bond_profile_last_sweep": profile}
+            **({} if filling else {"leg_bond_profile_last_sweep": profile})}
 
 
 def link_probe(dev):
@@ -856,8 +882,9 @@ def main():
                          "reference energy (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep", action="store_true", help="also run the DMRG sweep (4 x 12 ladder)")
-    ap.add_argument("--sweep-m", default="128,512,512,1024,1024",
-                    help="states kept per finite sweep")
+    ap.add_argument("--sweep-lattice", default="heisenberg4x12", choices=sorted(SWEEP_LATTICES))
+    ap.add_argument("--sweep-m", default=None,
+                    help="states kept per finite sweep (default: the lattice's schedule)")
     ap.add_argument("--sweep-m-warmup", type=int, default=128)
     ap.add_argument("--sweep-precision", default=None, choices=["tf32", "bf16", "fp64"],
                     help="ground-state H·v precision of the sweep (default: --precision)")
