@@ -559,6 +559,17 @@ const char* dmrg2d_last_error(void);
 /* Library version string. */
 const char* dmrg2d_version(void);
 
+/* sizeof of a public struct as this library was compiled, for bindings that mirror the
+ * structs (an ABI check; no device work): which = DMRG2D_STRUCT_*; 0 for an unknown
+ * value. */
+enum {
+  DMRG2D_STRUCT_MODEL = 0, DMRG2D_STRUCT_BLOCK = 1, DMRG2D_STRUCT_OPS_INFO = 2,
+  DMRG2D_STRUCT_SOLVER_OPTS = 3, DMRG2D_STRUCT_SOLVER_STATS = 4,
+  DMRG2D_STRUCT_DAVIDSON_OPTS = 5, DMRG2D_STRUCT_SWEEP_OPTS = 6,
+  DMRG2D_STRUCT_SWEEP_REPORT = 7, DMRG2D_STRUCT_STATE_INFO = 8
+};
+size_t dmrg2d_struct_size(int which);
+
 #ifdef __cplusplus
 }
 #endif

@@ -577,6 +577,21 @@ extern "C" const char* dmrg2d_last_error(void) { return g_err.c_str(); }
 
 extern "C" const char* dmrg2d_version(void) { return "dmrg2d-gb300 0.1 (sm_103a)"; }
 
+extern "C" size_t dmrg2d_struct_size(int which) {
+  switch (which) {
+    case DMRG2D_STRUCT_MODEL: return sizeof(dmrg2d_model);
+    case DMRG2D_STRUCT_BLOCK: return sizeof(dmrg2d_block);
+    case DMRG2D_STRUCT_OPS_INFO: return sizeof(dmrg2d_ops_info);
+    case DMRG2D_STRUCT_SOLVER_OPTS: return sizeof(dmrg2d_solver_opts);
+    case DMRG2D_STRUCT_SOLVER_STATS: return sizeof(dmrg2d_solver_stats);
+    case DMRG2D_STRUCT_DAVIDSON_OPTS: return sizeof(dmrg2d_davidson_opts);
+    case DMRG2D_STRUCT_SWEEP_OPTS: return sizeof(dmrg2d_sweep_opts);
+    case DMRG2D_STRUCT_SWEEP_REPORT: return sizeof(dmrg2d_sweep_report);
+    case DMRG2D_STRUCT_STATE_INFO: return sizeof(dmrg2d_state_info);
+    default: return 0;
+  }
+}
+
 extern "C" void dmrg2d_default_solver_opts(dmrg2d_solver_opts* o) {
   if (!o) return;
   o->max_iter = 300;

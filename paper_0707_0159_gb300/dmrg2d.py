@@ -149,6 +149,7 @@ SIGNATURES = {
     "dmrg2d_site_densities": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dmrg2d_last_error": (C.c_char_p, []),
     "dmrg2d_version": (C.c_char_p, []),
+    "dmrg2d_struct_size": (C.c_size_t, [C.c_int]),
 }
 
 

@@ -148,3 +148,16 @@ def test_sweep_rejects_an_unknown_solver(lib):
     assert dmrg2d.lib().dmrg2d_sweep(st._p, dmrg2d.C.byref(opts), dmrg2d.C.byref(rep), None) == -1
     assert st.info()["failed"] == 0
     st.free()
+
+
+def test_mirrored_structs_match_the_library(lib):
+    """Every struct the binding mirrors has the size the library was compiled with (a
+    field added on one side only would shift every later field)."""
+    from paper_0707_0159_gb300 import dmrg2d
+    C = dmrg2d.C
+    pairs = [(0, dmrg2d.Model), (1, dmrg2d.Block), (2, dmrg2d.OpsInfo), (3, dmrg2d.SolverOpts),
+             (4, dmrg2d.SolverStats), (5, dmrg2d.DavidsonOpts), (6, dmrg2d.SweepOpts),
+             (7, dmrg2d.SweepReport), (8, dmrg2d.StateInfo)]
+    for which, cls in pairs:
+        assert dmrg2d.lib().dmrg2d_struct_size(which) == C.sizeof(cls), cls.__name__
+    assert dmrg2d.lib().dmrg2d_struct_size(99) == 0
