@@ -161,3 +161,39 @@ def test_mirrored_structs_match_the_library(lib):
     for which, cls in pairs:
         assert dmrg2d.lib().dmrg2d_struct_size(which) == C.sizeof(cls), cls.__name__
     assert dmrg2d.lib().dmrg2d_struct_size(99) == 0
+
+
+def test_header_compiles_as_c_and_links(lib, tmp_path):
+    """The boundary is a C ABI: include/dmrg2d.h compiles as C99 with warnings as errors,
+    and a C program that calls the library through it links against libdmrg2d.so and
+    runs (host-only calls: version, defaults, struct sizes)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "use.c"
+    src.write_text(
+        '#include "dmrg2d.h"\n'
+        "#include <stdio.h>\n"
+        "int main(void) {\n"
+        "  dmrg2d_solver_opts o;\n"
+        "  dmrg2d_default_solver_opts(&o);\n"
+        "  if (o.max_iter < 1) return 2;\n"
+        "  if (dmrg2d_struct_size(DMRG2D_STRUCT_SWEEP_OPTS) != sizeof(dmrg2d_sweep_opts))\n"
+        "    return 3;\n"
+        "  if (dmrg2d_struct_size(DMRG2D_STRUCT_SWEEP_REPORT) != sizeof(dmrg2d_sweep_report))\n"
+        "    return 4;\n"
+        '  printf("%s\\n", dmrg2d_version());\n'
+        "  return 0;\n"
+        "}\n")
+    exe = tmp_path / "use"
+    libdir = os.path.join(root, "paper_0707_0159_gb300")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(root, "include"),
+                        str(src), "-o", str(exe), "-L", libdir, "-ldmrg2d",
+                        "-Wl,-rpath," + libdir], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, (r.returncode, r.stderr)
+    assert "dmrg2d" in r.stdout
