@@ -40,10 +40,11 @@ METRIC = "superblock H·v TFLOP/s & time to ground energy at 1e-8 rel. vs plain 
 
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture of
 # this workload (dram__bytes_read.sum + dram__bytes_write.sum), keyed by tile
-# configuration name and dtype.  They hold only for the kernel source they were taken
-# on: `traffic` is reported as null when csrc/hv_tc.cu no longer has this SHA-256.
+# configuration name and dtype.  They hold only for the kernel code they were taken on:
+# `traffic` is reported as null when the device part of csrc/hv_tc.cu (everything before
+# its host-side section) together with csrc/tc_ptx.cuh no longer has this SHA-256.
 NCU_TRAFFIC = {
-    "hv_tc.cu sha256": "91219050f32fedb6f43c765dd1f019281b6f570488124341b14d92751c68d004",
+    "kernel sha256": "d49bf130d81d1a0bdd43a4515dc1382c9e7a80cca9432f14a5533abd182f5af8",
     "bytes": {
         "CTA-pair kernel 256x256 (8x8-tile blocked raster), phase-2 V in one 3-D copy|tf32":
             15.21e9 + 1.07e9,
@@ -53,12 +54,21 @@ NCU_TRAFFIC = {
 }
 
 
-def ncu_traffic(config_name, dtype):
+def kernel_digest():
+    """SHA-256 of the tensor-core kernels' source: csrc/hv_tc.cu up to its host-side
+    section, then csrc/tc_ptx.cuh."""
     import hashlib
-    src = os.path.join(ROOT, "paper_0707_0159_gb300", "csrc", "hv_tc.cu")
-    with open(src, "rb") as f:
-        digest = hashlib.sha256(f.read()).hexdigest()
-    if digest != NCU_TRAFFIC["hv_tc.cu sha256"]:
+    csrc = os.path.join(ROOT, "paper_0707_0159_gb300", "csrc")
+    with open(os.path.join(csrc, "hv_tc.cu"), "rb") as f:
+        hv = f.read()
+    with open(os.path.join(csrc, "tc_ptx.cuh"), "rb") as f:
+        ptx = f.read()
+    cut = hv.find(b"// ---- host side")
+    return hashlib.sha256((hv if cut < 0 else hv[:cut]) + ptx).hexdigest()
+
+
+def ncu_traffic(config_name, dtype):
+    if kernel_digest() != NCU_TRAFFIC["kernel sha256"]:
         return None
     return NCU_TRAFFIC["bytes"].get(f"{config_name}|{dtype}")
 WORKLOAD = "ladder3_hubbard_d64_m256_dense"

@@ -1270,7 +1270,7 @@ extern "C" int dmrg2d_autotune(dmrg2d_ops* ops, int precision, int* best, double
     double t = -1.0;
     if (tc_candidate_ok(ops, c)) {
       st = tc_run_candidate(ops, v, y, precision, c, s);  // warm-up
-      if (st == DMRG2D_EUNSUPPORTED) {  // a candidate whose tensor maps the driver refuses
+      if (st == DMRG2D_EUNSUPPORTED) {  // a candidate whose tensor maps cannot be encoded
         st = DMRG2D_OK;
         clear_error();
         if (ms && c < n_ms) ms[c] = -1.0;

@@ -1,5 +1,5 @@
 """The benchmark's JSON contract on the host: the reference arm (the CPU oracle timed on a
-bounded sample of the workload) prints one line with the fields the driver reads, and the
+bounded sample of the workload) prints one JSON line with the contract's fields, and the
 option parser offers every documented mode."""
 import json
 import os
